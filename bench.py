@@ -1,0 +1,384 @@
+"""Throughput benchmark of the TVLBM sweep: MLUPS and fraction of the HBM roofline.
+
+Default workload (one GPU): 1024 x 1024 periodic D2Q16, FP32 populations, tau = 0.7,
+T = 1 + 0.05 Gaussian bump (sigma 64 cells), seeded random Fourier flow (|k| <= 8, 0.02).
+One bench step = the workload's full run of 1000 time steps (each time step is one fused
+stream+collide sweep over the grid).  Inputs are resident in HBM when a timed step starts; the
+L2 is flushed (a 512 MiB write) between timed steps, outside the timed events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload c1|c1_4096|c0|c2] [--form tiled|plain] [--no-cpu-baseline]
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle on this machine's host
+cores on the same workload (each step a bounded sample of the time steps).  Under torchrun
+(N > 1) every rank advances its own replica of the workload (no data exchange) and the line
+reports the aggregate.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+WORKLOADS = {
+    "c1": dict(desc="D2Q16 1024x1024 periodic FP32 tau=0.7, Gaussian T bump + random Fourier flow, 1000 time steps",
+               nx=1024, ny=1024, velset="D2Q16", storage="fp32", tau=0.7, walls=None, tsteps=1000),
+    "c1_4096": dict(desc="D2Q16 4096x4096 periodic FP32 tau=0.7 (C1 recipe, sigma 256), 100 time steps",
+                    nx=4096, ny=4096, velset="D2Q16", storage="fp32", tau=0.7, walls=None, tsteps=100),
+    "c0": dict(desc="D2Q16 64x64 periodic FP64 tau=0.8 shear wave, 200 time steps",
+               nx=64, ny=64, velset="D2Q16", storage="fp64", tau=0.8, walls=None, tsteps=200),
+    "c2": dict(desc="D2Q36 4096x512 thermal Couette FP16-deviation storage tau=0.9, walls T=1.0/1.1, u_top=0.1, "
+                    "1000 time steps", nx=4096, ny=512, velset="D2Q36", storage="fp16_dev", tau=0.9,
+               walls=(0.0, 1.0, 0.1, 1.1), tsteps=1000),
+}
+
+METRIC = "MLUPS (million lattice-cell updates per second) of the fused TVLBM sweep"
+UNIT = "MLUPS"
+
+
+def fields_for(name, w):
+    nx, ny = w["nx"], w["ny"]
+    if name.startswith("c1"):
+        return workloads.gaussian_bump_random_flow(nx, ny, seed=1, sigma=64.0 * nx / 1024)
+    if name == "c0":
+        return workloads.shear_wave(nx, ny, eps=0.01)
+    return workloads.couette_linear(nx, ny, 1.0, 1.1)
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+class Clocks:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + ",".join(self.FIELDS),
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[3 + k].lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak_hbm():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_traffic(workload, form):
+    """DRAM bytes per sweep launch from the committed ncu summary, if it was taken on the
+    current kernel sources (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1004_5059_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, fn), "rb").read())
+    e = d.get("%s/%s" % (workload, form))
+    if not e or e.get("csrc_sha256") != h.hexdigest():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def run_ours(args, w, rank, world, local_rank):
+    import torch
+    import paper_1004_5059_gb300 as tv
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    nx, ny, tsteps = w["nx"], w["ny"], w["tsteps"]
+    cells = nx * ny
+    fields = fields_for(args.workload, w)
+    stream = torch.cuda.current_stream(dev)
+
+    def make(form):
+        s = tv.Simulation(nx, ny, w["velset"], tau=w["tau"], dt=1.0, walls=w["walls"], storage=w["storage"],
+                          form=form, stream=stream)
+        s.init_moments(*fields)
+        return s
+
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def timed(sim, K, W):
+        for _ in range(W):
+            sim.step(tsteps)
+        torch.cuda.synchronize()
+        evs = []
+        barrier()
+        torch.cuda.synchronize()
+        for _ in range(K):
+            flush.zero_()  # evict the L2 between timed steps (outside the events)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sim.step(tsteps)
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        barrier()
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        return ms
+
+    forms = []
+    probe = make(args.form)
+    chosen = args.form
+    forms.append(chosen)
+    clocks = Clocks(local_rank)
+    clocks.start()
+    ms_total = timed(probe, args.steps, args.warmup)
+    clk = clocks.stop()
+    bytes_per_cell = probe.bytes_per_cell()
+    t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    launches_per_tstep = 2 if w["walls"] else 1
+    sweep_launches = args.steps * tsteps
+    avg_launch_s = ms_total / 1e3 / sweep_launches  # wall kernels of wall runs are counted in
+    value = world * cells * tsteps * args.steps / (ms_max / 1e3) / 1e6
+
+    # plain form beside the chosen one (the metric reports both)
+    plain = None
+    if chosen != "plain":
+        sp = make("plain")
+        msp = timed(sp, max(1, args.steps // 2), 1)
+        plain_launch_s = msp / 1e3 / (max(1, args.steps // 2) * tsteps)
+        plain = {"value": cells * tsteps * max(1, args.steps // 2) / (msp / 1e3) / 1e6, "unit": UNIT,
+                 "roofline_frac": None}
+        sp.close()
+
+    # end to end through the C ABI with host buffers: init from pinned host fields (H2D),
+    # run the time steps, read the moments back (D2H), every step
+    pinned_in = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in fields]
+    pinned_out = [torch.empty((ny, nx), dtype=torch.float64).pin_memory() for _ in range(4)]
+    host_in = [p.numpy() for p in pinned_in]
+    host_out = [p.numpy() for p in pinned_out]
+    e2e_steps = max(1, min(args.steps, 5))
+    probe.init_moments(*host_in)
+    probe.step(tsteps)
+    tv.tvlbm_moments(probe.ctx, nx, ny, out=host_out)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        probe.init_moments(*host_in)
+        probe.step(tsteps)
+        tv.tvlbm_moments(probe.ctx, nx, ny, out=host_out)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_value = world * cells * tsteps * e2e_steps / float(t.item()) / 1e6
+
+    peak, peak_kind = measured_peak_hbm()
+    achieved = bytes_per_cell * cells / avg_launch_s / 1e9
+    if plain is not None:
+        plain["roofline_frac"] = bytes_per_cell * cells / plain_launch_s / 1e9 / peak
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "fp64": "f64", "fp16_dev": "f32 (f16 storage)", "bf16_dev": "f32 (bf16 storage)",
+                  "fp32_dev": "f32"}[w["storage"]],
+        "data": "synthetic (seeded fields shaped like the paper's test problems)",
+        "config": {"workload": w["desc"], "nx": nx, "ny": ny, "velset": w["velset"], "storage": w["storage"],
+                   "tau": w["tau"], "time_steps_per_bench_step": tsteps, "form": chosen,
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "L2 flushed (512 MiB write) between timed steps; state %.0f MB" % (
+                       2 * bytes_per_cell / 2 * cells / 1e6)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_kind": peak_kind, "bytes_per_cell": bytes_per_cell,
+                     "traffic": kernel_traffic(args.workload, chosen)},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * 8 * cells,
+                "d2h_bytes_per_step": 4 * 8 * cells},
+        "gpu_launches": args.steps * tsteps * launches_per_tstep,
+        "clocks": clk,
+    }
+    if plain is not None:
+        line["plain_form"] = plain
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.workload, w, fields, probe)
+    probe.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return line if rank == 0 else None
+
+
+def _oracle_threads():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(name, w, fields, sim=None, target_s=12.0):
+    """The FP64 oracle, as it stands, on this machine's host cores, over a bounded sample of the
+    workload's time steps (whole grid); also compares the GPU after the same number of steps."""
+    import oracle
+    cores = _oracle_threads()
+    o = oracle.Oracle(w["nx"], w["ny"], w["velset"], tau=w["tau"], dt=1.0, walls=w["walls"], threads=cores)
+    o.init_moments(*fields)
+    t0 = time.perf_counter()
+    o.run(1)
+    one = time.perf_counter() - t0
+    n = int(max(1, min(w["tsteps"] - 1, target_s / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    o.run(n)
+    dt = time.perf_counter() - t0
+    out = {"value": w["nx"] * w["ny"] * n / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": "%d of the workload's %d time steps on the full %dx%d grid (after 1 untimed step)" % (
+               n, w["tsteps"], w["nx"], w["ny"])}
+    if sim is not None:
+        sim.init_moments(*fields)
+        sim.step(n + 1)
+        got = sim.moments()
+        want = o.moments()
+        e_rho = float(np.max(np.abs(got[0] - want[0])) / np.max(np.abs(want[0])))
+        umax = max(np.max(np.abs(want[1])), np.max(np.abs(want[2])))
+        e_u = float(max(np.max(np.abs(got[1] - want[1])), np.max(np.abs(got[2] - want[2]))) / umax)
+        e_T = float(np.max(np.abs(got[3] - want[3])) / np.max(np.abs(want[3])))
+        out["gpu_vs_oracle_after_sample"] = {"time_steps": n + 1, "max_rel_err_rho": e_rho, "max_rel_err_u": e_u,
+                                             "max_rel_err_T": e_T}
+    return out
+
+
+def run_reference(args, w, rank, world):
+    """The FP64 CPU oracle timed on the host cores: each bench step runs a bounded sample of
+    `sample_steps` of the workload's time steps on the full grid."""
+    if rank != 0:
+        return None
+    import oracle
+    cores = _oracle_threads()
+    fields = fields_for(args.workload, w)
+    o = oracle.Oracle(w["nx"], w["ny"], w["velset"], tau=w["tau"], dt=1.0, walls=w["walls"], threads=cores)
+    o.init_moments(*fields)
+    t0 = time.perf_counter()
+    o.run(1)
+    one = time.perf_counter() - t0
+    # size each step so that warmup + steps stay within ~3 minutes
+    per_step_budget = 180.0 / max(1, args.steps + args.warmup)
+    sample = int(max(1, min(w["tsteps"], per_step_budget / max(one, 1e-6))))
+    for _ in range(args.warmup):
+        o.run(sample)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.run(sample)
+    dt = time.perf_counter() - t0
+    value = w["nx"] * w["ny"] * sample * args.steps / dt / 1e6
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["desc"], "nx": w["nx"], "ny": w["ny"], "velset": w["velset"],
+                   "storage": "fp64 (oracle)", "tau": w["tau"], "time_steps_per_bench_step": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "%d of the workload's %d time steps per bench step, full grid" % (sample, w["tsteps"])},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c1", choices=sorted(WORKLOADS))
+    ap.add_argument("--form", default=None, choices=["tiled", "plain"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local_rank = dist_env()
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        line = run_reference(args, w, rank, world)
+    else:
+        if args.form is None:
+            import paper_1004_5059_gb300 as tv
+            import torch
+            torch.cuda.set_device(local_rank)
+            s = tv.Simulation(16, 16, w["velset"], storage=w["storage"])
+            try:
+                s.set_form("tiled")
+                args.form = "tiled"
+            except tv.TvlbmError:
+                args.form = "plain"
+            s.close()
+        line = run_ours(args, w, rank, world, local_rank)
+    if rank == 0 and line is not None:
+        print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

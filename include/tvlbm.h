@@ -1,0 +1,182 @@
+/*
+ * tvlbm.h -- C ABI of the GB300 thermal volumetric lattice Boltzmann (TVLBM) library.
+ *
+ * The library advances the BGK kinetic equation (Eq. "eq:lb") on a 2-D grid of unit cells
+ * with an off-lattice tensor-product Gauss-Hermite velocity set.  One time step is one fused
+ * CUDA sweep:
+ *   stream   every population moves by c_l dt and is shared among the (up to four) cells its
+ *            shifted cell volume overlaps, with area-overlap weights fixed per velocity
+ *            (the volumetric formulation of the Introduction: off-lattice velocities without
+ *            giving up exact conservation), written as a pull-gather;
+ *   moments  rho, u, T (Sec. "The TVLBM model", moment definitions);
+ *   equilib. the Hermite expansion f_eq = w sum_n a^(n):H^(n)/n! (Sec. "The TVLBM model";
+ *            Appendix A), truncated at the order the velocity set integrates exactly;
+ *   relax    f* = f - (dt/tau)(f - f_eq).
+ * Walls (optional) are diffuse reflectors: the flux that leaves the fluid through a wall is
+ * re-emitted in the shape of the wall equilibrium (Sec. "Boundary Condition: Diffuse
+ * Scattering Kernel", Eq. IMPOSITION).
+ *
+ * Conventions for every call:
+ *   - returns TVLBM_OK (0) or a negative TVLBM_E* code; never aborts or exits;
+ *     tvlbm_last_error() gives a message for the last failing call on a context;
+ *   - host buffers passed in are owned by the caller and only used during the call;
+ *   - device memory given to tvlbm_create_in is owned by the caller and must outlive the
+ *     context; memory the library allocates itself is freed by tvlbm_destroy;
+ *   - grid fields are row-major [ny][nx] (x fastest), FP64; population arrays are
+ *     [Q][ny][nx] with velocity index l = i + n*j, where c_l = (x_i, x_j) and x_0 < ... < x_{n-1}
+ *     are the n Gauss-Hermite nodes (n = 3, 4, 6 for D2Q9, D2Q16, D2Q36);
+ *   - lattice units: cell size dx = dy = 1, sound speed c_s = 1 (reference temperature 1);
+ *   - calls on one context are not thread-safe; distinct contexts are independent.
+ *   - GPU work is queued on the context's stream (tvlbm_set_stream); calls that return
+ *     host data synchronise that stream.
+ */
+#ifndef TVLBM_H
+#define TVLBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------------- */
+#define TVLBM_OK 0
+#define TVLBM_EINVAL (-1)     /* invalid argument (size, parameter, null pointer, combination) */
+#define TVLBM_ENOMEM (-2)     /* device or host allocation failed, or caller memory too small */
+#define TVLBM_ECUDA (-3)      /* a CUDA runtime call failed (including: no GPU present)        */
+#define TVLBM_ESTATE (-4)     /* call not valid in the context's current state                 */
+#define TVLBM_ETIMEOUT (-5)   /* a bounded device-side wait gave up                            */
+#define TVLBM_ENONFINITE (-6) /* non-finite populations detected                               */
+
+/* ---- velocity sets: tensor products of n-point Gauss-Hermite rules ----------------------- */
+#define TVLBM_D2Q9 9   /* n = 3, nodes 0, +-sqrt(3); Hermite order N = 2                 */
+#define TVLBM_D2Q16 16 /* n = 4, nodes +-sqrt(3 -+ sqrt 6); N = 3                        */
+#define TVLBM_D2Q36 36 /* n = 6; N = 5                                                   */
+
+/* ---- population storage ----------------------------------------------------------------- */
+#define TVLBM_FP64 0     /* f_l as double; FP64 arithmetic                                   */
+#define TVLBM_FP32 1     /* f_l as float;  FP32 arithmetic                                   */
+#define TVLBM_BF16_DEV 2 /* d_l = (f_l - w_l rho0)/w_l as bfloat16 (round to nearest even);
+                            FP32 arithmetic                                                   */
+#define TVLBM_FP16_DEV 3 /* d_l as IEEE binary16 (round to nearest even); FP32 arithmetic     */
+#define TVLBM_FP32_DEV 4 /* d_l as float; FP32 arithmetic                                      */
+
+/* ---- sweep kernel forms ------------------------------------------------------------------ */
+#define TVLBM_FORM_PLAIN 0 /* one thread per cell, direct gathers from global memory           */
+#define TVLBM_FORM_TILED 1 /* 2-D tiles whose per-velocity source windows are staged in shared
+                              memory by TMA; the default                                       */
+
+/* ---- boundary conditions ----------------------------------------------------------------- */
+#define TVLBM_BC_PERIODIC 0
+#define TVLBM_BC_WALLS 1 /* periodic in x; diffuse walls on the faces y = -1/2 and y = ny - 1/2 */
+
+typedef struct tvlbm_bc {
+    int kind;    /* TVLBM_BC_PERIODIC or TVLBM_BC_WALLS                               */
+    double u_lo; /* x-velocity of the wall at y = -1/2 (walls only)                   */
+    double T_lo; /* temperature of that wall, > 0                                     */
+    double u_hi; /* x-velocity of the wall at y = ny - 1/2                            */
+    double T_hi; /* temperature of that wall, > 0                                     */
+} tvlbm_bc;
+
+typedef struct tvlbm_ctx tvlbm_ctx;
+
+/* Device bytes a context needs for these arguments (populations, ghost frame, scratch).
+ * Host-only; needs no GPU.  bc may be NULL (periodic).  Errors: EINVAL. */
+int tvlbm_memory_bytes(int nx, int ny, int velset, const tvlbm_bc *bc, int storage, size_t *bytes);
+
+/* Create a context on the current CUDA device and allocate its device memory.
+ *   nx, ny   fluid cells, >= 1 each (walls: ny >= 9);  nx*ny < 2^31
+ *   velset   TVLBM_D2Q9 / TVLBM_D2Q16 / TVLBM_D2Q36
+ *   tau      BGK relaxation time (Eq. "eq:lb"), tau > dt/2 for a positive viscosity;
+ *            +inf gives collisionless streaming
+ *   dt       time step; every shift |c dt| must stay below 4 cells
+ *   bc       boundary conditions, NULL for periodic
+ *   storage  TVLBM_FP64 .. TVLBM_FP32_DEV
+ *   rho0     reference density of the deviation storage (also used by FP storage), > 0
+ * Populations start at the rest equilibrium f = rho0 w_l.  *out receives the handle.
+ * Errors: EINVAL (arguments), ENOMEM, ECUDA (no device or a CUDA failure). */
+int tvlbm_create(int nx, int ny, int velset, double tau, double dt, const tvlbm_bc *bc, int storage,
+                 double rho0, tvlbm_ctx **out);
+
+/* As tvlbm_create, but the context lives in caller-owned device memory `device_memory` of
+ * `bytes` >= tvlbm_memory_bytes(...) bytes, 256-byte aligned; the library allocates no device
+ * memory.  Errors: EINVAL, ENOMEM (too small), ECUDA. */
+int tvlbm_create_in(int nx, int ny, int velset, double tau, double dt, const tvlbm_bc *bc, int storage,
+                    double rho0, void *device_memory, size_t bytes, tvlbm_ctx **out);
+
+/* Free the context (synchronises its stream first).  NULL is accepted. */
+int tvlbm_destroy(tvlbm_ctx *ctx);
+
+/* Queue all later GPU work of this context on `stream` (a cudaStream_t; NULL = legacy default).
+ * The stream must belong to the context's device. */
+int tvlbm_set_stream(tvlbm_ctx *ctx, void *stream);
+
+/* Select the sweep kernel form (TVLBM_FORM_PLAIN / TVLBM_FORM_TILED).  Both give the same
+ * populations up to floating-point rounding order. */
+int tvlbm_set_form(tvlbm_ctx *ctx, int form);
+
+/* Enable (1, default) or disable (0) replay of multi-step runs through captured CUDA graphs. */
+int tvlbm_set_graphs(tvlbm_ctx *ctx, int enable);
+
+/* Initialise every cell to the equilibrium f_eq(rho, u, T) (Sec. "The TVLBM model"),
+ * computed in FP64 and rounded to the storage format.  Host FP64 fields [ny][nx];
+ * requires rho > 0 and T > 0 everywhere (EINVAL otherwise, nothing written).
+ * Synchronises the stream. */
+int tvlbm_init_moments(tvlbm_ctx *ctx, const double *rho, const double *ux, const double *uy, const double *T);
+
+/* Advance n >= 0 time steps (asynchronous on the context's stream).  Each step: (walls) fill
+ * the ghost rows from the flux leaving the fluid (Eq. IMPOSITION), then one fused sweep
+ * stream -> moments -> equilibrium -> BGK -> store.  Errors: EINVAL (n < 0), ECUDA. */
+int tvlbm_step(tvlbm_ctx *ctx, int n);
+
+/* Macroscopic fields of the current state (Sec. "The TVLBM model": rho = sum f,
+ * rho u = sum c f, rho T = (1/D) sum |c - u|^2 f, D = 2), computed in FP64 on the GPU from
+ * the stored populations.  Any output pointer may be NULL.  Host arrays [ny][nx].
+ * Synchronises the stream. */
+int tvlbm_moments(tvlbm_ctx *ctx, double *rho, double *ux, double *uy, double *T);
+
+/* Global sums over all fluid cells and velocities, accumulated in FP64 on the GPU by a
+ * deterministic two-pass reduction (the conserved quantities of the Abstract and Sec. "The
+ * TVLBM model"):
+ *   out[0] = M  = sum f,  out[1] = P_x = sum c_x f,  out[2] = P_y = sum c_y f,
+ *   out[3] = E  = (1/2) sum |c|^2 f,  out[4] = number of non-finite stored populations.
+ * Synchronises the stream. */
+int tvlbm_conserved_sums(tvlbm_ctx *ctx, double out[5]);
+
+/* Checkpoint: copy the raw stored populations (storage format, [Q][ny][nx], no ghost frame)
+ * to / from host memory of exactly tvlbm_population_bytes(ctx) bytes.  set_populations also
+ * refreshes the periodic ghost frame.  Both synchronise the stream.  Errors: EINVAL (size). */
+size_t tvlbm_population_bytes(const tvlbm_ctx *ctx);
+int tvlbm_get_populations(tvlbm_ctx *ctx, void *host, size_t bytes);
+int tvlbm_set_populations(tvlbm_ctx *ctx, const void *host, size_t bytes);
+
+/* Populations decoded to f_l in FP64, [Q][ny][nx] (deviation storage: f = w (rho0 + d)). */
+int tvlbm_get_populations_f64(tvlbm_ctx *ctx, double *host);
+/* Encode FP64 populations f_l [Q][ny][nx] into the storage format (round to nearest even). */
+int tvlbm_set_populations_f64(tvlbm_ctx *ctx, const double *host);
+
+/* The library's velocity set (host-only; no GPU): Q nodes c_l = (cx[l], cy[l]) and weights
+ * w[l], ordered l = i + n j; *hermite_order receives N.  Arrays hold >= 36 entries.
+ * Errors: EINVAL (unknown set). */
+int tvlbm_velocity_set(int velset, double *cx, double *cy, double *w, int *hermite_order);
+
+/* Per-velocity streaming table (host-only): shift of c_l dt in cells along x and y as
+ * integer part (floor) and overlap fraction alpha in [0, 1); a shift within 1e-12 of an
+ * integer counts as that integer with alpha = 0.  Arrays hold >= 36 entries. */
+int tvlbm_stream_table(int velset, double dt, int *sx, int *sy, double *ax, double *ay);
+
+/* Algorithmic bytes moved by one sweep per fluid cell: Q * (read + write) * bytes per stored
+ * population (halo re-reads and ghost-frame copies not counted). */
+double tvlbm_bytes_per_cell(const tvlbm_ctx *ctx);
+
+/* Message of the last failing call on ctx (never NULL; "" if none). */
+const char *tvlbm_last_error(const tvlbm_ctx *ctx);
+
+/* Static description of a status code. */
+const char *tvlbm_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TVLBM_H */

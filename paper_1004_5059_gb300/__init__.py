@@ -1,0 +1,297 @@
+"""Python binding of the GB300 TVLBM library (include/tvlbm.h).
+
+Argument marshalling only: every step of the time loop runs in the library's CUDA kernels.
+PyTorch supplies device memory (contexts are created inside a torch-allocated block through
+tvlbm_create_in) and the stream (torch's current stream).  There is no CPU fallback: if the
+compiled library is missing, importing this package raises.
+
+The functions mirror the C names; `Simulation` bundles them for one context.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtvlbm.so")
+
+TVLBM_OK = 0
+TVLBM_EINVAL = -1
+TVLBM_ENOMEM = -2
+TVLBM_ECUDA = -3
+TVLBM_ESTATE = -4
+TVLBM_ETIMEOUT = -5
+TVLBM_ENONFINITE = -6
+
+TVLBM_D2Q9, TVLBM_D2Q16, TVLBM_D2Q36 = 9, 16, 36
+TVLBM_FP64, TVLBM_FP32, TVLBM_BF16_DEV, TVLBM_FP16_DEV, TVLBM_FP32_DEV = 0, 1, 2, 3, 4
+TVLBM_FORM_PLAIN, TVLBM_FORM_TILED = 0, 1
+TVLBM_BC_PERIODIC, TVLBM_BC_WALLS = 0, 1
+
+VELSETS = {"D2Q9": TVLBM_D2Q9, "D2Q16": TVLBM_D2Q16, "D2Q36": TVLBM_D2Q36}
+STORAGES = {"fp64": TVLBM_FP64, "fp32": TVLBM_FP32, "bf16_dev": TVLBM_BF16_DEV, "fp16_dev": TVLBM_FP16_DEV,
+            "fp32_dev": TVLBM_FP32_DEV}
+FORMS = {"plain": TVLBM_FORM_PLAIN, "tiled": TVLBM_FORM_TILED}
+STORAGE_NUMPY = {TVLBM_FP64: np.float64, TVLBM_FP32: np.float32, TVLBM_FP32_DEV: np.float32,
+                 TVLBM_BF16_DEV: np.uint16, TVLBM_FP16_DEV: np.float16}
+
+
+class TvlbmError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__("tvlbm error %d: %s" % (code, message))
+        self.code = code
+
+
+class tvlbm_bc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("u_lo", ctypes.c_double), ("T_lo", ctypes.c_double),
+                ("u_hi", ctypes.c_double), ("T_hi", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_DP = ctypes.POINTER(ctypes.c_double)
+_IP = ctypes.POINTER(ctypes.c_int)
+_SZ = ctypes.c_size_t
+
+
+def _load_library() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libtvlbm.so is not built (run __graft_entry__.build() or "
+                          "python paper_1004_5059_gb300/build.py); there is no fallback")
+    lib = ctypes.CDLL(LIB_PATH)
+    sig = {
+        "tvlbm_memory_bytes": (_I, [_I, _I, _I, ctypes.POINTER(tvlbm_bc), _I, ctypes.POINTER(_SZ)]),
+        "tvlbm_create": (_I, [_I, _I, _I, _D, _D, ctypes.POINTER(tvlbm_bc), _I, _D, ctypes.POINTER(_P)]),
+        "tvlbm_create_in": (_I, [_I, _I, _I, _D, _D, ctypes.POINTER(tvlbm_bc), _I, _D, _P, _SZ, ctypes.POINTER(_P)]),
+        "tvlbm_destroy": (_I, [_P]),
+        "tvlbm_set_stream": (_I, [_P, _P]),
+        "tvlbm_set_form": (_I, [_P, _I]),
+        "tvlbm_set_graphs": (_I, [_P, _I]),
+        "tvlbm_init_moments": (_I, [_P, _DP, _DP, _DP, _DP]),
+        "tvlbm_step": (_I, [_P, _I]),
+        "tvlbm_moments": (_I, [_P, _DP, _DP, _DP, _DP]),
+        "tvlbm_conserved_sums": (_I, [_P, _DP]),
+        "tvlbm_population_bytes": (_SZ, [_P]),
+        "tvlbm_get_populations": (_I, [_P, _P, _SZ]),
+        "tvlbm_set_populations": (_I, [_P, _P, _SZ]),
+        "tvlbm_get_populations_f64": (_I, [_P, _DP]),
+        "tvlbm_set_populations_f64": (_I, [_P, _DP]),
+        "tvlbm_velocity_set": (_I, [_I, _DP, _DP, _DP, _IP]),
+        "tvlbm_stream_table": (_I, [_I, _D, _IP, _IP, _DP, _DP]),
+        "tvlbm_bytes_per_cell": (_D, [_P]),
+        "tvlbm_last_error": (ctypes.c_char_p, [_P]),
+        "tvlbm_strerror": (ctypes.c_char_p, [_I]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load_library()
+lib = _lib
+
+
+def _dp(a: np.ndarray):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_DP)
+
+
+def _check(rc: int, ctx=None):
+    if rc != TVLBM_OK:
+        msg = _lib.tvlbm_last_error(ctx).decode() if ctx else ""
+        raise TvlbmError(rc, msg or _lib.tvlbm_strerror(rc).decode())
+
+
+def _bc(bc):
+    if bc is None:
+        return None
+    if isinstance(bc, tvlbm_bc):
+        return ctypes.byref(bc)
+    u_lo, T_lo, u_hi, T_hi = bc
+    return ctypes.byref(tvlbm_bc(TVLBM_BC_WALLS, u_lo, T_lo, u_hi, T_hi))
+
+
+# ---- functions with the C names -----------------------------------------------------------
+
+def tvlbm_memory_bytes(nx, ny, velset, bc, storage) -> int:
+    out = _SZ(0)
+    _check(_lib.tvlbm_memory_bytes(nx, ny, velset, _bc(bc), storage, ctypes.byref(out)))
+    return out.value
+
+
+def tvlbm_create(nx, ny, velset, tau, dt, bc, storage, rho0):
+    h = _P()
+    _check(_lib.tvlbm_create(nx, ny, velset, tau, dt, _bc(bc), storage, rho0, ctypes.byref(h)))
+    return h
+
+
+def tvlbm_create_in(nx, ny, velset, tau, dt, bc, storage, rho0, device_ptr: int, nbytes: int):
+    h = _P()
+    _check(_lib.tvlbm_create_in(nx, ny, velset, tau, dt, _bc(bc), storage, rho0, _P(device_ptr), nbytes,
+                                ctypes.byref(h)))
+    return h
+
+
+def tvlbm_destroy(ctx):
+    _check(_lib.tvlbm_destroy(ctx))
+
+
+def tvlbm_set_stream(ctx, stream_handle: int):
+    _check(_lib.tvlbm_set_stream(ctx, _P(stream_handle)), ctx)
+
+
+def tvlbm_set_form(ctx, form: int):
+    _check(_lib.tvlbm_set_form(ctx, form), ctx)
+
+
+def tvlbm_set_graphs(ctx, enable: bool):
+    _check(_lib.tvlbm_set_graphs(ctx, 1 if enable else 0), ctx)
+
+
+def tvlbm_init_moments(ctx, rho, ux, uy, T):
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (rho, ux, uy, T)]
+    _check(_lib.tvlbm_init_moments(ctx, *[_dp(a) for a in arrs]), ctx)
+
+
+def tvlbm_step(ctx, n: int):
+    _check(_lib.tvlbm_step(ctx, int(n)), ctx)
+
+
+def tvlbm_moments(ctx, nx, ny, out=None):
+    outs = out if out is not None else [np.empty((ny, nx)) for _ in range(4)]
+    _check(_lib.tvlbm_moments(ctx, *[_dp(o) for o in outs]), ctx)
+    return tuple(outs)
+
+
+def tvlbm_conserved_sums(ctx) -> np.ndarray:
+    out = np.zeros(5)
+    _check(_lib.tvlbm_conserved_sums(ctx, _dp(out)), ctx)
+    return out
+
+
+def tvlbm_population_bytes(ctx) -> int:
+    return int(_lib.tvlbm_population_bytes(ctx))
+
+
+def tvlbm_get_populations(ctx, host: np.ndarray):
+    _check(_lib.tvlbm_get_populations(ctx, host.ctypes.data_as(_P), host.nbytes), ctx)
+    return host
+
+
+def tvlbm_set_populations(ctx, host: np.ndarray):
+    host = np.ascontiguousarray(host)
+    _check(_lib.tvlbm_set_populations(ctx, host.ctypes.data_as(_P), host.nbytes), ctx)
+
+
+def tvlbm_get_populations_f64(ctx, out: np.ndarray):
+    _check(_lib.tvlbm_get_populations_f64(ctx, _dp(out)), ctx)
+    return out
+
+
+def tvlbm_set_populations_f64(ctx, f: np.ndarray):
+    _check(_lib.tvlbm_set_populations_f64(ctx, _dp(np.ascontiguousarray(f, dtype=np.float64))), ctx)
+
+
+def tvlbm_velocity_set(velset: int):
+    cx, cy, w = np.zeros(36), np.zeros(36), np.zeros(36)
+    N = ctypes.c_int(0)
+    _check(_lib.tvlbm_velocity_set(velset, _dp(cx), _dp(cy), _dp(w), ctypes.byref(N)))
+    Q = velset
+    return cx[:Q].copy(), cy[:Q].copy(), w[:Q].copy(), N.value
+
+
+def tvlbm_stream_table(velset: int, dt: float):
+    sx, sy = np.zeros(36, dtype=np.int32), np.zeros(36, dtype=np.int32)
+    ax, ay = np.zeros(36), np.zeros(36)
+    _check(_lib.tvlbm_stream_table(velset, dt, sx.ctypes.data_as(_IP), sy.ctypes.data_as(_IP), _dp(ax), _dp(ay)))
+    Q = velset
+    return sx[:Q].copy(), sy[:Q].copy(), ax[:Q].copy(), ay[:Q].copy()
+
+
+def tvlbm_bytes_per_cell(ctx) -> float:
+    return float(_lib.tvlbm_bytes_per_cell(ctx))
+
+
+def tvlbm_last_error(ctx) -> str:
+    return _lib.tvlbm_last_error(ctx).decode()
+
+
+# ---- one context, torch-owned device memory and stream -------------------------------------
+
+class Simulation:
+    """A TVLBM context on the current CUDA device.  Device memory is a torch uint8 tensor held
+    by this object; work is queued on torch's current stream at construction (or `stream`)."""
+
+    def __init__(self, nx, ny, velset="D2Q16", tau=0.8, dt=1.0, walls=None, storage="fp32", rho0=1.0,
+                 form=None, stream=None, graphs=True):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("TVLBM needs a CUDA GPU")
+        self.nx, self.ny = int(nx), int(ny)
+        self.velset = VELSETS[velset] if isinstance(velset, str) else int(velset)
+        self.storage = STORAGES[storage] if isinstance(storage, str) else int(storage)
+        self.Q = self.velset
+        bc = None if walls is None else tuple(float(v) for v in walls)
+        nbytes = tvlbm_memory_bytes(self.nx, self.ny, self.velset, bc, self.storage)
+        self._mem = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        base = self._mem.data_ptr()
+        aligned = (base + 255) // 256 * 256
+        self.ctx = tvlbm_create_in(self.nx, self.ny, self.velset, float(tau), float(dt), bc, self.storage,
+                                   float(rho0), aligned, nbytes)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = s
+        tvlbm_set_stream(self.ctx, s.cuda_stream)
+        if form is not None:
+            tvlbm_set_form(self.ctx, FORMS[form] if isinstance(form, str) else int(form))
+        tvlbm_set_graphs(self.ctx, graphs)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            tvlbm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_form(self, form):
+        tvlbm_set_form(self.ctx, FORMS[form] if isinstance(form, str) else int(form))
+
+    def init_moments(self, rho, ux, uy, T):
+        tvlbm_init_moments(self.ctx, rho, ux, uy, T)
+
+    def step(self, n=1):
+        tvlbm_step(self.ctx, n)
+
+    def moments(self):
+        return tvlbm_moments(self.ctx, self.nx, self.ny)
+
+    def conserved_sums(self):
+        return tvlbm_conserved_sums(self.ctx)
+
+    def populations_f64(self):
+        out = np.empty((self.Q, self.ny, self.nx))
+        return tvlbm_get_populations_f64(self.ctx, out)
+
+    def set_populations_f64(self, f):
+        tvlbm_set_populations_f64(self.ctx, f)
+
+    def raw_populations(self):
+        out = np.empty((self.Q, self.ny, self.nx), dtype=STORAGE_NUMPY[self.storage])
+        return tvlbm_get_populations(self.ctx, out)
+
+    def set_raw_populations(self, host):
+        tvlbm_set_populations(self.ctx, host)
+
+    def bytes_per_cell(self):
+        return tvlbm_bytes_per_cell(self.ctx)

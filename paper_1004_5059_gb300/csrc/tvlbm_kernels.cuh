@@ -1,0 +1,251 @@
+// Device-side building blocks of the TVLBM sweep: launch parameters, storage codecs, the
+// per-cell collision (moments -> Hermite equilibrium -> BGK) and the kernel table that the
+// host API dispatches through.  Every kernel is a template on the 1-D node count N1
+// (3, 4, 6 -> D2Q9, D2Q16, D2Q36) and on the storage codec.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+namespace tvlbm {
+
+constexpr int kMaxN1 = 6;
+constexpr int kMaxQ = kMaxN1 * kMaxN1;
+// Ghost frame around the fluid: HX columns on each side (keeps the interior 16-byte aligned
+// for every storage type), HY rows above and below; FILL of them are ever read (|shift| <= 4).
+constexpr int HX = 8;
+constexpr int HY = 4;
+constexpr int FILL = 4;
+constexpr int kRedBlocks = 1024;  // fixed partial count of the FP64 reduction (deterministic)
+
+enum Storage { ST_FP64 = 0, ST_FP32 = 1, ST_BF16_DEV = 2, ST_FP16_DEV = 3, ST_FP32_DEV = 4 };
+enum Form { FORM_PLAIN = 0, FORM_TILED = 1 };
+
+// Everything a kernel needs, passed by value (lands in the constant bank).
+struct KParams {
+    // 1-D Gauss-Hermite nodes x_i, weights w_i, overlap fractions alpha_i of the shift x_i dt,
+    // integer shifts sh_i = floor(x_i dt), and He_a(x_i)/a! for a <= N.  Same table on both
+    // axes (tensor-product set, dx = dy).
+    float xf[kMaxN1], wf[kMaxN1], af[kMaxN1];
+    double xd[kMaxN1], wd[kMaxN1], ad[kMaxN1];
+    float Ef[kMaxN1][kMaxN1];
+    double Ed[kMaxN1][kMaxN1];
+    int sh[kMaxN1];
+    float omegaf, rho0f;
+    double omegad, rho0d;
+    int nx, ny;      // fluid cells
+    int pitch;       // elements per stored row (>= nx + 2 HX)
+    int rows;        // stored rows (ny + 2 HY)
+    long long plane; // elements per velocity plane (rows * pitch)
+    int walls;       // 0 periodic, 1 diffuse walls at y = -1/2 and y = ny - 1/2
+    // Walls: equilibrium f_eq_l(rho=1, u_w, T_w) of each wall (f-space) and the inverse of
+    // sum_{incoming} |c_y dt| f_eq_l.
+    float feqwf[2][kMaxQ];
+    double feqwd[2][kMaxQ];
+    float inv_denf[2];
+    double inv_dend[2];
+};
+
+template <class R> __device__ __forceinline__ R kx(const KParams& p, int i) {
+    if constexpr (std::is_same<R, double>::value) return p.xd[i]; else return p.xf[i];
+}
+template <class R> __device__ __forceinline__ R kw(const KParams& p, int i) {
+    if constexpr (std::is_same<R, double>::value) return p.wd[i]; else return p.wf[i];
+}
+template <class R> __device__ __forceinline__ R ka(const KParams& p, int i) {
+    if constexpr (std::is_same<R, double>::value) return p.ad[i]; else return p.af[i];
+}
+template <class R> __device__ __forceinline__ R kE(const KParams& p, int i, int a) {
+    if constexpr (std::is_same<R, double>::value) return p.Ed[i][a]; else return p.Ef[i][a];
+}
+template <class R> __device__ __forceinline__ R komega(const KParams& p) {
+    if constexpr (std::is_same<R, double>::value) return p.omegad; else return p.omegaf;
+}
+template <class R> __device__ __forceinline__ R krho0(const KParams& p) {
+    if constexpr (std::is_same<R, double>::value) return p.rho0d; else return p.rho0f;
+}
+template <class R> __device__ __forceinline__ R kfeqw(const KParams& p, int side, int l) {
+    if constexpr (std::is_same<R, double>::value) return p.feqwd[side][l]; else return p.feqwf[side][l];
+}
+template <class R> __device__ __forceinline__ R kinvden(const KParams& p, int side) {
+    if constexpr (std::is_same<R, double>::value) return p.inv_dend[side]; else return p.inv_denf[side];
+}
+
+// ---- storage codecs ----------------------------------------------------------------------
+// Full codecs store f_l; deviation codecs store d_l = f_l / w_l - rho0.  Sweep arithmetic runs
+// in "storage space" (the stored quantity), so the gather and the BGK update are linear in
+// what is loaded and stored; moments and equilibrium know which space they are in.
+struct CodecF64 {
+    using T = double; using R = double; static constexpr bool dev = false;
+    __device__ static R ld(const T* p) { return __ldg(p); }
+    __device__ static T enc(R v) { return v; }
+};
+struct CodecF32 {
+    using T = float; using R = float; static constexpr bool dev = false;
+    __device__ static R ld(const T* p) { return __ldg(p); }
+    __device__ static T enc(R v) { return v; }
+};
+struct CodecF32Dev {
+    using T = float; using R = float; static constexpr bool dev = true;
+    __device__ static R ld(const T* p) { return __ldg(p); }
+    __device__ static T enc(R v) { return v; }
+};
+struct CodecBF16Dev {
+    using T = __nv_bfloat16; using R = float; static constexpr bool dev = true;
+    __device__ static R ld(const T* p) { return __bfloat162float(__ldg(p)); }
+    __device__ static T enc(R v) { return __float2bfloat16_rn(v); }
+};
+struct CodecF16Dev {
+    using T = __half; using R = float; static constexpr bool dev = true;
+    __device__ static R ld(const T* p) { return __half2float(__ldg(p)); }
+    __device__ static T enc(R v) { return __float2half_rn(v); }
+};
+
+// Storage value -> f_l and back, in precision R (used off the hot path: init, moments,
+// reductions, walls).
+template <class C, class R>
+__device__ __forceinline__ R to_f(R v, R w, R rho0) { if constexpr (C::dev) return w * (rho0 + v); else return v; }
+template <class C, class R>
+__device__ __forceinline__ R from_f(R f, R w, R rho0) { if constexpr (C::dev) return f / w - rho0; else return f; }
+
+// ---- moments, equilibrium, BGK on one cell -----------------------------------------------
+// s[l], l = i + N1 j, holds the cell's (gathered) populations in storage space.
+// Moments (Sec. "The TVLBM model"): rho = sum f, rho u = sum c f, D rho T + rho u^2 = sum |c|^2 f
+// with D = 2.  In deviation space f = w (rho0 + d), and sum w = 1, sum w c = 0, sum w |c|^2 = D
+// (exact quadrature), so rho = rho0 + sum w d, rho u = sum w c d, and
+// T - 1 = ((sum w |c|^2 d - D sum w d)/rho - u^2)/D.
+template <int N1, bool DEV, class R>
+__device__ __forceinline__ void cell_moments(const R (&s)[N1 * N1], const KParams& p, R& rho, R& ux, R& uy, R& th) {
+    R m0 = 0, mx = 0, my = 0, me = 0;
+#pragma unroll
+    for (int j = 0; j < N1; ++j) {
+        R r = 0, rx = 0, rxx = 0;
+#pragma unroll
+        for (int i = 0; i < N1; ++i) {
+            const R v = DEV ? kw<R>(p, i) * s[i + N1 * j] : s[i + N1 * j];
+            const R xi = kx<R>(p, i);
+            r += v;
+            rx = fma(xi, v, rx);
+            rxx = fma(xi * xi, v, rxx);
+        }
+        const R yj = kx<R>(p, j);
+        const R wj = DEV ? kw<R>(p, j) : R(1);
+        m0 = fma(wj, r, m0);
+        mx = fma(wj, rx, mx);
+        my = fma(wj * yj, r, my);
+        me = fma(wj, fma(yj * yj, r, rxx), me);
+    }
+    if constexpr (DEV) {
+        rho = krho0<R>(p) + m0;
+        const R inv = R(1) / rho;
+        ux = mx * inv;
+        uy = my * inv;
+        th = R(0.5) * ((me - R(2) * m0) * inv - (ux * ux + uy * uy));
+    } else {
+        rho = m0;
+        const R inv = R(1) / rho;
+        ux = mx * inv;
+        uy = my * inv;
+        th = R(0.5) * (me * inv - (ux * ux + uy * uy)) - R(1);
+    }
+}
+
+// Hermite equilibrium (Sec. "The TVLBM model"; Appendix A) for a tensor-product set, in
+// separable form.  The Hermite coefficients of a Maxwellian factorise per axis:
+//   f_eq_l = rho w_i w_j sum_{a+b<=N} h_a(u_x) He_a(x_i)/a! * h_b(u_y) He_b(x_j)/b!,
+// h_0 = 1, h_1 = u, h_{n+1} = u h_n + n (T-1) h_{n-1}  (the Gaussian moments E[He_n(u+sqrt(T) Z)]).
+// With X_ia = h_a(u_x) E_ia (X_i0 = 1), P_jk = sum_{1<=b<=k} h_b(u_y) E_jb:
+//   sum_{a+b<=N} X_ia Y_jb = 1 + phi_ij,  phi_ij = sum_{a>=1} X_ia + sum_{a<N} X_ia P_j,N-a.
+// Storage-space equilibrium: full f_eq = w rho (1 + phi); deviation d_eq = (rho - rho0) + rho phi.
+template <int N1, bool DEV, class R>
+__device__ __forceinline__ void cell_equilibrium(const KParams& p, R rho, R ux, R uy, R th, R (&eq)[N1 * N1]) {
+    constexpr int N = N1 - 1;
+    R hx[N + 1], hy[N + 1];
+    hx[0] = R(1); hy[0] = R(1);
+    hx[1] = ux;   hy[1] = uy;
+#pragma unroll
+    for (int n = 1; n < N; ++n) {
+        hx[n + 1] = fma(ux, hx[n], R(n) * th * hx[n - 1]);
+        hy[n + 1] = fma(uy, hy[n], R(n) * th * hy[n - 1]);
+    }
+    R X[N1][N], SX[N1], P[N1][N + 1];
+#pragma unroll
+    for (int i = 0; i < N1; ++i) {
+        R sx = 0, acc = 0;
+#pragma unroll
+        for (int a = 1; a <= N; ++a) {
+            const R v = hx[a] * kE<R>(p, i, a);
+            if (a < N) X[i][a] = v;
+            sx += v;
+            acc = fma(hy[a], kE<R>(p, i, a), acc);
+            P[i][a] = acc;
+        }
+        SX[i] = sx;
+    }
+    const R drho = DEV ? rho - krho0<R>(p) : R(0);
+#pragma unroll
+    for (int j = 0; j < N1; ++j) {
+#pragma unroll
+        for (int i = 0; i < N1; ++i) {
+            R phi = SX[i] + P[j][N];  // a = 0 term: X_i0 = 1
+#pragma unroll
+            for (int a = 1; a < N; ++a) phi = fma(X[i][a], P[j][N - a], phi);
+            if constexpr (DEV) eq[i + N1 * j] = fma(rho, phi, drho);
+            else eq[i + N1 * j] = (kw<R>(p, i) * kw<R>(p, j) * rho) * (R(1) + phi);
+        }
+    }
+}
+
+// Moments -> equilibrium -> BGK relaxation s* = s + (dt/tau)(s_eq - s), in place.
+template <int N1, bool DEV, class R>
+__device__ __forceinline__ void cell_collide(R (&s)[N1 * N1], const KParams& p) {
+    R rho, ux, uy, th;
+    cell_moments<N1, DEV, R>(s, p, rho, ux, uy, th);
+    R eq[N1 * N1];
+    cell_equilibrium<N1, DEV, R>(p, rho, ux, uy, th, eq);
+    const R om = komega<R>(p);
+#pragma unroll
+    for (int l = 0; l < N1 * N1; ++l) s[l] = fma(om, eq[l] - s[l], s[l]);
+}
+
+// Padded storage index of fluid cell (x, y) in velocity plane l (x, y may lie in the frame).
+__device__ __forceinline__ long long sidx(const KParams& p, int l, int x, int y) {
+    return (long long)l * p.plane + (long long)(y + HY) * p.pitch + (x + HX);
+}
+
+// Store v at fluid cell (x, y) and at every periodic image of it inside the read frame
+// (x in [-FILL, nx+FILL); y likewise when periodic in y).
+template <class T>
+__device__ __forceinline__ void store_with_images(T* f, const KParams& p, long long lbase, int x, int y, T v) {
+    const int x0 = x - p.nx * ((x + FILL) / p.nx);
+    if (p.walls) {
+        for (int xx = x0; xx < p.nx + FILL; xx += p.nx) f[lbase + (long long)(y + HY) * p.pitch + (xx + HX)] = v;
+    } else {
+        const int y0 = y - p.ny * ((y + FILL) / p.ny);
+        for (int yy = y0; yy < p.ny + FILL; yy += p.ny)
+            for (int xx = x0; xx < p.nx + FILL; xx += p.nx) f[lbase + (long long)(yy + HY) * p.pitch + (xx + HX)] = v;
+    }
+}
+
+// ---- kernel table (one per N1, defined in tvlbm_kernels_q*.cu) ----------------------------
+struct KernelTable {
+    cudaError_t (*sweep)(int storage, int form, const void* fin, void* fout, const KParams& p, cudaStream_t s);
+    cudaError_t (*init)(int storage, const double* fields, void* f, const KParams& p, cudaStream_t s);
+    cudaError_t (*moments)(int storage, const void* f, double* out4, const KParams& p, cudaStream_t s);
+    cudaError_t (*reduce)(int storage, const void* f, double* partials, double* out5, const KParams& p, cudaStream_t s);
+    cudaError_t (*wall)(int storage, void* f, const KParams& p, cudaStream_t s);
+    cudaError_t (*halo)(int storage, void* f, const KParams& p, cudaStream_t s);
+    cudaError_t (*decode_plane)(int storage, const void* f, int l, double* out, const KParams& p, cudaStream_t s);
+    cudaError_t (*encode_plane)(int storage, void* f, int l, const double* in, const KParams& p, cudaStream_t s);
+    int (*tiled_available)(int storage);
+};
+
+const KernelTable* kernel_table_q3();
+const KernelTable* kernel_table_q4();
+const KernelTable* kernel_table_q6();
+
+}  // namespace tvlbm

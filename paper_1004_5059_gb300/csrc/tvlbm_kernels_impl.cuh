@@ -1,0 +1,369 @@
+// Kernel bodies, instantiated per velocity set by tvlbm_kernels_q{3,4,6}.cu.
+#pragma once
+
+#include "tvlbm_kernels.cuh"
+#include "tvlbm_tiled.cuh"
+
+namespace tvlbm {
+
+// =============================================================================================
+// Plain sweep: one thread per fluid cell, gathers straight from global memory.
+// For velocity l = (i, j) with shift x_i dt = sh_i + a_i (and likewise along y), destination
+// (x, y) pulls from the four cells it is overlapped by:
+//   s~ = (1-a_y)[(1-a_x) f(x-sh_i, y-sh_j) + a_x f(x-sh_i-1, y-sh_j)]
+//      +    a_y [(1-a_x) f(x-sh_i, y-sh_j-1) + a_x f(x-sh_i-1, y-sh_j-1)]
+// (the area of the shifted source square inside the destination square).  Periodic images
+// and wall ghost rows live in the stored frame, so no index wraps here.
+// =============================================================================================
+template <int N1, class C>
+__global__ void __launch_bounds__(256) sweep_plain_kernel(const typename C::T* __restrict__ fin,
+                                                          typename C::T* __restrict__ fout, const KParams p) {
+    using R = typename C::R;
+    using T = typename C::T;
+    constexpr int Q = N1 * N1;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= p.nx || y >= p.ny) return;
+    R s[Q];
+#pragma unroll
+    for (int j = 0; j < N1; ++j) {
+        const R ay = ka<R>(p, j);
+        const int ys = y + HY - p.sh[j];
+#pragma unroll
+        for (int i = 0; i < N1; ++i) {
+            const R ax = ka<R>(p, i);
+            const int xs = x + HX - p.sh[i];
+            const T* b = fin + (long long)(i + N1 * j) * p.plane + (long long)ys * p.pitch + xs;
+            const R v00 = C::ld(b), v01 = C::ld(b - 1);
+            const R v10 = C::ld(b - p.pitch), v11 = C::ld(b - p.pitch - 1);
+            const R r0 = fma(ax, v01 - v00, v00);
+            const R r1 = fma(ax, v11 - v10, v10);
+            s[i + N1 * j] = fma(ay, r1 - r0, r0);
+        }
+    }
+    cell_collide<N1, C::dev, R>(s, p);
+#pragma unroll
+    for (int l = 0; l < Q; ++l) store_with_images(fout, p, (long long)l * p.plane, x, y, C::enc(s[l]));
+}
+
+// =============================================================================================
+// Initialisation to the equilibrium of host-given FP64 fields (FP64 arithmetic).
+// fields = [rho | ux | uy | T], each [ny][nx].
+// =============================================================================================
+template <int N1, class C>
+__global__ void init_kernel(const double* __restrict__ fields, typename C::T* __restrict__ f, const KParams p) {
+    constexpr int Q = N1 * N1;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= p.nx || y >= p.ny) return;
+    const long long c = (long long)y * p.nx + x, n = (long long)p.nx * p.ny;
+    const double rho = fields[c], ux = fields[n + c], uy = fields[2 * n + c], T = fields[3 * n + c];
+    double eq[Q];
+    cell_equilibrium<N1, C::dev, double>(p, rho, ux, uy, T - 1.0, eq);
+#pragma unroll
+    for (int l = 0; l < Q; ++l) store_with_images(f, p, (long long)l * p.plane, x, y, C::enc((typename C::R)eq[l]));
+}
+
+// =============================================================================================
+// Macroscopic fields of the stored state, FP64.  out4 = [rho | ux | uy | T], each [ny][nx].
+// =============================================================================================
+template <int N1, class C>
+__global__ void moments_kernel(const typename C::T* __restrict__ f, double* __restrict__ out4, const KParams p) {
+    constexpr int Q = N1 * N1;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= p.nx || y >= p.ny) return;
+    double s[Q];
+#pragma unroll
+    for (int l = 0; l < Q; ++l) s[l] = (double)C::ld(f + sidx(p, l, x, y));
+    double rho, ux, uy, th;
+    cell_moments<N1, C::dev, double>(s, p, rho, ux, uy, th);
+    const long long c = (long long)y * p.nx + x, n = (long long)p.nx * p.ny;
+    out4[c] = rho;
+    out4[n + c] = ux;
+    out4[2 * n + c] = uy;
+    out4[3 * n + c] = 1.0 + th;
+}
+
+// =============================================================================================
+// FP64 conserved sums, pass 1: a fixed grid of kRedBlocks blocks, each summing the cells
+// c = blockIdx.x + k*kRedBlocks (grid stride) in a fixed order, then a fixed-shape shuffle tree.
+// Partials [kRedBlocks][5] = (M, Px, Py, E, non-finite count).
+// =============================================================================================
+static __device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int N1, class C>
+__global__ void __launch_bounds__(256) reduce_kernel(const typename C::T* __restrict__ f, double* __restrict__ partials,
+                                                     const KParams p) {
+    constexpr int Q = N1 * N1;
+    double acc[5] = {0, 0, 0, 0, 0};
+    const long long ncell = (long long)p.nx * p.ny;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(c / p.nx), x = (int)(c - (long long)y * p.nx);
+#pragma unroll
+        for (int j = 0; j < N1; ++j) {
+            double r = 0, rx = 0, rxx = 0;
+#pragma unroll
+            for (int i = 0; i < N1; ++i) {
+                const double v = (double)C::ld(f + sidx(p, i + N1 * j, x, y));
+                acc[4] += isfinite(v) ? 0.0 : 1.0;
+                const double fv = to_f<C, double>(v, p.wd[i] * p.wd[j], p.rho0d);
+                r += fv;
+                rx += p.xd[i] * fv;
+                rxx += p.xd[i] * p.xd[i] * fv;
+            }
+            acc[0] += r;
+            acc[1] += rx;
+            acc[2] += p.xd[j] * r;
+            acc[3] += 0.5 * (rxx + p.xd[j] * p.xd[j] * r);
+        }
+    }
+    __shared__ double sh[5][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const double v = warp_sum(acc[k]);
+        if (lane == 0) sh[k][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 5) {
+        double t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[threadIdx.x][w];
+        partials[(long long)blockIdx.x * 5 + threadIdx.x] = t;
+    }
+}
+
+// Pass 2: one block folds the kRedBlocks partials in a fixed order.
+static __global__ void __launch_bounds__(256) reduce_final_kernel(const double* __restrict__ partials, double* __restrict__ out5) {
+    __shared__ double sh[5][8];
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < kRedBlocks; b += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) acc[k] += partials[(long long)b * 5 + k];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const double v = warp_sum(acc[k]);
+        if (lane == 0) sh[k][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 5) {
+        double t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[threadIdx.x][w];
+        out5[threadIdx.x] = t;
+    }
+}
+
+// =============================================================================================
+// Diffuse-reflection walls through ghost rows (Eq. IMPOSITION).  One thread per (column, wall).
+// M_out(x): what the gather would move into the rows beyond the wall for the outgoing
+// velocities (c.n > 0, n the wall's outward normal), counting only fluid sources.  Every
+// incoming ghost row of column x then holds A(x) f_eq_l(1, u_w, T_w) with
+// A = M_out / sum_in |c_y dt| f_eq_l, so a uniform ghost column re-emits exactly M_out.
+// Columns of the x-frame are filled too (periodic images).
+// =============================================================================================
+template <int N1, class C>
+__global__ void wall_kernel(typename C::T* __restrict__ f, const KParams p) {
+    using R = typename C::R;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int ncol = p.nx + 2 * FILL;
+    if (t >= 2 * ncol) return;
+    const int side = t / ncol;          // 0: wall at y = -1/2, 1: wall at y = ny - 1/2
+    const int xo = t - side * ncol - FILL;  // output column, in [-FILL, nx + FILL)
+    const int x = ((xo % p.nx) + p.nx) % p.nx;
+    const R rho0 = krho0<R>(p);
+    R mout = 0;
+#pragma unroll
+    for (int j = 0; j < N1; ++j) {
+        const R cyj = kx<R>(p, j);
+        const bool outgoing = side == 0 ? cyj < R(0) : cyj > R(0);
+        if (!outgoing) continue;
+        const R ay = ka<R>(p, j);
+#pragma unroll
+        for (int i = 0; i < N1; ++i) {
+            const R ax = ka<R>(p, i), w = kw<R>(p, i) * kw<R>(p, j);
+            const int l = i + N1 * j;
+            for (int d = 1; d <= HY; ++d) {
+                const int yd = side == 0 ? -d : p.ny - 1 + d;
+                R acc = 0;
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int ys = yd - p.sh[j] - q;
+                    if (ys < 0 || ys >= p.ny) continue;  // beyond the wall: no mass
+                    const R wy = q ? ay : R(1) - ay;
+#pragma unroll
+                    for (int pp = 0; pp < 2; ++pp) {
+                        const int xs = x - p.sh[i] - pp;
+                        const R wx = pp ? ax : R(1) - ax;
+                        acc += wx * wy * to_f<C, R>(C::ld(f + sidx(p, l, xs, ys)), w, rho0);
+                    }
+                }
+                mout += acc;
+            }
+        }
+    }
+    const R A = mout * kinvden<R>(p, side);
+#pragma unroll
+    for (int j = 0; j < N1; ++j) {
+        const R cyj = kx<R>(p, j);
+        const bool incoming = side == 0 ? cyj > R(0) : cyj < R(0);
+        if (!incoming) continue;
+#pragma unroll
+        for (int i = 0; i < N1; ++i) {
+            const int l = i + N1 * j;
+            const R w = kw<R>(p, i) * kw<R>(p, j);
+            const typename C::T v = C::enc(from_f<C, R>(A * kfeqw<R>(p, side, l), w, rho0));
+            for (int d = 1; d <= HY; ++d) {
+                const int yd = side == 0 ? -d : p.ny - 1 + d;
+                f[sidx(p, l, xo, yd)] = v;
+            }
+        }
+    }
+}
+
+// =============================================================================================
+// Refresh the periodic frame from the interior (after raw population uploads).
+// =============================================================================================
+template <class T>
+__global__ void halo_kernel(T* __restrict__ f, const KParams p, int Q) {
+    const int fx = p.nx + 2 * FILL, fy = p.walls ? p.ny : p.ny + 2 * FILL;
+    const long long per = (long long)fx * fy;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < per * Q;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int l = (int)(t / per);
+        const long long r = t - (long long)l * per;
+        const int yy = (int)(r / fx) - (p.walls ? 0 : FILL);
+        const int xx = (int)(r % fx) - FILL;
+        if (xx >= 0 && xx < p.nx && yy >= 0 && yy < p.ny) continue;
+        const int x = ((xx % p.nx) + p.nx) % p.nx, y = ((yy % p.ny) + p.ny) % p.ny;
+        f[sidx(p, l, xx, yy)] = f[sidx(p, l, x, y)];
+    }
+}
+
+// Decode one velocity plane to FP64 f_l (packed [ny][nx]) / encode FP64 f_l into storage.
+template <class C>
+__global__ void decode_plane_kernel(const typename C::T* __restrict__ f, int l, int n1, double* __restrict__ out,
+                                    const KParams p) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= p.nx || y >= p.ny) return;
+    const double w = p.wd[l % n1] * p.wd[l / n1];
+    out[(long long)y * p.nx + x] = to_f<C, double>((double)C::ld(f + sidx(p, l, x, y)), w, p.rho0d);
+}
+template <class C>
+__global__ void encode_plane_kernel(typename C::T* __restrict__ f, int l, int n1, const double* __restrict__ in,
+                                    const KParams p) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= p.nx || y >= p.ny) return;
+    const double w = p.wd[l % n1] * p.wd[l / n1];
+    f[sidx(p, l, x, y)] = C::enc((typename C::R)from_f<C, double>(in[(long long)y * p.nx + x], w, p.rho0d));
+}
+
+// =============================================================================================
+// Host-side launchers for one N1.
+// =============================================================================================
+template <int N1>
+struct Launch {
+    static dim3 grid2d(const KParams& p, dim3 b) { return dim3((p.nx + b.x - 1) / b.x, (p.ny + b.y - 1) / b.y); }
+
+    template <class C>
+    static cudaError_t sweep_c(int form, const void* fin, void* fout, const KParams& p, cudaStream_t s) {
+        using T = typename C::T;
+        if (form == FORM_TILED) return tiled_sweep<N1, C>((const T*)fin, (T*)fout, p, s);
+        const dim3 b(32, 8);
+        sweep_plain_kernel<N1, C><<<grid2d(p, b), b, 0, s>>>((const T*)fin, (T*)fout, p);
+        return cudaGetLastError();
+    }
+    template <class C>
+    static cudaError_t init_c(const double* fields, void* f, const KParams& p, cudaStream_t s) {
+        const dim3 b(32, 8);
+        init_kernel<N1, C><<<grid2d(p, b), b, 0, s>>>(fields, (typename C::T*)f, p);
+        return cudaGetLastError();
+    }
+    template <class C>
+    static cudaError_t moments_c(const void* f, double* out4, const KParams& p, cudaStream_t s) {
+        const dim3 b(32, 8);
+        moments_kernel<N1, C><<<grid2d(p, b), b, 0, s>>>((const typename C::T*)f, out4, p);
+        return cudaGetLastError();
+    }
+    template <class C>
+    static cudaError_t reduce_c(const void* f, double* partials, double* out5, const KParams& p, cudaStream_t s) {
+        reduce_kernel<N1, C><<<kRedBlocks, 256, 0, s>>>((const typename C::T*)f, partials, p);
+        reduce_final_kernel<<<1, 256, 0, s>>>(partials, out5);
+        return cudaGetLastError();
+    }
+    template <class C>
+    static cudaError_t wall_c(void* f, const KParams& p, cudaStream_t s) {
+        const int n = 2 * (p.nx + 2 * FILL);
+        wall_kernel<N1, C><<<(n + 127) / 128, 128, 0, s>>>((typename C::T*)f, p);
+        return cudaGetLastError();
+    }
+    template <class C>
+    static cudaError_t halo_c(void* f, const KParams& p, cudaStream_t s) {
+        halo_kernel<typename C::T><<<1024, 256, 0, s>>>((typename C::T*)f, p, N1 * N1);
+        return cudaGetLastError();
+    }
+    template <class C>
+    static cudaError_t decode_c(const void* f, int l, double* out, const KParams& p, cudaStream_t s) {
+        const dim3 b(32, 8);
+        decode_plane_kernel<C><<<grid2d(p, b), b, 0, s>>>((const typename C::T*)f, l, N1, out, p);
+        return cudaGetLastError();
+    }
+    template <class C>
+    static cudaError_t encode_c(void* f, int l, const double* in, const KParams& p, cudaStream_t s) {
+        const dim3 b(32, 8);
+        encode_plane_kernel<C><<<grid2d(p, b), b, 0, s>>>((typename C::T*)f, l, N1, in, p);
+        return cudaGetLastError();
+    }
+
+#define TVLBM_DISPATCH(call, args)                              \
+    switch (storage) {                                          \
+        case ST_FP64: return call<CodecF64> args;               \
+        case ST_FP32: return call<CodecF32> args;               \
+        case ST_BF16_DEV: return call<CodecBF16Dev> args;       \
+        case ST_FP16_DEV: return call<CodecF16Dev> args;        \
+        case ST_FP32_DEV: return call<CodecF32Dev> args;        \
+        default: return cudaErrorInvalidValue;                  \
+    }
+
+    static cudaError_t sweep(int storage, int form, const void* fin, void* fout, const KParams& p, cudaStream_t s) {
+        switch (storage) {
+            case ST_FP64: return sweep_c<CodecF64>(form, fin, fout, p, s);
+            case ST_FP32: return sweep_c<CodecF32>(form, fin, fout, p, s);
+            case ST_BF16_DEV: return sweep_c<CodecBF16Dev>(form, fin, fout, p, s);
+            case ST_FP16_DEV: return sweep_c<CodecF16Dev>(form, fin, fout, p, s);
+            case ST_FP32_DEV: return sweep_c<CodecF32Dev>(form, fin, fout, p, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    static cudaError_t init(int storage, const double* fields, void* f, const KParams& p, cudaStream_t s) {
+        TVLBM_DISPATCH(init_c, (fields, f, p, s))
+    }
+    static cudaError_t moments(int storage, const void* f, double* out4, const KParams& p, cudaStream_t s) {
+        TVLBM_DISPATCH(moments_c, (f, out4, p, s))
+    }
+    static cudaError_t reduce(int storage, const void* f, double* partials, double* out5, const KParams& p, cudaStream_t s) {
+        TVLBM_DISPATCH(reduce_c, (f, partials, out5, p, s))
+    }
+    static cudaError_t wall(int storage, void* f, const KParams& p, cudaStream_t s) { TVLBM_DISPATCH(wall_c, (f, p, s)) }
+    static cudaError_t halo(int storage, void* f, const KParams& p, cudaStream_t s) { TVLBM_DISPATCH(halo_c, (f, p, s)) }
+    static cudaError_t decode(int storage, const void* f, int l, double* out, const KParams& p, cudaStream_t s) {
+        TVLBM_DISPATCH(decode_c, (f, l, out, p, s))
+    }
+    static cudaError_t encode(int storage, void* f, int l, const double* in, const KParams& p, cudaStream_t s) {
+        TVLBM_DISPATCH(encode_c, (f, l, in, p, s))
+    }
+    static int tiled_available(int storage) { return tiled_supported<N1>(storage); }
+#undef TVLBM_DISPATCH
+
+    static const KernelTable* table() {
+        static const KernelTable t = {&sweep, &init, &moments, &reduce, &wall, &halo, &decode, &encode, &tiled_available};
+        return &t;
+    }
+};
+
+}  // namespace tvlbm
