@@ -1,5 +1,7 @@
 // Host side of the TVLBM library: velocity sets, streaming tables, context lifetime, argument
 // validation, memory layout and kernel launches behind the C ABI of include/tvlbm.h.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdarg.h>
@@ -159,7 +161,7 @@ struct Layout {
     int pitch, rows;
     long long plane;
     size_t buf_bytes, mom_bytes, part_bytes, total;
-    size_t off_f[2], off_mom, off_part, off_sums;
+    size_t off_f[2], off_mom, off_part, off_sums, off_status;
 };
 
 Layout make_layout(int nx, int ny, int Q, int storage) {
@@ -177,6 +179,7 @@ Layout make_layout(int nx, int ny, int Q, int storage) {
     L.off_mom = 2 * L.buf_bytes;
     L.off_part = L.off_mom + L.mom_bytes;
     L.off_sums = L.off_part + L.part_bytes;
+    L.off_status = L.off_sums + 128;
     L.total = L.off_sums + 256;
     return L;
 }
@@ -209,6 +212,8 @@ struct tvlbm_ctx {
     cudaStream_t stream;
     cudaStream_t capture_stream;
     cudaGraphExec_t graph[2];
+    int have_tmap;
+    alignas(64) CUtensorMap tmap[2];  // TMA descriptors of the two population buffers
     char err[512];
 };
 
@@ -340,7 +345,63 @@ cudaError_t launch_step(tvlbm_ctx* c, int from, cudaStream_t s) {
         const cudaError_t e = c->kt->wall(c->storage, fin, c->kp, s);
         if (e != cudaSuccess) return e;
     }
-    return c->kt->sweep(c->storage, c->form, fin, fout, c->kp, s);
+    return c->kt->sweep(c->storage, c->form, fin, fout, &c->tmap[from], c->kp, s);
+}
+
+// TMA descriptors for the tiled form: a 3-D view [Q][rows][pitch] of each population buffer,
+// box = the tile's source window (BX x BY x 1 elements), no swizzle, zero fill out of bounds.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+bool make_tensor_maps(tvlbm_ctx* c) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc || !c->kt->tiled_available(c->storage)) return false;
+    int bx = 0, by = 0;
+    c->kt->tiled_box(c->storage, &bx, &by);
+    CUtensorMapDataType dt;
+    switch (c->storage) {
+        case TVLBM_FP64: dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT64; break;
+        case TVLBM_BF16_DEV: dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16; break;
+        case TVLBM_FP16_DEV: dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT16; break;
+        default: dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32; break;
+    }
+    const size_t es = elem_size(c->storage);
+    const cuuint64_t dims[3] = {(cuuint64_t)c->L.pitch, (cuuint64_t)c->L.rows, (cuuint64_t)c->Q};
+    const cuuint64_t strides[2] = {(cuuint64_t)c->L.pitch * es, (cuuint64_t)c->L.plane * es};
+    const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    for (int b = 0; b < 2; ++b) {
+        const CUresult r = enc(&c->tmap[b], dt, 3, dptr(c, c->L.off_f[b]), dims, strides, box, estr,
+                               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return false;
+    }
+    return true;
+}
+
+// Read and clear the device status word; a set bit means a bounded device wait gave up.
+int check_status(tvlbm_ctx* c) {
+    int st = 0;
+    int* d = (int*)dptr(c, c->L.off_status);
+    TVLBM_CUDA(c, cudaMemcpyAsync(&st, d, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "cudaMemcpyAsync status");
+    TVLBM_CUDA(c, cudaStreamSynchronize(c->stream), "status synchronize");
+    if (st) {
+        cudaMemsetAsync(d, 0, sizeof(int), c->stream);
+        cudaStreamSynchronize(c->stream);
+        return fail(c, TVLBM_ETIMEOUT, "a device-side wait for a TMA load timed out (status %d)", st);
+    }
+    return TVLBM_OK;
 }
 
 int build_graph(tvlbm_ctx* c, int parity) {
@@ -389,7 +450,6 @@ int create_common(int nx, int ny, int velset, double tau, double dt, const tvlbm
     c->L = make_layout(nx, ny, c->Q, storage);
     c->kt = table_for(c->n1);
     fill_params(c);
-    if (c->kt->tiled_available(storage)) c->form = FORM_TILED;
     cudaGetDevice(&c->device);
     if (device_memory) {
         if (bytes < c->L.total) { delete c; return TVLBM_ENOMEM; }
@@ -408,6 +468,9 @@ int create_common(int nx, int ny, int velset, double tau, double dt, const tvlbm
         return TVLBM_ECUDA;
     }
     c->stream = nullptr;
+    c->kp.status = (int*)dptr(c, c->L.off_status);
+    c->have_tmap = make_tensor_maps(c) ? 1 : 0;
+    if (c->have_tmap) c->form = FORM_TILED;
     // Both buffers (frame included) start as the rest equilibrium f = rho0 w: zero the memory,
     // then initialise through the same path as tvlbm_init_moments.
     e = cudaMemsetAsync(c->mem, 0, c->L.total, c->stream);
@@ -494,8 +557,8 @@ int tvlbm_set_stream(tvlbm_ctx* c, void* stream) {
 int tvlbm_set_form(tvlbm_ctx* c, int form) {
     if (!c) return TVLBM_EINVAL;
     if (form != FORM_PLAIN && form != FORM_TILED) return fail(c, TVLBM_EINVAL, "unknown form %d", form);
-    if (form == FORM_TILED && !c->kt->tiled_available(c->storage))
-        return fail(c, TVLBM_EINVAL, "tiled form not available for this storage");
+    if (form == FORM_TILED && !c->have_tmap)
+        return fail(c, TVLBM_EINVAL, "tiled form not available (no TMA descriptor for this storage/driver)");
     if (form != c->form) drop_graphs(c);
     c->form = form;
     return TVLBM_OK;
@@ -555,7 +618,7 @@ int tvlbm_moments(tvlbm_ctx* c, double* rho, double* ux, double* uy, double* T) 
             TVLBM_CUDA(c, cudaMemcpyAsync(dst[k], d + k * n, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
                        "cudaMemcpyAsync moments");
     TVLBM_CUDA(c, cudaStreamSynchronize(c->stream), "moments synchronize");
-    return TVLBM_OK;
+    return check_status(c);
 }
 
 int tvlbm_conserved_sums(tvlbm_ctx* c, double out[5]) {
@@ -566,7 +629,7 @@ int tvlbm_conserved_sums(tvlbm_ctx* c, double out[5]) {
     TVLBM_CUDA(c, c->kt->reduce(c->storage, fcur(c), part, sums, c->kp, c->stream), "reduction kernels");
     TVLBM_CUDA(c, cudaMemcpyAsync(out, sums, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "cudaMemcpyAsync sums");
     TVLBM_CUDA(c, cudaStreamSynchronize(c->stream), "sums synchronize");
-    return TVLBM_OK;
+    return check_status(c);
 }
 
 size_t tvlbm_population_bytes(const tvlbm_ctx* c) {
@@ -586,7 +649,7 @@ int tvlbm_get_populations(tvlbm_ctx* c, void* host, size_t bytes) {
                    "cudaMemcpy2DAsync");
     }
     TVLBM_CUDA(c, cudaStreamSynchronize(c->stream), "get_populations synchronize");
-    return TVLBM_OK;
+    return check_status(c);
 }
 
 int tvlbm_set_populations(tvlbm_ctx* c, const void* host, size_t bytes) {

@@ -48,6 +48,8 @@ struct KParams {
     double feqwd[2][kMaxQ];
     float inv_denf[2];
     double inv_dend[2];
+    // Device status word: bit 0 is set by a kernel whose bounded wait gave up.
+    int* status;
 };
 
 template <class R> __device__ __forceinline__ R kx(const KParams& p, int i) {
@@ -233,7 +235,9 @@ __device__ __forceinline__ void store_with_images(T* f, const KParams& p, long l
 
 // ---- kernel table (one per N1, defined in tvlbm_kernels_q*.cu) ----------------------------
 struct KernelTable {
-    cudaError_t (*sweep)(int storage, int form, const void* fin, void* fout, const KParams& p, cudaStream_t s);
+    // tmap: TMA descriptor (CUtensorMap) of fin, used by the tiled form
+    cudaError_t (*sweep)(int storage, int form, const void* fin, void* fout, const void* tmap, const KParams& p,
+                         cudaStream_t s);
     cudaError_t (*init)(int storage, const double* fields, void* f, const KParams& p, cudaStream_t s);
     cudaError_t (*moments)(int storage, const void* f, double* out4, const KParams& p, cudaStream_t s);
     cudaError_t (*reduce)(int storage, const void* f, double* partials, double* out5, const KParams& p, cudaStream_t s);
@@ -242,6 +246,7 @@ struct KernelTable {
     cudaError_t (*decode_plane)(int storage, const void* f, int l, double* out, const KParams& p, cudaStream_t s);
     cudaError_t (*encode_plane)(int storage, void* f, int l, const double* in, const KParams& p, cudaStream_t s);
     int (*tiled_available)(int storage);
+    void (*tiled_box)(int storage, int* bx, int* by);  // TMA box (elements) of the tiled form
 };
 
 const KernelTable* kernel_table_q3();

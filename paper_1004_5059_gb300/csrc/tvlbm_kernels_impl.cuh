@@ -42,8 +42,9 @@ __global__ void __launch_bounds__(256) sweep_plain_kernel(const typename C::T* _
         }
     }
     cell_collide<N1, C::dev, R>(s, p);
+    const bool edge = x < FILL || x >= p.nx - FILL || (!p.walls && (y < FILL || y >= p.ny - FILL));
 #pragma unroll
-    for (int l = 0; l < Q; ++l) store_with_images(fout, p, (long long)l * p.plane, x, y, C::enc(s[l]));
+    for (int l = 0; l < Q; ++l) store_cell(fout, p, (long long)l * p.plane, x, y, edge, C::enc(s[l]));
 }
 
 // =============================================================================================
@@ -271,9 +272,10 @@ struct Launch {
     static dim3 grid2d(const KParams& p, dim3 b) { return dim3((p.nx + b.x - 1) / b.x, (p.ny + b.y - 1) / b.y); }
 
     template <class C>
-    static cudaError_t sweep_c(int form, const void* fin, void* fout, const KParams& p, cudaStream_t s) {
+    static cudaError_t sweep_c(int form, const void* fin, void* fout, const void* tmap, const KParams& p,
+                               cudaStream_t s) {
         using T = typename C::T;
-        if (form == FORM_TILED) return tiled_sweep<N1, C>((const T*)fin, (T*)fout, p, s);
+        if (form == FORM_TILED) return tiled_sweep<N1, C>((const CUtensorMap*)tmap, (T*)fout, p, s);
         const dim3 b(32, 8);
         sweep_plain_kernel<N1, C><<<grid2d(p, b), b, 0, s>>>((const T*)fin, (T*)fout, p);
         return cudaGetLastError();
@@ -330,15 +332,9 @@ struct Launch {
         default: return cudaErrorInvalidValue;                  \
     }
 
-    static cudaError_t sweep(int storage, int form, const void* fin, void* fout, const KParams& p, cudaStream_t s) {
-        switch (storage) {
-            case ST_FP64: return sweep_c<CodecF64>(form, fin, fout, p, s);
-            case ST_FP32: return sweep_c<CodecF32>(form, fin, fout, p, s);
-            case ST_BF16_DEV: return sweep_c<CodecBF16Dev>(form, fin, fout, p, s);
-            case ST_FP16_DEV: return sweep_c<CodecF16Dev>(form, fin, fout, p, s);
-            case ST_FP32_DEV: return sweep_c<CodecF32Dev>(form, fin, fout, p, s);
-            default: return cudaErrorInvalidValue;
-        }
+    static cudaError_t sweep(int storage, int form, const void* fin, void* fout, const void* tmap, const KParams& p,
+                             cudaStream_t s) {
+        TVLBM_DISPATCH(sweep_c, (form, fin, fout, tmap, p, s))
     }
     static cudaError_t init(int storage, const double* fields, void* f, const KParams& p, cudaStream_t s) {
         TVLBM_DISPATCH(init_c, (fields, f, p, s))
@@ -358,10 +354,20 @@ struct Launch {
         TVLBM_DISPATCH(encode_c, (f, l, in, p, s))
     }
     static int tiled_available(int storage) { return tiled_supported<N1>(storage); }
+    static void box(int storage, int* bx, int* by) {
+        switch (storage) {
+            case ST_FP64: tiled_box<N1, CodecF64>(bx, by); break;
+            case ST_FP32: tiled_box<N1, CodecF32>(bx, by); break;
+            case ST_BF16_DEV: tiled_box<N1, CodecBF16Dev>(bx, by); break;
+            case ST_FP16_DEV: tiled_box<N1, CodecF16Dev>(bx, by); break;
+            default: tiled_box<N1, CodecF32Dev>(bx, by); break;
+        }
+    }
 #undef TVLBM_DISPATCH
 
     static const KernelTable* table() {
-        static const KernelTable t = {&sweep, &init, &moments, &reduce, &wall, &halo, &decode, &encode, &tiled_available};
+        static const KernelTable t = {&sweep, &init, &moments, &reduce, &wall, &halo, &decode, &encode, &tiled_available,
+                                      &box};
         return &t;
     }
 };

@@ -14,9 +14,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 @pytest.fixture(scope="module")
 def tv():
-    from paper_1004_5059_gb300 import build
-    build.build()
-    import paper_1004_5059_gb300 as tv
+    import paper_1004_5059_gb300 as tv  # built by conftest at session start
     return tv
 
 
