@@ -158,7 +158,7 @@ size_t elem_size(int storage) {
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 struct Layout {
-    int pitch, rows;
+    int hx, pitch, rows;
     long long plane;
     size_t buf_bytes, mom_bytes, part_bytes, total;
     size_t off_f[2], off_mom, off_part, off_sums, off_status;
@@ -167,8 +167,9 @@ struct Layout {
 Layout make_layout(int nx, int ny, int Q, int storage) {
     Layout L;
     const size_t es = elem_size(storage);
-    // pitch: a multiple of 32 elements (>= 64-byte rows) holding the fluid and the x frame
-    L.pitch = (int)align_up((size_t)nx + 2 * HX, 32);
+    // pitch: a multiple of 32 elements holding the fluid and the x frame of hx columns per side
+    L.hx = (int)(32 / es);
+    L.pitch = (int)align_up((size_t)nx + 2 * L.hx, 32);
     L.rows = ny + 2 * HY;
     L.plane = (long long)L.pitch * L.rows;
     L.buf_bytes = align_up((size_t)Q * L.plane * es, 256);
@@ -289,6 +290,7 @@ void fill_params(tvlbm_ctx* c) {
         p.sh[i] = sh;
         p.xd[i] = r.x[i];
         p.xf[i] = (float)r.x[i];
+        p.x2f[i] = p.xf[i] * p.xf[i];
         p.wd[i] = r.w[i];
         p.wf[i] = (float)r.w[i];
         p.ad[i] = a;
@@ -298,6 +300,27 @@ void fill_params(tvlbm_ctx* c) {
             p.Ef[i][k] = (float)p.Ed[i][k];
         }
     }
+    // Mirror nodes +-x share one overlap fraction pair alpha(-x) = 1 - alpha(x); keep that exact
+    // in float (the member >= 1/2 is rounded, the other is 1 minus it, exact by Sterbenz).
+    for (int i = 0; i < r.n; ++i) {
+        const int m = r.n - 1 - i;
+        if (m == i || p.ad[i] == 0.0 || p.ad[m] == 0.0) continue;
+        if (p.ad[i] >= 0.5) p.af[m] = 1.0f - p.af[i];
+    }
+    // Defects of the float tables (exact products of floats in double, summed in long double).
+    for (int a = 0; a < kMaxN1; ++a) p.dS[a] = p.dU[a] = p.dV[a] = 0.0f;
+    for (int a = 0; a <= c->N; ++a) {
+        long double S = 0, U = 0, V = 0;
+        for (int i = 0; i < r.n; ++i) {
+            const long double w = p.wf[i], x = p.xf[i], x2 = p.x2f[i], e = p.Ef[i][a];
+            S += w * e;
+            U += w * x * e;
+            V += w * x2 * e;
+        }
+        p.dS[a] = (float)(S - (a == 0 ? 1.0L : 0.0L));
+        p.dU[a] = (float)(U - (a == 1 ? 1.0L : 0.0L));
+        p.dV[a] = (float)(V - (a == 0 ? 1.0L : 0.0L) - (a == 2 ? 1.0L : 0.0L));
+    }
     p.omegad = c->dt / c->tau;
     p.omegaf = (float)p.omegad;
     p.rho0d = c->rho0;
@@ -305,6 +328,7 @@ void fill_params(tvlbm_ctx* c) {
     p.nx = c->nx;
     p.ny = c->ny;
     p.pitch = c->L.pitch;
+    p.hx = c->L.hx;
     p.rows = c->L.rows;
     p.plane = c->L.plane;
     p.walls = c->bc.kind == TVLBM_BC_WALLS;
@@ -643,7 +667,7 @@ int tvlbm_get_populations(tvlbm_ctx* c, void* host, size_t bytes) {
     const size_t es = elem_size(c->storage), row = (size_t)c->nx * es;
     const unsigned char* base = (const unsigned char*)fcur(c);
     for (int l = 0; l < c->Q; ++l) {
-        const unsigned char* src = base + ((size_t)l * c->L.plane + (size_t)HY * c->L.pitch + HX) * es;
+        const unsigned char* src = base + ((size_t)l * c->L.plane + (size_t)HY * c->L.pitch + c->L.hx) * es;
         TVLBM_CUDA(c, cudaMemcpy2DAsync((unsigned char*)host + (size_t)l * c->ny * row, row, src, (size_t)c->L.pitch * es,
                                         row, c->ny, cudaMemcpyDeviceToHost, c->stream),
                    "cudaMemcpy2DAsync");
@@ -659,7 +683,7 @@ int tvlbm_set_populations(tvlbm_ctx* c, const void* host, size_t bytes) {
     const size_t es = elem_size(c->storage), row = (size_t)c->nx * es;
     unsigned char* base = (unsigned char*)fcur(c);
     for (int l = 0; l < c->Q; ++l) {
-        unsigned char* dst = base + ((size_t)l * c->L.plane + (size_t)HY * c->L.pitch + HX) * es;
+        unsigned char* dst = base + ((size_t)l * c->L.plane + (size_t)HY * c->L.pitch + c->L.hx) * es;
         TVLBM_CUDA(c, cudaMemcpy2DAsync(dst, (size_t)c->L.pitch * es, (const unsigned char*)host + (size_t)l * c->ny * row,
                                         row, row, c->ny, cudaMemcpyHostToDevice, c->stream),
                    "cudaMemcpy2DAsync");

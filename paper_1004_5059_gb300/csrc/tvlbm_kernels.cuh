@@ -15,9 +15,9 @@ namespace tvlbm {
 
 constexpr int kMaxN1 = 6;
 constexpr int kMaxQ = kMaxN1 * kMaxN1;
-// Ghost frame around the fluid: HX columns on each side (keeps the interior 16-byte aligned
-// for every storage type), HY rows above and below; FILL of them are ever read (|shift| <= 4).
-constexpr int HX = 8;
+// Ghost frame around the fluid: hx columns on each side (KParams::hx = 32 bytes worth, so the
+// interior starts on a 32-byte sector for every storage type), HY rows above and below; FILL
+// of them are ever read (|shift| <= 4 cells).
 constexpr int HY = 4;
 constexpr int FILL = 4;
 constexpr int kRedBlocks = 1024;  // fixed partial count of the FP64 reduction (deterministic)
@@ -34,10 +34,17 @@ struct KParams {
     double xd[kMaxN1], wd[kMaxN1], ad[kMaxN1];
     float Ef[kMaxN1][kMaxN1];
     double Ed[kMaxN1][kMaxN1];
+    float x2f[kMaxN1];  // float(xf * xf), the squares the FP32 moment sums use
+    // Defects of the FP32 tables against the quadrature identities they stand for, evaluated
+    // exactly on the host from the float values (each ~1e-8, so a float holds it to ~1e-15):
+    //   dS[a] = sum_i w_i E_ia - [a=0],  dU[a] = sum_i w_i x_i E_ia - [a=1],
+    //   dV[a] = sum_i w_i x_i^2 E_ia - [a=0] - [a=2].
+    float dS[kMaxN1], dU[kMaxN1], dV[kMaxN1];
     int sh[kMaxN1];
     float omegaf, rho0f;
     double omegad, rho0d;
     int nx, ny;      // fluid cells
+    int hx;          // frame columns left of the fluid (32 bytes of elements, >= FILL)
     int pitch;       // elements per stored row (>= nx + 2 HX)
     int rows;        // stored rows (ny + 2 HY)
     long long plane; // elements per velocity plane (rows * pitch)
@@ -54,6 +61,9 @@ struct KParams {
 
 template <class R> __device__ __forceinline__ R kx(const KParams& p, int i) {
     if constexpr (std::is_same<R, double>::value) return p.xd[i]; else return p.xf[i];
+}
+template <class R> __device__ __forceinline__ R kx2(const KParams& p, int i) {
+    if constexpr (std::is_same<R, double>::value) return p.xd[i] * p.xd[i]; else return p.x2f[i];
 }
 template <class R> __device__ __forceinline__ R kw(const KParams& p, int i) {
     if constexpr (std::is_same<R, double>::value) return p.wd[i]; else return p.wf[i];
@@ -132,14 +142,14 @@ __device__ __forceinline__ void cell_moments(const R (&s)[N1 * N1], const KParam
             const R xi = kx<R>(p, i);
             r += v;
             rx = fma(xi, v, rx);
-            rxx = fma(xi * xi, v, rxx);
+            rxx = fma(kx2<R>(p, i), v, rxx);
         }
         const R yj = kx<R>(p, j);
         const R wj = DEV ? kw<R>(p, j) : R(1);
         m0 = fma(wj, r, m0);
         mx = fma(wj, rx, mx);
         my = fma(wj * yj, r, my);
-        me = fma(wj, fma(yj * yj, r, rxx), me);
+        me = fma(wj, fma(kx2<R>(p, j), r, rxx), me);
     }
     if constexpr (DEV) {
         rho = krho0<R>(p) + m0;
@@ -188,7 +198,45 @@ __device__ __forceinline__ void cell_equilibrium(const KParams& p, R rho, R ux, 
         }
         SX[i] = sx;
     }
-    const R drho = DEV ? rho - krho0<R>(p) : R(0);
+    R drho = DEV ? rho - krho0<R>(p) : R(0);
+    // FP32 deviation storage: the float tables miss the quadrature identities by ~1e-8, which
+    // would make every collision create mass, momentum and energy in proportion to the cell's
+    // own values -- a drift of ~1e-8 per step that repeats step after step.  Cancel it to first
+    // order in the defects: D = (moments of the equilibrium the tables produce) - (moments the
+    // sums measured), then subtract A + Bx c_x + By c_y + G (|c|^2 - D)/2 with A = D_m,
+    // B = D_j, G = D_e/2 - D_m, the combination whose moments are D under exact quadrature.
+    R ci[N1], cj[N1];
+    constexpr bool kCorrect = DEV && !std::is_same<R, double>::value;
+    if constexpr (kCorrect) {
+        const R m0 = drho;
+        R Dm = R(2) * p.dS[0] * m0, De = R(2) * m0 * (p.dV[0] + p.dS[0]);
+        R Dx = rho * ux * (p.dU[1] + p.dS[0]), Dy = rho * uy * (p.dU[1] + p.dS[0]);
+#pragma unroll
+        for (int a = 1; a <= N; ++a) {
+            Dm = fma(rho * p.dS[a], hx[a] + hy[a], Dm);
+            De = fma(rho * (p.dV[a] + p.dS[a]), hx[a] + hy[a], De);
+        }
+        if (N >= 2) De = fma(rho * p.dS[0], hx[2] + hy[2], De);
+#pragma unroll
+        for (int a = 3; a <= N; a += 2) {
+            Dx = fma(rho * p.dU[a], hx[a], Dx);
+            Dy = fma(rho * p.dU[a], hy[a], Dy);
+        }
+#pragma unroll
+        for (int b = 2; b <= N - 1; b += 2) {
+            Dx = fma(rho * ux * p.dS[b], hy[b], Dx);
+            Dy = fma(rho * uy * p.dS[b], hx[b], Dy);
+        }
+#pragma unroll
+        for (int b = 1; b <= N - 2; ++b) De = fma(rho * p.dS[b], fma(hx[2], hy[b], hy[2] * hx[b]), De);
+        const R G = R(0.5) * De - Dm;
+        drho -= Dm - G;
+#pragma unroll
+        for (int i = 0; i < N1; ++i) {
+            ci[i] = fma(Dx, kx<R>(p, i), R(0.5) * G * kx2<R>(p, i));
+            cj[i] = fma(Dy, kx<R>(p, i), R(0.5) * G * kx2<R>(p, i));
+        }
+    }
 #pragma unroll
     for (int j = 0; j < N1; ++j) {
 #pragma unroll
@@ -196,7 +244,8 @@ __device__ __forceinline__ void cell_equilibrium(const KParams& p, R rho, R ux, 
             R phi = SX[i] + P[j][N];  // a = 0 term: X_i0 = 1
 #pragma unroll
             for (int a = 1; a < N; ++a) phi = fma(X[i][a], P[j][N - a], phi);
-            if constexpr (DEV) eq[i + N1 * j] = fma(rho, phi, drho);
+            if constexpr (kCorrect) eq[i + N1 * j] = fma(rho, phi, drho) - (ci[i] + cj[j]);
+            else if constexpr (DEV) eq[i + N1 * j] = fma(rho, phi, drho);
             else eq[i + N1 * j] = (kw<R>(p, i) * kw<R>(p, j) * rho) * (R(1) + phi);
         }
     }
@@ -216,7 +265,7 @@ __device__ __forceinline__ void cell_collide(R (&s)[N1 * N1], const KParams& p) 
 
 // Padded storage index of fluid cell (x, y) in velocity plane l (x, y may lie in the frame).
 __device__ __forceinline__ long long sidx(const KParams& p, int l, int x, int y) {
-    return (long long)l * p.plane + (long long)(y + HY) * p.pitch + (x + HX);
+    return (long long)l * p.plane + (long long)(y + HY) * p.pitch + (x + p.hx);
 }
 
 // Store v at fluid cell (x, y) and at every periodic image of it inside the read frame
@@ -225,11 +274,11 @@ template <class T>
 __device__ __forceinline__ void store_with_images(T* f, const KParams& p, long long lbase, int x, int y, T v) {
     const int x0 = x - p.nx * ((x + FILL) / p.nx);
     if (p.walls) {
-        for (int xx = x0; xx < p.nx + FILL; xx += p.nx) f[lbase + (long long)(y + HY) * p.pitch + (xx + HX)] = v;
+        for (int xx = x0; xx < p.nx + FILL; xx += p.nx) f[lbase + (long long)(y + HY) * p.pitch + (xx + p.hx)] = v;
     } else {
         const int y0 = y - p.ny * ((y + FILL) / p.ny);
         for (int yy = y0; yy < p.ny + FILL; yy += p.ny)
-            for (int xx = x0; xx < p.nx + FILL; xx += p.nx) f[lbase + (long long)(yy + HY) * p.pitch + (xx + HX)] = v;
+            for (int xx = x0; xx < p.nx + FILL; xx += p.nx) f[lbase + (long long)(yy + HY) * p.pitch + (xx + p.hx)] = v;
     }
 }
 

@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(256) sweep_plain_kernel(const typename C::T* _
 #pragma unroll
         for (int i = 0; i < N1; ++i) {
             const R ax = ka<R>(p, i);
-            const int xs = x + HX - p.sh[i];
+            const int xs = x + p.hx - p.sh[i];
             const T* b = fin + (long long)(i + N1 * j) * p.plane + (long long)ys * p.pitch + xs;
             const R v00 = C::ld(b), v01 = C::ld(b - 1);
             const R v10 = C::ld(b - p.pitch), v11 = C::ld(b - p.pitch - 1);

@@ -87,7 +87,7 @@ constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s: a TMA load never takes
 // Store v at (x, y) and, for cells within FILL of a periodic edge, at their frame images.
 template <class T>
 __device__ __forceinline__ void store_cell(T* f, const KParams& p, long long lbase, int x, int y, bool edge, T v) {
-    if (!edge) f[lbase + (long long)(y + HY) * p.pitch + (x + HX)] = v;
+    if (!edge) f[lbase + (long long)(y + HY) * p.pitch + (x + p.hx)] = v;
     else store_with_images(f, p, lbase, x, y, v);
 }
 
@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(TileCfg<N1, C>::THREADS)
 #pragma unroll 1
         for (int l = 0; l < Q; ++l) {
             const int i = l % N1, j = l / N1;
-            const int xs = x0 + HX - p.sh[i] - 1;
+            const int xs = x0 + p.hx - p.sh[i] - 1;
             const int ys = y0 + HY - p.sh[j] - 1;
             mbar_arrive_expect_tx(&bars[l], (uint32_t)(BX * Cfg::BY * Cfg::ES));
             tma_load_3d(base + l * Cfg::WIN_BYTES, &tmap, &bars[l], xs & ~(A - 1), ys, l);
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(TileCfg<N1, C>::THREADS)
             const int l = i + N1 * j;
             if (ok && !mbar_wait_bounded(&bars[l], 0, kWaitLimitNs)) ok = false;
             const R ax = ka<R>(p, i);
-            const int xs = x0 + HX - p.sh[i] - 1;
+            const int xs = x0 + p.hx - p.sh[i] - 1;
             const int col = cx + (xs & (A - 1));
             const T* w = (const T*)(base + l * Cfg::WIN_BYTES) + r0 * BX + col;
             R a = lds<C>(w + 1), b = lds<C>(w);
