@@ -191,10 +191,16 @@ def run_ours(args, w, rank, world, local_rank):
         ms = sum(a.elapsed_time(b) for a, b in evs)
         return ms
 
-    forms = []
     probe = make(args.form)
     chosen = args.form
-    forms.append(chosen)
+    tuning = None
+    if chosen == "tiled":
+        if args.tile >= 0:
+            probe.set_tile(args.tile)
+        else:
+            from paper_1004_5059_gb300 import autotune
+            tuning = autotune.autotune(probe, steps=min(tsteps, 100), repeats=3)
+        probe.init_moments(*fields)
     clocks = Clocks(local_rank)
     clocks.start()
     ms_total = timed(probe, args.steps, args.warmup)
@@ -258,6 +264,10 @@ def run_ours(args, w, rank, world, local_rank):
         "data": "synthetic (seeded fields shaped like the paper's test problems)",
         "config": {"workload": w["desc"], "nx": nx, "ny": ny, "velset": w["velset"], "storage": w["storage"],
                    "tau": w["tau"], "time_steps_per_bench_step": tsteps, "form": chosen,
+                   "tile": (list(tv.tvlbm_tile_shape(probe.ctx, tuning["best"])) if tuning else
+                            (list(tv.tvlbm_tile_shape(probe.ctx, max(args.tile, 0))) if chosen == "tiled" else None)),
+                   "autotune": ({str(tuple(t["tile"])): round(t["s_per_step"] * 1e6, 2) for t in tuning["trials"]}
+                                if tuning else None),
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "L2 flushed (512 MiB write) between timed steps; state %.0f MB" % (
                        bytes_per_cell * cells / 1e6)},
@@ -362,6 +372,7 @@ def main():
     ap.add_argument("--workload", default="c1", choices=sorted(WORKLOADS))
     ap.add_argument("--form", default=None, choices=["tiled", "plain"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tile", type=int, default=-1, help="tile configuration of the tiled form (-1: autotune)")
     args = ap.parse_args()
     rank, world, local_rank = dist_env()
     w = WORKLOADS[args.workload]

@@ -118,6 +118,13 @@ int tvlbm_set_form(tvlbm_ctx *ctx, int form);
 /* Enable (1, default) or disable (0) replay of multi-step runs through captured CUDA graphs. */
 int tvlbm_set_graphs(tvlbm_ctx *ctx, int enable);
 
+/* Tile configurations of the tiled form (an autotuner picks among them): their number, and
+ * the shape of one -- tile width and height in cells and rows each thread walks.
+ * tvlbm_set_tile selects one (synchronises the stream; default 0).  Errors: EINVAL. */
+int tvlbm_tile_count(const tvlbm_ctx *ctx);
+int tvlbm_tile_shape(const tvlbm_ctx *ctx, int config, int *tx, int *ty, int *rows_per_thread);
+int tvlbm_set_tile(tvlbm_ctx *ctx, int config);
+
 /* Initialise every cell to the equilibrium f_eq(rho, u, T) (Sec. "The TVLBM model"),
  * computed in FP64 and rounded to the storage format.  Host FP64 fields [ny][nx];
  * requires rho > 0 and T > 0 everywhere (EINVAL otherwise, nothing written).

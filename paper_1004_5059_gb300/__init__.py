@@ -70,6 +70,9 @@ def _load_library() -> ctypes.CDLL:
         "tvlbm_set_stream": (_I, [_P, _P]),
         "tvlbm_set_form": (_I, [_P, _I]),
         "tvlbm_set_graphs": (_I, [_P, _I]),
+        "tvlbm_tile_count": (_I, [_P]),
+        "tvlbm_tile_shape": (_I, [_P, _I, _IP, _IP, _IP]),
+        "tvlbm_set_tile": (_I, [_P, _I]),
         "tvlbm_init_moments": (_I, [_P, _DP, _DP, _DP, _DP]),
         "tvlbm_step": (_I, [_P, _I]),
         "tvlbm_moments": (_I, [_P, _DP, _DP, _DP, _DP]),
@@ -153,6 +156,20 @@ def tvlbm_set_form(ctx, form: int):
 
 def tvlbm_set_graphs(ctx, enable: bool):
     _check(_lib.tvlbm_set_graphs(ctx, 1 if enable else 0), ctx)
+
+
+def tvlbm_tile_count(ctx) -> int:
+    return int(_lib.tvlbm_tile_count(ctx))
+
+
+def tvlbm_tile_shape(ctx, config: int):
+    tx, ty, r = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(_lib.tvlbm_tile_shape(ctx, config, ctypes.byref(tx), ctypes.byref(ty), ctypes.byref(r)), ctx)
+    return tx.value, ty.value, r.value
+
+
+def tvlbm_set_tile(ctx, config: int):
+    _check(_lib.tvlbm_set_tile(ctx, int(config)), ctx)
 
 
 def tvlbm_init_moments(ctx, rho, ux, uy, T):
@@ -266,6 +283,9 @@ class Simulation:
 
     def set_form(self, form):
         tvlbm_set_form(self.ctx, FORMS[form] if isinstance(form, str) else int(form))
+
+    def set_tile(self, config: int):
+        tvlbm_set_tile(self.ctx, config)
 
     def init_moments(self, rho, ux, uy, T):
         tvlbm_init_moments(self.ctx, rho, ux, uy, T)

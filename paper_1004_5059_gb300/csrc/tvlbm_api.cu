@@ -12,6 +12,7 @@
 
 #include "tvlbm.h"
 #include "tvlbm_kernels.cuh"
+#include "tvlbm_tiled.cuh"
 
 using namespace tvlbm;
 
@@ -214,6 +215,7 @@ struct tvlbm_ctx {
     cudaStream_t capture_stream;
     cudaGraphExec_t graph[2];
     int have_tmap;
+    int tile_cfg;                     // tiled-form tile configuration
     alignas(64) CUtensorMap tmap[2];  // TMA descriptors of the two population buffers
     char err[512];
 };
@@ -307,15 +309,20 @@ void fill_params(tvlbm_ctx* c) {
         if (m == i || p.ad[i] == 0.0 || p.ad[m] == 0.0) continue;
         if (p.ad[i] >= 0.5) p.af[m] = 1.0f - p.af[i];
     }
-    // Defects of the float tables (exact products of floats in double, summed in long double).
+    // Pre-multiplied FP32 constants of the moment sums and their defects against the
+    // quadrature identities (exact products of floats in long double).
+    for (int i = 0; i < r.n; ++i) {
+        p.wxf[i] = p.wf[i] * p.xf[i];
+        p.wx2f[i] = p.wf[i] * p.x2f[i];
+    }
     for (int a = 0; a < kMaxN1; ++a) p.dS[a] = p.dU[a] = p.dV[a] = 0.0f;
     for (int a = 0; a <= c->N; ++a) {
         long double S = 0, U = 0, V = 0;
         for (int i = 0; i < r.n; ++i) {
-            const long double w = p.wf[i], x = p.xf[i], x2 = p.x2f[i], e = p.Ef[i][a];
-            S += w * e;
-            U += w * x * e;
-            V += w * x2 * e;
+            const long double e = p.Ef[i][a];
+            S += (long double)p.wf[i] * e;
+            U += (long double)p.wxf[i] * e;
+            V += (long double)p.wx2f[i] * e;
         }
         p.dS[a] = (float)(S - (a == 0 ? 1.0L : 0.0L));
         p.dU[a] = (float)(U - (a == 1 ? 1.0L : 0.0L));
@@ -369,7 +376,7 @@ cudaError_t launch_step(tvlbm_ctx* c, int from, cudaStream_t s) {
         const cudaError_t e = c->kt->wall(c->storage, fin, c->kp, s);
         if (e != cudaSuccess) return e;
     }
-    return c->kt->sweep(c->storage, c->form, fin, fout, &c->tmap[from], c->kp, s);
+    return c->kt->sweep(c->storage, c->form, c->tile_cfg, fin, fout, &c->tmap[from], c->kp, s);
 }
 
 // TMA descriptors for the tiled form: a 3-D view [Q][rows][pitch] of each population buffer,
@@ -392,7 +399,7 @@ bool make_tensor_maps(tvlbm_ctx* c) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc || !c->kt->tiled_available(c->storage)) return false;
     int bx = 0, by = 0;
-    c->kt->tiled_box(c->storage, &bx, &by);
+    c->kt->tiled_box(c->storage, c->tile_cfg, &bx, &by);
     CUtensorMapDataType dt;
     switch (c->storage) {
         case TVLBM_FP64: dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT64; break;
@@ -493,6 +500,7 @@ int create_common(int nx, int ny, int velset, double tau, double dt, const tvlbm
     }
     c->stream = nullptr;
     c->kp.status = (int*)dptr(c, c->L.off_status);
+    c->tile_cfg = 0;
     c->have_tmap = make_tensor_maps(c) ? 1 : 0;
     if (c->have_tmap) c->form = FORM_TILED;
     // Both buffers (frame included) start as the rest equilibrium f = rho0 w: zero the memory,
@@ -591,6 +599,31 @@ int tvlbm_set_form(tvlbm_ctx* c, int form) {
 int tvlbm_set_graphs(tvlbm_ctx* c, int enable) {
     if (!c) return TVLBM_EINVAL;
     c->graphs = enable ? 1 : 0;
+    return TVLBM_OK;
+}
+
+int tvlbm_tile_count(const tvlbm_ctx* c) { return c ? kTileConfigs : 0; }
+
+int tvlbm_tile_shape(const tvlbm_ctx* c, int config, int* tx, int* ty, int* rows_per_thread) {
+    if (!c || config < 0 || config >= kTileConfigs || !tx || !ty || !rows_per_thread) return TVLBM_EINVAL;
+    c->kt->tile_shape(c->storage, config, tx, ty, rows_per_thread);
+    return TVLBM_OK;
+}
+
+int tvlbm_set_tile(tvlbm_ctx* c, int config) {
+    if (!c) return TVLBM_EINVAL;
+    if (config < 0 || config >= kTileConfigs) return fail(c, TVLBM_EINVAL, "tile configuration %d out of range", config);
+    if (config == c->tile_cfg) return TVLBM_OK;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);  // launched work keeps its own copy of the descriptors
+    const int old = c->tile_cfg;
+    c->tile_cfg = config;
+    if (!make_tensor_maps(c)) {
+        c->tile_cfg = old;
+        make_tensor_maps(c);
+        return fail(c, TVLBM_EINVAL, "no TMA descriptor for tile configuration %d", config);
+    }
+    drop_graphs(c);
     return TVLBM_OK;
 }
 

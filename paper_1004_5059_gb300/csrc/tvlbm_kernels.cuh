@@ -34,11 +34,13 @@ struct KParams {
     double xd[kMaxN1], wd[kMaxN1], ad[kMaxN1];
     float Ef[kMaxN1][kMaxN1];
     double Ed[kMaxN1][kMaxN1];
-    float x2f[kMaxN1];  // float(xf * xf), the squares the FP32 moment sums use
-    // Defects of the FP32 tables against the quadrature identities they stand for, evaluated
-    // exactly on the host from the float values (each ~1e-8, so a float holds it to ~1e-15):
-    //   dS[a] = sum_i w_i E_ia - [a=0],  dU[a] = sum_i w_i x_i E_ia - [a=1],
-    //   dV[a] = sum_i w_i x_i^2 E_ia - [a=0] - [a=2].
+    float x2f[kMaxN1];   // float(xf * xf)
+    float wxf[kMaxN1];   // float(wf * xf): the constants of the FP32 momentum sums
+    float wx2f[kMaxN1];  // float(wf * x2f): the constants of the FP32 energy sums
+    // Defects of those FP32 constants against the quadrature identities they stand for,
+    // evaluated exactly on the host (each ~1e-8, so a float holds it to ~1e-15):
+    //   dS[a] = sum_i wf_i E_ia - [a=0],  dU[a] = sum_i wxf_i E_ia - [a=1],
+    //   dV[a] = sum_i wx2f_i E_ia - [a=0] - [a=2].
     float dS[kMaxN1], dU[kMaxN1], dV[kMaxN1];
     int sh[kMaxN1];
     float omegaf, rho0f;
@@ -198,45 +200,7 @@ __device__ __forceinline__ void cell_equilibrium(const KParams& p, R rho, R ux, 
         }
         SX[i] = sx;
     }
-    R drho = DEV ? rho - krho0<R>(p) : R(0);
-    // FP32 deviation storage: the float tables miss the quadrature identities by ~1e-8, which
-    // would make every collision create mass, momentum and energy in proportion to the cell's
-    // own values -- a drift of ~1e-8 per step that repeats step after step.  Cancel it to first
-    // order in the defects: D = (moments of the equilibrium the tables produce) - (moments the
-    // sums measured), then subtract A + Bx c_x + By c_y + G (|c|^2 - D)/2 with A = D_m,
-    // B = D_j, G = D_e/2 - D_m, the combination whose moments are D under exact quadrature.
-    R ci[N1], cj[N1];
-    constexpr bool kCorrect = DEV && !std::is_same<R, double>::value;
-    if constexpr (kCorrect) {
-        const R m0 = drho;
-        R Dm = R(2) * p.dS[0] * m0, De = R(2) * m0 * (p.dV[0] + p.dS[0]);
-        R Dx = rho * ux * (p.dU[1] + p.dS[0]), Dy = rho * uy * (p.dU[1] + p.dS[0]);
-#pragma unroll
-        for (int a = 1; a <= N; ++a) {
-            Dm = fma(rho * p.dS[a], hx[a] + hy[a], Dm);
-            De = fma(rho * (p.dV[a] + p.dS[a]), hx[a] + hy[a], De);
-        }
-        if (N >= 2) De = fma(rho * p.dS[0], hx[2] + hy[2], De);
-#pragma unroll
-        for (int a = 3; a <= N; a += 2) {
-            Dx = fma(rho * p.dU[a], hx[a], Dx);
-            Dy = fma(rho * p.dU[a], hy[a], Dy);
-        }
-#pragma unroll
-        for (int b = 2; b <= N - 1; b += 2) {
-            Dx = fma(rho * ux * p.dS[b], hy[b], Dx);
-            Dy = fma(rho * uy * p.dS[b], hx[b], Dy);
-        }
-#pragma unroll
-        for (int b = 1; b <= N - 2; ++b) De = fma(rho * p.dS[b], fma(hx[2], hy[b], hy[2] * hx[b]), De);
-        const R G = R(0.5) * De - Dm;
-        drho -= Dm - G;
-#pragma unroll
-        for (int i = 0; i < N1; ++i) {
-            ci[i] = fma(Dx, kx<R>(p, i), R(0.5) * G * kx2<R>(p, i));
-            cj[i] = fma(Dy, kx<R>(p, i), R(0.5) * G * kx2<R>(p, i));
-        }
-    }
+    const R drho = DEV ? rho - krho0<R>(p) : R(0);
 #pragma unroll
     for (int j = 0; j < N1; ++j) {
 #pragma unroll
@@ -244,8 +208,7 @@ __device__ __forceinline__ void cell_equilibrium(const KParams& p, R rho, R ux, 
             R phi = SX[i] + P[j][N];  // a = 0 term: X_i0 = 1
 #pragma unroll
             for (int a = 1; a < N; ++a) phi = fma(X[i][a], P[j][N - a], phi);
-            if constexpr (kCorrect) eq[i + N1 * j] = fma(rho, phi, drho) - (ci[i] + cj[j]);
-            else if constexpr (DEV) eq[i + N1 * j] = fma(rho, phi, drho);
+            if constexpr (DEV) eq[i + N1 * j] = fma(rho, phi, drho);
             else eq[i + N1 * j] = (kw<R>(p, i) * kw<R>(p, j) * rho) * (R(1) + phi);
         }
     }
@@ -285,8 +248,9 @@ __device__ __forceinline__ void store_with_images(T* f, const KParams& p, long l
 // ---- kernel table (one per N1, defined in tvlbm_kernels_q*.cu) ----------------------------
 struct KernelTable {
     // tmap: TMA descriptor (CUtensorMap) of fin, used by the tiled form
-    cudaError_t (*sweep)(int storage, int form, const void* fin, void* fout, const void* tmap, const KParams& p,
-                         cudaStream_t s);
+    // cfg: tile configuration of the tiled form (0 .. kTileConfigs-1)
+    cudaError_t (*sweep)(int storage, int form, int cfg, const void* fin, void* fout, const void* tmap,
+                         const KParams& p, cudaStream_t s);
     cudaError_t (*init)(int storage, const double* fields, void* f, const KParams& p, cudaStream_t s);
     cudaError_t (*moments)(int storage, const void* f, double* out4, const KParams& p, cudaStream_t s);
     cudaError_t (*reduce)(int storage, const void* f, double* partials, double* out5, const KParams& p, cudaStream_t s);
@@ -295,7 +259,8 @@ struct KernelTable {
     cudaError_t (*decode_plane)(int storage, const void* f, int l, double* out, const KParams& p, cudaStream_t s);
     cudaError_t (*encode_plane)(int storage, void* f, int l, const double* in, const KParams& p, cudaStream_t s);
     int (*tiled_available)(int storage);
-    void (*tiled_box)(int storage, int* bx, int* by);  // TMA box (elements) of the tiled form
+    void (*tiled_box)(int storage, int cfg, int* bx, int* by);  // TMA box (elements) of a tile config
+    void (*tile_shape)(int storage, int cfg, int* tx, int* ty, int* rows_per_thread);
 };
 
 const KernelTable* kernel_table_q3();

@@ -41,10 +41,8 @@ __global__ void __launch_bounds__(256) sweep_plain_kernel(const typename C::T* _
             s[i + N1 * j] = fma(ay, r1 - r0, r0);
         }
     }
-    cell_collide<N1, C::dev, R>(s, p);
-    const bool edge = x < FILL || x >= p.nx - FILL || (!p.walls && (y < FILL || y >= p.ny - FILL));
-#pragma unroll
-    for (int l = 0; l < Q; ++l) store_cell(fout, p, (long long)l * p.plane, x, y, edge, C::enc(s[l]));
+    collide_cell<N1, C>(s, p);
+    store_collided<N1, C>(fout, p, x, y, s);
 }
 
 // =============================================================================================
@@ -272,10 +270,10 @@ struct Launch {
     static dim3 grid2d(const KParams& p, dim3 b) { return dim3((p.nx + b.x - 1) / b.x, (p.ny + b.y - 1) / b.y); }
 
     template <class C>
-    static cudaError_t sweep_c(int form, const void* fin, void* fout, const void* tmap, const KParams& p,
+    static cudaError_t sweep_c(int form, int cfg, const void* fin, void* fout, const void* tmap, const KParams& p,
                                cudaStream_t s) {
         using T = typename C::T;
-        if (form == FORM_TILED) return tiled_sweep<N1, C>((const CUtensorMap*)tmap, (T*)fout, p, s);
+        if (form == FORM_TILED) return tiled_sweep<N1, C>(cfg, (const CUtensorMap*)tmap, (T*)fout, p, s);
         const dim3 b(32, 8);
         sweep_plain_kernel<N1, C><<<grid2d(p, b), b, 0, s>>>((const T*)fin, (T*)fout, p);
         return cudaGetLastError();
@@ -332,9 +330,9 @@ struct Launch {
         default: return cudaErrorInvalidValue;                  \
     }
 
-    static cudaError_t sweep(int storage, int form, const void* fin, void* fout, const void* tmap, const KParams& p,
-                             cudaStream_t s) {
-        TVLBM_DISPATCH(sweep_c, (form, fin, fout, tmap, p, s))
+    static cudaError_t sweep(int storage, int form, int cfg, const void* fin, void* fout, const void* tmap,
+                             const KParams& p, cudaStream_t s) {
+        TVLBM_DISPATCH(sweep_c, (form, cfg, fin, fout, tmap, p, s))
     }
     static cudaError_t init(int storage, const double* fields, void* f, const KParams& p, cudaStream_t s) {
         TVLBM_DISPATCH(init_c, (fields, f, p, s))
@@ -354,20 +352,27 @@ struct Launch {
         TVLBM_DISPATCH(encode_c, (f, l, in, p, s))
     }
     static int tiled_available(int storage) { return tiled_supported<N1>(storage); }
-    static void box(int storage, int* bx, int* by) {
+    static void box(int storage, int cfg, int* bx, int* by) {
         switch (storage) {
-            case ST_FP64: tiled_box<N1, CodecF64>(bx, by); break;
-            case ST_FP32: tiled_box<N1, CodecF32>(bx, by); break;
-            case ST_BF16_DEV: tiled_box<N1, CodecBF16Dev>(bx, by); break;
-            case ST_FP16_DEV: tiled_box<N1, CodecF16Dev>(bx, by); break;
-            default: tiled_box<N1, CodecF32Dev>(bx, by); break;
+            case ST_FP64: tiled_box<N1, CodecF64>(cfg, bx, by); break;
+            case ST_FP32: tiled_box<N1, CodecF32>(cfg, bx, by); break;
+            case ST_BF16_DEV: tiled_box<N1, CodecBF16Dev>(cfg, bx, by); break;
+            case ST_FP16_DEV: tiled_box<N1, CodecF16Dev>(cfg, bx, by); break;
+            default: tiled_box<N1, CodecF32Dev>(cfg, bx, by); break;
         }
+    }
+    static void shape(int storage, int cfg, int* tx, int* ty, int* r) {
+        const int es = storage == ST_FP64 ? 8 : (storage == ST_BF16_DEV || storage == ST_FP16_DEV) ? 2 : 4;
+        const TileShape t = tile_shape(es, cfg);
+        *tx = t.tx;
+        *ty = t.ty;
+        *r = t.ty / t.rs;
     }
 #undef TVLBM_DISPATCH
 
     static const KernelTable* table() {
         static const KernelTable t = {&sweep, &init, &moments, &reduce, &wall, &halo, &decode, &encode, &tiled_available,
-                                      &box};
+                                      &box, &shape};
         return &t;
     }
 };
