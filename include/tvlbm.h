@@ -150,6 +150,25 @@ int tvlbm_moments(tvlbm_ctx *ctx, double *rho, double *ux, double *uy, double *T
  * Synchronises the stream. */
 int tvlbm_conserved_sums(tvlbm_ctx *ctx, double out[5]);
 
+/* Conserved sums that allocate nothing, for callers that cannot call cudaMalloc or any other
+ * allocator on this path (code running inside another framework's memory pool or a
+ * stream-ordered pipeline that owns all device memory).  The paper has no counterpart: this
+ * is an interface variant of tvlbm_conserved_sums, the same FP64 two-pass reduction.
+ *   populations  device pointer, packed [Q][ny][nx] in the storage format (the layout
+ *                tvlbm_get_populations returns), caller-owned
+ *   velset, storage, nx, ny, rho0   describe that array (rho0: deviation reference)
+ *   out5         device pointer to 5 doubles, caller-owned: M, P_x, P_y, E, #non-finite
+ *   stream       cudaStream_t the two kernels are queued on (asynchronous; NULL = default)
+ * The per-block partial sums live in a fixed device array of 1024 x 5 doubles (40 KiB) that
+ * every GPU which loads the library holds until the process exits.  The first call on a device
+ * looks up that array's address (cudaGetSymbolAddress) with the device current: make it before
+ * any stream capture.  Each call overwrites the whole array, so nothing needs clearing; calls
+ * that overlap on the GPU race on it.  No cudaMalloc, cudaFree or allocating library call.
+ * Errors: EINVAL (null pointer, unknown set or storage, Q*nx*ny > 2^31 - 1 populations),
+ * ECUDA. */
+int tvlbm_conserved_sums_static(const void *populations, int velset, int storage, int nx, int ny, double rho0,
+                                double *out5, void *stream);
+
 /* Checkpoint: copy the raw stored populations (storage format, [Q][ny][nx], no ghost frame)
  * to / from host memory of exactly tvlbm_population_bytes(ctx) bytes.  set_populations also
  * refreshes the periodic ghost frame.  Both synchronise the stream.  Errors: EINVAL (size). */
