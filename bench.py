@@ -44,8 +44,13 @@ WORKLOADS = {
                nx=64, ny=64, velset="D2Q16", storage="fp64", plain_storage="fp64", tau=0.8, walls=None, tsteps=200),
     "c2": dict(desc="D2Q36 4096x512 thermal Couette FP16-deviation storage tau=0.9, walls T=1.0/1.1, u_top=0.1, "
                     "1000 time steps", nx=4096, ny=512, velset="D2Q36", storage="fp16_dev", plain_storage="fp16_dev",
-               tau=0.9, walls=(0.0, 1.0, 0.1, 1.1), tsteps=1000),
+               tau=0.9, walls=(0.0, 1.0, 0.1, 1.1), tsteps=1000, reference=(0.05, 0.0, 1.05)),
 }
+
+BATCH = dict(desc="256 independent periodic D2Q16 domains, sides drawn from {128,256,512,768,1024}, tau~U[0.55,1.5], "
+                   "Mach~U[0.05,0.3], seeded fields, FP32 populations; one persistent launch per time step over all "
+                   "tiles, CUDA-graph replay, autotuned tile shape; 20 time steps per bench step",
+             count=256, seed=3, velset="D2Q16", storage="fp32_dev", tsteps=20)
 
 METRIC = "MLUPS (million lattice-cell updates per second) of the fused TVLBM sweep"
 UNIT = "MLUPS"
@@ -162,6 +167,8 @@ def run_ours(args, w, rank, world, local_rank):
     def make(form, storage=None):
         s = tv.Simulation(nx, ny, w["velset"], tau=w["tau"], dt=1.0, walls=w["walls"],
                           storage=storage or w["storage"], form=form, stream=stream)
+        if w.get("reference") and (storage or w["storage"]).endswith("_dev"):
+            s.set_reference(*w["reference"])
         s.init_moments(*fields)
         return s
 
@@ -264,6 +271,7 @@ def run_ours(args, w, rank, world, local_rank):
         "data": "synthetic (seeded fields shaped like the paper's test problems)",
         "config": {"workload": w["desc"], "nx": nx, "ny": ny, "velset": w["velset"], "storage": w["storage"],
                    "tau": w["tau"], "time_steps_per_bench_step": tsteps, "form": chosen,
+                   "deviation_reference": w.get("reference"),
                    "tile": (list(tv.tvlbm_tile_shape(probe.ctx, tuning["best"])) if tuning else
                             (list(tv.tvlbm_tile_shape(probe.ctx, max(args.tile, 0))) if chosen == "tiled" else None)),
                    "autotune": ({str(tuple(t["tile"])): round(t["s_per_step"] * 1e6, 2) for t in tuning["trials"]}
@@ -363,18 +371,157 @@ def run_reference(args, w, rank, world):
     }
 
 
+def batch_fields(spec):
+    """Seeded initial fields of one batched domain: T bump + random Fourier flow scaled to the
+    domain's Mach number (c_s = 1)."""
+    n = spec["n"]
+    return workloads.gaussian_bump_random_flow(n, n, seed=spec["seed"], amp_u=spec["mach"], sigma=n / 16.0)
+
+
+def run_batch(args, rank, world, local_rank):
+    import torch
+    import paper_1004_5059_gb300 as tv
+    from paper_1004_5059_gb300 import autotune
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    specs = workloads.batched_domains(BATCH["count"], seed=BATCH["seed"])
+    n = [s["n"] for s in specs]
+    stream = torch.cuda.current_stream(dev)
+    b = tv.Batch(n, n, [s["tau"] for s in specs], BATCH["velset"], storage=BATCH["storage"], stream=stream)
+    fields = [batch_fields(s) for s in specs]
+    for d, f in enumerate(fields):
+        b.init_moments(d, *f)
+    tsteps = BATCH["tsteps"]
+    # autotune the tile shape on the batch itself (untimed), then restart from the initial state
+    trials = {}
+    for cfg in range(b.tile_count()):
+        b.set_tile(cfg)
+        b.step(tsteps)
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        b.step(tsteps)
+        e.record(stream)
+        e.synchronize()
+        trials[cfg] = a.elapsed_time(e) / tsteps
+    best = min(trials, key=trials.get)
+    b.set_tile(best)
+    for d, f in enumerate(fields):
+        b.init_moments(d, *f)
+    cells = b.cells()
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        b.step(tsteps)
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    clocks = Clocks(local_rank)
+    clocks.start()
+    evs = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        b.step(tsteps)
+        e.record(stream)
+        evs.append((a, e))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(e) for a, e in evs)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * cells * tsteps * args.steps / (ms_max / 1e3) / 1e6
+    peak, peak_kind = measured_peak_hbm()
+    achieved = b.bytes_per_cell() * cells / (ms / 1e3 / (args.steps * tsteps)) / 1e9
+    # end to end: host fields of every domain in (pinned), time steps, every domain's moments out
+    pinned = [[torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in f] for f in fields]
+    e2e_steps = 2
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for d, f in enumerate(pinned):
+            b.init_moments(d, *f)
+        b.step(tsteps)
+        for d in range(b.count):
+            b.moments(d)
+    torch.cuda.synchronize()
+    e2e = world * cells * tsteps * e2e_steps / (time.perf_counter() - t0) / 1e6
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded fields)",
+        "config": {"workload": BATCH["desc"], "domains": b.count, "cells": cells, "velset": BATCH["velset"],
+                   "storage": BATCH["storage"], "time_steps_per_bench_step": tsteps,
+                   "tile": list(b.tile_shape(best)), "autotune_ms_per_time_step": {
+                       str(b.tile_shape(k)): round(v, 4) for k, v in trials.items()},
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "L2 flushed between timed steps; state %.1f GB" % (b.bytes_per_cell() * cells / 1e9)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_kind": peak_kind, "bytes_per_cell": b.bytes_per_cell(), "traffic": None},
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 32 * cells, "d2h_bytes_per_step": 32 * cells},
+        "gpu_launches": args.steps * tsteps,
+        "clocks": clk,
+    }
+    b.close()
+    return line if rank == 0 else None
+
+
+def run_batch_reference(args, rank):
+    """The oracle on the batched workload: each bench step one time step of a bounded sample of
+    the domains (the smallest ones first), timed on the host cores."""
+    if rank != 0:
+        return None
+    import oracle
+    specs = sorted(workloads.batched_domains(BATCH["count"], seed=BATCH["seed"]), key=lambda s: s["n"])[:8]
+    cores = _oracle_threads()
+    sims = []
+    for s in specs:
+        o = oracle.Oracle(s["n"], s["n"], BATCH["velset"], tau=s["tau"], threads=cores)
+        o.init_moments(*batch_fields(s))
+        sims.append(o)
+    cells = sum(s["n"] ** 2 for s in specs)
+    for _ in range(args.warmup):
+        for o in sims:
+            o.run(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for o in sims:
+            o.run(1)
+    dt = time.perf_counter() - t0
+    value = cells * args.steps / dt / 1e6
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": BATCH["desc"], "sample": "one time step of the %d smallest domains" % len(specs)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "one time step of the %d smallest domains per bench step" % len(specs)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c1", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="c1", choices=sorted(WORKLOADS) + ["c3"])
     ap.add_argument("--form", default=None, choices=["tiled", "plain"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile", type=int, default=-1, help="tile configuration of the tiled form (-1: autotune)")
     args = ap.parse_args()
     rank, world, local_rank = dist_env()
+    if args.workload == "c3":
+        line = run_batch(args, rank, world, local_rank) if args.impl == "ours" else run_batch_reference(args, rank)
+        if rank == 0 and line is not None:
+            print(json.dumps(line))
+        return
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
         line = run_reference(args, w, rank, world)

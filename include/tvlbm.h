@@ -118,6 +118,13 @@ int tvlbm_set_form(tvlbm_ctx *ctx, int form);
 /* Enable (1, default) or disable (0) replay of multi-step runs through captured CUDA graphs. */
 int tvlbm_set_graphs(tvlbm_ctx *ctx, int enable);
 
+/* Deviation storage only: express the stored populations against the reference equilibrium
+ * f_eq(rho0, (ux, uy), T), i.e. store d_l = f_l / w_l - f_eq_l / w_l (default: at rest, T = 1).
+ * A reference near the flow's mean state shrinks |d| and with it the half-precision rounding
+ * error.  The current state is re-encoded (synchronises).  Errors: EINVAL (full-f storage,
+ * T <= 0). */
+int tvlbm_set_reference(tvlbm_ctx *ctx, double ux, double uy, double T);
+
 /* Tile configurations of the tiled form (an autotuner picks among them): their number, and
  * the shape of one -- tile width and height in cells and rows each thread walks.
  * tvlbm_set_tile selects one (synchronises the stream; default 0).  Errors: EINVAL. */
@@ -194,6 +201,45 @@ int tvlbm_stream_table(int velset, double dt, int *sx, int *sy, double *ax, doub
 /* Algorithmic bytes moved by one sweep per fluid cell: Q * (read + write) * bytes per stored
  * population (halo re-reads and ghost-frame copies not counted). */
 double tvlbm_bytes_per_cell(const tvlbm_ctx *ctx);
+
+/* ---- batched domains ------------------------------------------------------------------------
+ * Many independent periodic domains of different sizes and relaxation times (one velocity set,
+ * storage and dt), advanced together: each time step is one persistent launch of the tiled
+ * sweep over the tiles of every domain, and multi-step runs replay captured CUDA graphs.
+ * Domain d is nx[d] x ny[d] cells with relaxation time tau[d]; everything else follows the
+ * single-domain calls above (layouts, errors, ownership, stream semantics). */
+typedef struct tvlbm_batch tvlbm_batch;
+
+/* Device bytes of a batch (host-only).  Errors: EINVAL. */
+int tvlbm_batch_memory_bytes(int count, const int *nx, const int *ny, int velset, int storage, size_t *bytes);
+/* Create a batch on the current device (library-owned memory, or caller-owned device memory of
+ * >= tvlbm_batch_memory_bytes bytes, 256-byte aligned).  All domains start at rest.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+int tvlbm_batch_create(int count, const int *nx, const int *ny, const double *tau, int velset, int storage, double dt,
+                       double rho0, tvlbm_batch **out);
+int tvlbm_batch_create_in(int count, const int *nx, const int *ny, const double *tau, int velset, int storage,
+                          double dt, double rho0, void *device_memory, size_t bytes, tvlbm_batch **out);
+int tvlbm_batch_destroy(tvlbm_batch *b);
+int tvlbm_batch_set_stream(tvlbm_batch *b, void *stream);
+int tvlbm_batch_set_graphs(tvlbm_batch *b, int enable);
+/* Tile configurations of the batched sweep (as tvlbm_tile_*); set_tile rebuilds the tile list. */
+int tvlbm_batch_tile_count(const tvlbm_batch *b);
+int tvlbm_batch_tile_shape(const tvlbm_batch *b, int config, int *tx, int *ty, int *rows_per_thread);
+int tvlbm_batch_set_tile(tvlbm_batch *b, int config);
+/* Initialise domain d to the equilibrium of host FP64 fields [ny[d]][nx[d]] (synchronises). */
+int tvlbm_batch_init_moments(tvlbm_batch *b, int domain, const double *rho, const double *ux, const double *uy,
+                             const double *T);
+/* Advance every domain n time steps (asynchronous). */
+int tvlbm_batch_step(tvlbm_batch *b, int n);
+/* Diagnostics and populations of domain d, as tvlbm_moments / tvlbm_conserved_sums /
+ * tvlbm_get_populations_f64 (synchronise). */
+int tvlbm_batch_moments(tvlbm_batch *b, int domain, double *rho, double *ux, double *uy, double *T);
+int tvlbm_batch_conserved_sums(tvlbm_batch *b, int domain, double out[5]);
+int tvlbm_batch_get_populations_f64(tvlbm_batch *b, int domain, double *host);
+/* Total fluid cells of all domains; algorithmic bytes per cell update (as tvlbm_bytes_per_cell). */
+long long tvlbm_batch_cells(const tvlbm_batch *b);
+double tvlbm_batch_bytes_per_cell(const tvlbm_batch *b);
+const char *tvlbm_batch_last_error(const tvlbm_batch *b);
 
 /* Message of the last failing call on ctx (never NULL; "" if none). */
 const char *tvlbm_last_error(const tvlbm_ctx *ctx);

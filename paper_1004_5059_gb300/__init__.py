@@ -70,6 +70,7 @@ def _load_library() -> ctypes.CDLL:
         "tvlbm_set_stream": (_I, [_P, _P]),
         "tvlbm_set_form": (_I, [_P, _I]),
         "tvlbm_set_graphs": (_I, [_P, _I]),
+        "tvlbm_set_reference": (_I, [_P, _D, _D, _D]),
         "tvlbm_tile_count": (_I, [_P]),
         "tvlbm_tile_shape": (_I, [_P, _I, _IP, _IP, _IP]),
         "tvlbm_set_tile": (_I, [_P, _I]),
@@ -85,6 +86,22 @@ def _load_library() -> ctypes.CDLL:
         "tvlbm_velocity_set": (_I, [_I, _DP, _DP, _DP, _IP]),
         "tvlbm_stream_table": (_I, [_I, _D, _IP, _IP, _DP, _DP]),
         "tvlbm_bytes_per_cell": (_D, [_P]),
+        "tvlbm_batch_memory_bytes": (_I, [_I, _IP, _IP, _I, _I, ctypes.POINTER(_SZ)]),
+        "tvlbm_batch_create_in": (_I, [_I, _IP, _IP, _DP, _I, _I, _D, _D, _P, _SZ, ctypes.POINTER(_P)]),
+        "tvlbm_batch_destroy": (_I, [_P]),
+        "tvlbm_batch_set_stream": (_I, [_P, _P]),
+        "tvlbm_batch_set_graphs": (_I, [_P, _I]),
+        "tvlbm_batch_tile_count": (_I, [_P]),
+        "tvlbm_batch_tile_shape": (_I, [_P, _I, _IP, _IP, _IP]),
+        "tvlbm_batch_set_tile": (_I, [_P, _I]),
+        "tvlbm_batch_init_moments": (_I, [_P, _I, _DP, _DP, _DP, _DP]),
+        "tvlbm_batch_step": (_I, [_P, _I]),
+        "tvlbm_batch_moments": (_I, [_P, _I, _DP, _DP, _DP, _DP]),
+        "tvlbm_batch_conserved_sums": (_I, [_P, _I, _DP]),
+        "tvlbm_batch_get_populations_f64": (_I, [_P, _I, _DP]),
+        "tvlbm_batch_cells": (ctypes.c_longlong, [_P]),
+        "tvlbm_batch_bytes_per_cell": (_D, [_P]),
+        "tvlbm_batch_last_error": (ctypes.c_char_p, [_P]),
         "tvlbm_last_error": (ctypes.c_char_p, [_P]),
         "tvlbm_strerror": (ctypes.c_char_p, [_I]),
     }
@@ -156,6 +173,10 @@ def tvlbm_set_form(ctx, form: int):
 
 def tvlbm_set_graphs(ctx, enable: bool):
     _check(_lib.tvlbm_set_graphs(ctx, 1 if enable else 0), ctx)
+
+
+def tvlbm_set_reference(ctx, ux: float, uy: float, T: float):
+    _check(_lib.tvlbm_set_reference(ctx, float(ux), float(uy), float(T)), ctx)
 
 
 def tvlbm_tile_count(ctx) -> int:
@@ -287,6 +308,9 @@ class Simulation:
     def set_tile(self, config: int):
         tvlbm_set_tile(self.ctx, config)
 
+    def set_reference(self, ux: float, uy: float, T: float):
+        tvlbm_set_reference(self.ctx, ux, uy, T)
+
     def init_moments(self, rho, ux, uy, T):
         tvlbm_init_moments(self.ctx, rho, ux, uy, T)
 
@@ -315,3 +339,102 @@ class Simulation:
 
     def bytes_per_cell(self):
         return tvlbm_bytes_per_cell(self.ctx)
+
+
+# ---- batched domains -----------------------------------------------------------------------
+
+def _bcheck(rc: int, b=None):
+    if rc != TVLBM_OK:
+        msg = _lib.tvlbm_batch_last_error(b).decode() if b else ""
+        raise TvlbmError(rc, msg or _lib.tvlbm_strerror(rc).decode())
+
+
+def tvlbm_batch_memory_bytes(nx, ny, velset, storage) -> int:
+    n = len(nx)
+    ax, ay = (np.ascontiguousarray(a, dtype=np.int32) for a in (nx, ny))
+    out = _SZ(0)
+    _bcheck(_lib.tvlbm_batch_memory_bytes(n, ax.ctypes.data_as(_IP), ay.ctypes.data_as(_IP), velset, storage,
+                                          ctypes.byref(out)))
+    return out.value
+
+
+class Batch:
+    """Independent periodic domains of different sizes and relaxation times, advanced together
+    (tvlbm_batch_*).  Device memory is a torch tensor held by this object."""
+
+    def __init__(self, nx, ny, tau, velset="D2Q16", storage="fp32_dev", dt=1.0, rho0=1.0, stream=None,
+                 graphs=True):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("TVLBM needs a CUDA GPU")
+        self.nx = np.ascontiguousarray(nx, dtype=np.int32)
+        self.ny = np.ascontiguousarray(ny, dtype=np.int32)
+        self.tau = np.ascontiguousarray(tau, dtype=np.float64)
+        self.count = len(self.nx)
+        self.velset = VELSETS[velset] if isinstance(velset, str) else int(velset)
+        self.storage = STORAGES[storage] if isinstance(storage, str) else int(storage)
+        self.Q = self.velset
+        nbytes = tvlbm_batch_memory_bytes(self.nx, self.ny, self.velset, self.storage)
+        self._mem = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        aligned = (self._mem.data_ptr() + 255) // 256 * 256
+        h = _P()
+        _bcheck(_lib.tvlbm_batch_create_in(self.count, self.nx.ctypes.data_as(_IP), self.ny.ctypes.data_as(_IP),
+                                           _dp(self.tau), self.velset, self.storage, float(dt), float(rho0),
+                                           _P(aligned), nbytes, ctypes.byref(h)))
+        self.handle = h
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = s
+        _bcheck(_lib.tvlbm_batch_set_stream(h, _P(s.cuda_stream)), h)
+        _bcheck(_lib.tvlbm_batch_set_graphs(h, 1 if graphs else 0), h)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.tvlbm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def tile_count(self) -> int:
+        return int(_lib.tvlbm_batch_tile_count(self.handle))
+
+    def tile_shape(self, config: int):
+        tx, ty, r = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _bcheck(_lib.tvlbm_batch_tile_shape(self.handle, config, ctypes.byref(tx), ctypes.byref(ty),
+                                            ctypes.byref(r)), self.handle)
+        return tx.value, ty.value, r.value
+
+    def set_tile(self, config: int):
+        _bcheck(_lib.tvlbm_batch_set_tile(self.handle, int(config)), self.handle)
+
+    def init_moments(self, d, rho, ux, uy, T):
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (rho, ux, uy, T)]
+        _bcheck(_lib.tvlbm_batch_init_moments(self.handle, int(d), *[_dp(a) for a in arrs]), self.handle)
+
+    def step(self, n=1):
+        _bcheck(_lib.tvlbm_batch_step(self.handle, int(n)), self.handle)
+
+    def moments(self, d):
+        outs = [np.empty((int(self.ny[d]), int(self.nx[d]))) for _ in range(4)]
+        _bcheck(_lib.tvlbm_batch_moments(self.handle, int(d), *[_dp(o) for o in outs]), self.handle)
+        return tuple(outs)
+
+    def conserved_sums(self, d):
+        out = np.zeros(5)
+        _bcheck(_lib.tvlbm_batch_conserved_sums(self.handle, int(d), _dp(out)), self.handle)
+        return out
+
+    def populations_f64(self, d):
+        out = np.empty((self.Q, int(self.ny[d]), int(self.nx[d])))
+        _bcheck(_lib.tvlbm_batch_get_populations_f64(self.handle, int(d), _dp(out)), self.handle)
+        return out
+
+    def cells(self) -> int:
+        return int(_lib.tvlbm_batch_cells(self.handle))
+
+    def bytes_per_cell(self) -> float:
+        return float(_lib.tvlbm_batch_bytes_per_cell(self.handle))

@@ -3,14 +3,28 @@
 // w_{n-1-i} = w_i) and with the relaxation folded into the equilibrium evaluation:
 //     d*_ij = (1 - omega) d_ij + omega d_eq_ij,
 //     omega d_eq_ij = A_i + B_j + sum_{a=1}^{N-1} X'_ia P_j,N-a          (N + 1 operations),
-// where, with X_ia = h_a(u_x) E_ia, P_jk = sum_{1<=b<=k} h_b(u_y) E_jb, SX_i = sum_{a>=1} X_ia:
+// where, with X_ia = h_a(u_x) E_ia, P_jk = sum_{1<=b<=k} h_b(u_y) E_jb, SX_i = sum_{a>=1} X_ia
+// (the separable Hermite equilibrium of cell_equilibrium, d_eq = (rho - rho0) + rho phi - Pref,
+// Pref the deviation of the storage reference, subtracted last when it is not zero):
 //     X'_ia = omega rho X_ia,  A_i = omega rho SX_i - omega c_i,
-//     B_j  = omega rho P_jN - omega c_j + omega (rho - rho0 - A0),
-// and (A0, c_i, c_j) the first-order correction that cancels the defects of the float tables
-// (see cell_equilibrium in tvlbm_kernels.cuh for the derivation; the constants here are the
-// pre-multiplied products w_i x_i and w_i x_i^2 the moment sums use, and the host evaluates
-// the defects for exactly those constants).
-// Host-callable so a CPU harness can compare it with the generic path.
+//     B_j  = omega rho P_jN - omega c_j + omega (rho - rho0 - (D_m - G)).
+//
+// Conservation in FP32.  The float constants (w_i, w_i x_i, w_i x_i^2, E_ia) miss the
+// quadrature identities they stand for -- sum w = 1, sum w x^2 = 1, sum w E_a = 0 (a >= 1), ... --
+// by ~1e-8.  Uncorrected, every collision then creates mass, momentum and energy in proportion
+// to the cell's own values, the same way every step: a drift that accumulates.  With the table
+// sums S_a = sum_i w_i E_ia, U_a = sum_i (w x)_i E_ia, V_a = sum_i (w x^2)_i E_ia and their
+// defects dS_a = S_a - [a=0], dU_a = U_a - [a=1], dV_a = V_a - [a=0] - [a=2] (evaluated exactly
+// by the host from the float constants), the moments of d_eq exceed the measured moments by, to
+// first order in the defects,
+//     D_m = 2 dS_0 m0 + rho sum_{a>=1} dS_a (h^x_a + h^y_a),
+//     D_x = rho u_x (dU_1 + dS_0) + rho sum_{a odd>=3} dU_a h^x_a + rho u_x sum_{b even} dS_b h^y_b,
+//     D_e = 2 m0 (dV_0 + dS_0) + rho sum_a (dV_a + dS_a)(h^x_a + h^y_a) + rho dS_0 (h^x_2 + h^y_2)
+//           + rho sum_b dS_b (h^x_2 h^y_b + h^y_2 h^x_b)
+// (D_y like D_x).  Subtracting c = D_m + D_x x_i + D_y x_j + G (x_i^2 + x_j^2 - 2)/2 with
+// G = D_e/2 - D_m, whose moments are (D_m, D_x, D_y, D_e) under exact quadrature, cancels the
+// drift up to second order.  A non-default storage reference adds the defect of its own float
+// table, refD, computed on the host the same way.
 #pragma once
 
 #include "tvlbm_kernels.cuh"
@@ -18,7 +32,7 @@
 namespace tvlbm {
 
 template <int N1>
-__host__ __device__ __forceinline__ void cell_collide_dev(float (&s)[N1 * N1], const KParams& p) {
+__device__ __forceinline__ void cell_collide_dev(float (&s)[N1 * N1], const KParams& p, float om) {
     constexpr int N = N1 - 1, H = N1 / 2;
     constexpr bool ODD = (N1 & 1) != 0;
     // ---- moments: rho = rho0 + sum w d, rho u = sum w c d, sum w |c|^2 d --------------------
@@ -56,9 +70,9 @@ __host__ __device__ __forceinline__ void cell_collide_dev(float (&s)[N1 * N1], c
         me = fmaf(p.wf[H], rxx[H], me);
     }
     const float rho = p.rho0f + m0;
-    const float inv = 1.0f / rho;
-    const float ux = mx * inv, uy = my * inv;
-    const float th = 0.5f * ((me - 2.0f * m0) * inv - (ux * ux + uy * uy));
+    const float inv = __frcp_rn(rho);  // correctly rounded reciprocal
+    const float ux = (p.jreff[0] + mx) * inv, uy = (p.jreff[1] + my) * inv;
+    const float th = 0.5f * ((p.ereff + me - 2.0f * m0) * inv - (ux * ux + uy * uy));
 
     // ---- Hermite coefficients of the Maxwellian, per axis ----------------------------------
     float hx[N + 1], hy[N + 1];
@@ -72,8 +86,8 @@ __host__ __device__ __forceinline__ void cell_collide_dev(float (&s)[N1 * N1], c
     }
 
     // ---- first-order cancellation of the table defects -------------------------------------
-    float Dm = 2.f * p.dS[0] * m0, De = 2.f * m0 * (p.dV[0] + p.dS[0]);
-    float Dx = rho * ux * (p.dU[1] + p.dS[0]), Dy = rho * uy * (p.dU[1] + p.dS[0]);
+    float Dm = fmaf(2.f * p.dS[0], m0, p.refD[0]), De = fmaf(2.f * m0, p.dV[0] + p.dS[0], p.refD[3]);
+    float Dx = fmaf(rho * ux, p.dU[1] + p.dS[0], p.refD[1]), Dy = fmaf(rho * uy, p.dU[1] + p.dS[0], p.refD[2]);
 #pragma unroll
     for (int a = 2; a <= N; a += 2) {  // dS, dV vanish for odd orders (mirror symmetry)
         Dm = fmaf(rho * p.dS[a], hx[a] + hy[a], Dm);
@@ -93,7 +107,7 @@ __host__ __device__ __forceinline__ void cell_collide_dev(float (&s)[N1 * N1], c
 #pragma unroll
     for (int b = 2; b <= N - 2; b += 2) De = fmaf(rho * p.dS[b], fmaf(hx[2], hy[b], hy[2] * hx[b]), De);
     const float G = 0.5f * De - Dm;
-    const float om = p.omegaf, orho = om * rho;
+    const float orho = om * rho;
 
     // ---- per-node tables: A_i (x part), B_j (y part), X'_ia, P_jk --------------------------
     float A[N1], B[N1], Xp[N1][N > 1 ? N : 1], P[N1][N + 1];
@@ -133,6 +147,10 @@ __host__ __device__ __forceinline__ void cell_collide_dev(float (&s)[N1 * N1], c
             for (int a = 1; a < N; ++a) weq = fmaf(Xp[i][a], P[j][N - a], weq);
             s[i + N1 * j] = fmaf(keep, s[i + N1 * j], weq);
         }
+    }
+    if (p.has_ref) {  // the reference's own deviation: d_eq -= Pref
+#pragma unroll
+        for (int l = 0; l < N1 * N1; ++l) s[l] = fmaf(-om, p.Preff[l], s[l]);
     }
 }
 

@@ -21,6 +21,7 @@ constexpr int kMaxQ = kMaxN1 * kMaxN1;
 constexpr int HY = 4;
 constexpr int FILL = 4;
 constexpr int kRedBlocks = 1024;  // fixed partial count of the FP64 reduction (deterministic)
+constexpr int kTileConfigs = 4;   // tile shapes of the tiled form
 
 enum Storage { ST_FP64 = 0, ST_FP32 = 1, ST_BF16_DEV = 2, ST_FP16_DEV = 3, ST_FP32_DEV = 4 };
 enum Form { FORM_PLAIN = 0, FORM_TILED = 1 };
@@ -57,6 +58,15 @@ struct KParams {
     double feqwd[2][kMaxQ];
     float inv_denf[2];
     double inv_dend[2];
+    // Deviation storage reference: d_l = f_l / w_l - R_l, R_l = f_eq_l(rho0, u_ref, T_ref) / w_l.
+    // Pref_l = R_l - rho0 (zero for the default reference: at rest, T_ref = 1), jref = rho0 u_ref,
+    // eref = rho0 (2 (T_ref - 1) + |u_ref|^2), refD = -(moments of the float Pref table under the
+    // FP32 moment constants - (0, jref, eref)), the reference's share of the table defects.
+    int has_ref;
+    float Preff[kMaxQ];
+    double Prefd[kMaxQ];
+    float jreff[2], ereff, refD[4];
+    double jrefd[2], erefd;
     // Device status word: bit 0 is set by a kernel whose bounded wait gave up.
     int* status;
 };
@@ -64,6 +74,27 @@ struct KParams {
 template <class R> __device__ __forceinline__ R kx(const KParams& p, int i) {
     if constexpr (std::is_same<R, double>::value) return p.xd[i]; else return p.xf[i];
 }
+// Geometry and relaxation of one domain.  A single-domain launch takes it from KParams; the
+// batched launch reads it from a per-domain table.
+struct Geom {
+    int nx, ny, pitch, hx, walls;
+    long long plane;
+    float omegaf;
+    double omegad;
+};
+__host__ __device__ __forceinline__ Geom geom_of(const KParams& p) {
+    Geom g;
+    g.nx = p.nx;
+    g.ny = p.ny;
+    g.pitch = p.pitch;
+    g.hx = p.hx;
+    g.walls = p.walls;
+    g.plane = p.plane;
+    g.omegaf = p.omegaf;
+    g.omegad = p.omegad;
+    return g;
+}
+
 template <class R> __device__ __forceinline__ R kx2(const KParams& p, int i) {
     if constexpr (std::is_same<R, double>::value) return p.xd[i] * p.xd[i]; else return p.x2f[i];
 }
@@ -82,6 +113,15 @@ template <class R> __device__ __forceinline__ R komega(const KParams& p) {
 template <class R> __device__ __forceinline__ R krho0(const KParams& p) {
     if constexpr (std::is_same<R, double>::value) return p.rho0d; else return p.rho0f;
 }
+template <class R> __device__ __forceinline__ R kPref(const KParams& p, int l) {
+    if constexpr (std::is_same<R, double>::value) return p.Prefd[l]; else return p.Preff[l];
+}
+template <class R> __device__ __forceinline__ R kjref(const KParams& p, int k) {
+    if constexpr (std::is_same<R, double>::value) return p.jrefd[k]; else return p.jreff[k];
+}
+template <class R> __device__ __forceinline__ R keref(const KParams& p) {
+    if constexpr (std::is_same<R, double>::value) return p.erefd; else return p.ereff;
+}
 template <class R> __device__ __forceinline__ R kfeqw(const KParams& p, int side, int l) {
     if constexpr (std::is_same<R, double>::value) return p.feqwd[side][l]; else return p.feqwf[side][l];
 }
@@ -90,7 +130,8 @@ template <class R> __device__ __forceinline__ R kinvden(const KParams& p, int si
 }
 
 // ---- storage codecs ----------------------------------------------------------------------
-// Full codecs store f_l; deviation codecs store d_l = f_l / w_l - rho0.  Sweep arithmetic runs
+// Full codecs store f_l; deviation codecs store d_l = f_l / w_l - R_l (R_l = rho0 for the default
+// reference, see KParams).  Sweep arithmetic runs
 // in "storage space" (the stored quantity), so the gather and the BGK update are linear in
 // what is loaded and stored; moments and equilibrium know which space they are in.
 struct CodecF64 {
@@ -120,18 +161,18 @@ struct CodecF16Dev {
 };
 
 // Storage value -> f_l and back, in precision R (used off the hot path: init, moments,
-// reductions, walls).
+// reductions, walls); ref = R_l, the deviation reference of velocity l.
 template <class C, class R>
-__device__ __forceinline__ R to_f(R v, R w, R rho0) { if constexpr (C::dev) return w * (rho0 + v); else return v; }
+__device__ __forceinline__ R to_f(R v, R w, R ref) { if constexpr (C::dev) return w * (ref + v); else return v; }
 template <class C, class R>
-__device__ __forceinline__ R from_f(R f, R w, R rho0) { if constexpr (C::dev) return f / w - rho0; else return f; }
+__device__ __forceinline__ R from_f(R f, R w, R ref) { if constexpr (C::dev) return f / w - ref; else return f; }
 
 // ---- moments, equilibrium, BGK on one cell -----------------------------------------------
 // s[l], l = i + N1 j, holds the cell's (gathered) populations in storage space.
 // Moments (Sec. "The TVLBM model"): rho = sum f, rho u = sum c f, D rho T + rho u^2 = sum |c|^2 f
-// with D = 2.  In deviation space f = w (rho0 + d), and sum w = 1, sum w c = 0, sum w |c|^2 = D
-// (exact quadrature), so rho = rho0 + sum w d, rho u = sum w c d, and
-// T - 1 = ((sum w |c|^2 d - D sum w d)/rho - u^2)/D.
+// with D = 2.  In deviation space f = w (R + d) with R the reference's f_eq / w, whose moments
+// are (rho0, rho0 u_ref, rho0 (D T_ref + u_ref^2)) by exact quadrature, so rho = rho0 + sum w d,
+// rho u = jref + sum w c d, and T - 1 = ((eref + sum w |c|^2 d - D sum w d)/rho - u^2)/D.
 template <int N1, bool DEV, class R>
 __device__ __forceinline__ void cell_moments(const R (&s)[N1 * N1], const KParams& p, R& rho, R& ux, R& uy, R& th) {
     R m0 = 0, mx = 0, my = 0, me = 0;
@@ -156,9 +197,9 @@ __device__ __forceinline__ void cell_moments(const R (&s)[N1 * N1], const KParam
     if constexpr (DEV) {
         rho = krho0<R>(p) + m0;
         const R inv = R(1) / rho;
-        ux = mx * inv;
-        uy = my * inv;
-        th = R(0.5) * ((me - R(2) * m0) * inv - (ux * ux + uy * uy));
+        ux = (kjref<R>(p, 0) + mx) * inv;
+        uy = (kjref<R>(p, 1) + my) * inv;
+        th = R(0.5) * ((keref<R>(p) + me - R(2) * m0) * inv - (ux * ux + uy * uy));
     } else {
         rho = m0;
         const R inv = R(1) / rho;
@@ -174,7 +215,7 @@ __device__ __forceinline__ void cell_moments(const R (&s)[N1 * N1], const KParam
 // h_0 = 1, h_1 = u, h_{n+1} = u h_n + n (T-1) h_{n-1}  (the Gaussian moments E[He_n(u+sqrt(T) Z)]).
 // With X_ia = h_a(u_x) E_ia (X_i0 = 1), P_jk = sum_{1<=b<=k} h_b(u_y) E_jb:
 //   sum_{a+b<=N} X_ia Y_jb = 1 + phi_ij,  phi_ij = sum_{a>=1} X_ia + sum_{a<N} X_ia P_j,N-a.
-// Storage-space equilibrium: full f_eq = w rho (1 + phi); deviation d_eq = (rho - rho0) + rho phi.
+// Storage-space equilibrium: full f_eq = w rho (1 + phi); deviation d_eq = (rho - rho0) + rho phi - Pref.
 template <int N1, bool DEV, class R>
 __device__ __forceinline__ void cell_equilibrium(const KParams& p, R rho, R ux, R uy, R th, R (&eq)[N1 * N1]) {
     constexpr int N = N1 - 1;
@@ -208,7 +249,7 @@ __device__ __forceinline__ void cell_equilibrium(const KParams& p, R rho, R ux, 
             R phi = SX[i] + P[j][N];  // a = 0 term: X_i0 = 1
 #pragma unroll
             for (int a = 1; a < N; ++a) phi = fma(X[i][a], P[j][N - a], phi);
-            if constexpr (DEV) eq[i + N1 * j] = fma(rho, phi, drho);
+            if constexpr (DEV) eq[i + N1 * j] = fma(rho, phi, drho) - kPref<R>(p, i + N1 * j);
             else eq[i + N1 * j] = (kw<R>(p, i) * kw<R>(p, j) * rho) * (R(1) + phi);
         }
     }
@@ -216,14 +257,24 @@ __device__ __forceinline__ void cell_equilibrium(const KParams& p, R rho, R ux, 
 
 // Moments -> equilibrium -> BGK relaxation s* = s + (dt/tau)(s_eq - s), in place.
 template <int N1, bool DEV, class R>
-__device__ __forceinline__ void cell_collide(R (&s)[N1 * N1], const KParams& p) {
+__device__ __forceinline__ void cell_collide(R (&s)[N1 * N1], const KParams& p, R om) {
     R rho, ux, uy, th;
     cell_moments<N1, DEV, R>(s, p, rho, ux, uy, th);
     R eq[N1 * N1];
     cell_equilibrium<N1, DEV, R>(p, rho, ux, uy, th, eq);
-    const R om = komega<R>(p);
 #pragma unroll
     for (int l = 0; l < N1 * N1; ++l) s[l] = fma(om, eq[l] - s[l], s[l]);
+}
+
+// Explicit global-space stores and loads: the population buffers are always global memory, and
+// saying so keeps generic accesses (which could alias shared memory) out of the sweeps.
+__device__ __forceinline__ void stg(float* p, float v) { asm volatile("st.global.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory"); }
+__device__ __forceinline__ void stg(double* p, double v) { asm volatile("st.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory"); }
+__device__ __forceinline__ void stg(__half* p, __half v) {
+    asm volatile("st.global.b16 [%0], %1;" ::"l"(p), "h"(__half_as_ushort(v)) : "memory");
+}
+__device__ __forceinline__ void stg(__nv_bfloat16* p, __nv_bfloat16 v) {
+    asm volatile("st.global.b16 [%0], %1;" ::"l"(p), "h"(__bfloat16_as_ushort(v)) : "memory");
 }
 
 // Padded storage index of fluid cell (x, y) in velocity plane l (x, y may lie in the frame).
@@ -234,22 +285,35 @@ __device__ __forceinline__ long long sidx(const KParams& p, int l, int x, int y)
 // Store v at fluid cell (x, y) and at every periodic image of it inside the read frame
 // (x in [-FILL, nx+FILL); y likewise when periodic in y).
 template <class T>
-__device__ __forceinline__ void store_with_images(T* f, const KParams& p, long long lbase, int x, int y, T v) {
-    const int x0 = x - p.nx * ((x + FILL) / p.nx);
-    if (p.walls) {
-        for (int xx = x0; xx < p.nx + FILL; xx += p.nx) f[lbase + (long long)(y + HY) * p.pitch + (xx + p.hx)] = v;
+__device__ __forceinline__ void store_with_images(T* f, const Geom& g, long long lbase, int x, int y, T v) {
+    const int x0 = x - g.nx * ((x + FILL) / g.nx);
+    if (g.walls) {
+        for (int xx = x0; xx < g.nx + FILL; xx += g.nx) stg(f + lbase + (long long)(y + HY) * g.pitch + (xx + g.hx), v);
     } else {
-        const int y0 = y - p.ny * ((y + FILL) / p.ny);
-        for (int yy = y0; yy < p.ny + FILL; yy += p.ny)
-            for (int xx = x0; xx < p.nx + FILL; xx += p.nx) f[lbase + (long long)(yy + HY) * p.pitch + (xx + p.hx)] = v;
+        const int y0 = y - g.ny * ((y + FILL) / g.ny);
+        for (int yy = y0; yy < g.ny + FILL; yy += g.ny)
+            for (int xx = x0; xx < g.nx + FILL; xx += g.nx) stg(f + lbase + (long long)(yy + HY) * g.pitch + (xx + g.hx), v);
     }
 }
 
+// TMA descriptors (CUtensorMap) of a tiled sweep: input windows (out: reserved, may be null).
+struct SweepMaps {
+    const void* in;
+    const void* out;
+};
+
+struct BatchSrc;  // tile source of the batched sweep (tvlbm_tiled.cuh)
+
+// Per-velocity change of the deviation reference: d_l += delta_l re-expresses stored
+// populations against a new reference.
+struct RefShift {
+    float delta[kMaxQ];
+};
+
 // ---- kernel table (one per N1, defined in tvlbm_kernels_q*.cu) ----------------------------
 struct KernelTable {
-    // tmap: TMA descriptor (CUtensorMap) of fin, used by the tiled form
-    // cfg: tile configuration of the tiled form (0 .. kTileConfigs-1)
-    cudaError_t (*sweep)(int storage, int form, int cfg, const void* fin, void* fout, const void* tmap,
+    // maps: TMA descriptors of the tiled form; cfg: its tile configuration (0 .. kTileConfigs-1)
+    cudaError_t (*sweep)(int storage, int form, int cfg, const void* fin, void* fout, const SweepMaps* maps,
                          const KParams& p, cudaStream_t s);
     cudaError_t (*init)(int storage, const double* fields, void* f, const KParams& p, cudaStream_t s);
     cudaError_t (*moments)(int storage, const void* f, double* out4, const KParams& p, cudaStream_t s);
@@ -261,6 +325,10 @@ struct KernelTable {
     int (*tiled_available)(int storage);
     void (*tiled_box)(int storage, int cfg, int* bx, int* by);  // TMA box (elements) of a tile config
     void (*tile_shape)(int storage, int cfg, int* tx, int* ty, int* rows_per_thread);
+    // re-express every stored element of buffer f against a new deviation reference
+    cudaError_t (*reencode)(int storage, void* f, const RefShift& shift, const KParams& p, cudaStream_t s);
+    // one time step of every domain of a batch (persistent launch over all tiles)
+    cudaError_t (*batch_sweep)(int storage, int cfg, const BatchSrc& src, const KParams& p, cudaStream_t s);
 };
 
 const KernelTable* kernel_table_q3();

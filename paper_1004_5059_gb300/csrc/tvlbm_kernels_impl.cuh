@@ -41,8 +41,9 @@ __global__ void __launch_bounds__(256) sweep_plain_kernel(const typename C::T* _
             s[i + N1 * j] = fma(ay, r1 - r0, r0);
         }
     }
-    collide_cell<N1, C>(s, p);
-    store_collided<N1, C>(fout, p, x, y, s);
+    const Geom g = geom_of(p);
+    collide_cell<N1, C>(s, p, g);
+    store_collided<N1, C>(fout, g, x, y, s);
 }
 
 // =============================================================================================
@@ -60,7 +61,9 @@ __global__ void init_kernel(const double* __restrict__ fields, typename C::T* __
     double eq[Q];
     cell_equilibrium<N1, C::dev, double>(p, rho, ux, uy, T - 1.0, eq);
 #pragma unroll
-    for (int l = 0; l < Q; ++l) store_with_images(f, p, (long long)l * p.plane, x, y, C::enc((typename C::R)eq[l]));
+    const Geom g = geom_of(p);
+#pragma unroll
+    for (int l = 0; l < Q; ++l) store_with_images(f, g, (long long)l * p.plane, x, y, C::enc((typename C::R)eq[l]));
 }
 
 // =============================================================================================
@@ -111,7 +114,7 @@ __global__ void __launch_bounds__(256) reduce_kernel(const typename C::T* __rest
             for (int i = 0; i < N1; ++i) {
                 const double v = (double)C::ld(f + sidx(p, i + N1 * j, x, y));
                 acc[4] += isfinite(v) ? 0.0 : 1.0;
-                const double fv = to_f<C, double>(v, p.wd[i] * p.wd[j], p.rho0d);
+                const double fv = to_f<C, double>(v, p.wd[i] * p.wd[j], p.rho0d + p.Prefd[i + N1 * j]);
                 r += fv;
                 rx += p.xd[i] * fv;
                 rxx += p.xd[i] * p.xd[i] * fv;
@@ -199,7 +202,7 @@ __global__ void wall_kernel(typename C::T* __restrict__ f, const KParams p) {
                     for (int pp = 0; pp < 2; ++pp) {
                         const int xs = x - p.sh[i] - pp;
                         const R wx = pp ? ax : R(1) - ax;
-                        acc += wx * wy * to_f<C, R>(C::ld(f + sidx(p, l, xs, ys)), w, rho0);
+                        acc += wx * wy * to_f<C, R>(C::ld(f + sidx(p, l, xs, ys)), w, rho0 + kPref<R>(p, l));
                     }
                 }
                 mout += acc;
@@ -216,7 +219,7 @@ __global__ void wall_kernel(typename C::T* __restrict__ f, const KParams p) {
         for (int i = 0; i < N1; ++i) {
             const int l = i + N1 * j;
             const R w = kw<R>(p, i) * kw<R>(p, j);
-            const typename C::T v = C::enc(from_f<C, R>(A * kfeqw<R>(p, side, l), w, rho0));
+            const typename C::T v = C::enc(from_f<C, R>(A * kfeqw<R>(p, side, l), w, rho0 + kPref<R>(p, l)));
             for (int d = 1; d <= HY; ++d) {
                 const int yd = side == 0 ? -d : p.ny - 1 + d;
                 f[sidx(p, l, xo, yd)] = v;
@@ -244,6 +247,16 @@ __global__ void halo_kernel(T* __restrict__ f, const KParams p, int Q) {
     }
 }
 
+// d_l += delta_l on every stored element (fluid and frame) of a deviation-coded buffer.
+template <class C>
+__global__ void reencode_kernel(typename C::T* __restrict__ f, long long plane, int Q, const RefShift sh) {
+    const long long n = plane * Q;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const int l = (int)(t / plane);
+        f[t] = C::enc(C::ld(f + t) + sh.delta[l]);
+    }
+}
+
 // Decode one velocity plane to FP64 f_l (packed [ny][nx]) / encode FP64 f_l into storage.
 template <class C>
 __global__ void decode_plane_kernel(const typename C::T* __restrict__ f, int l, int n1, double* __restrict__ out,
@@ -251,7 +264,7 @@ __global__ void decode_plane_kernel(const typename C::T* __restrict__ f, int l, 
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= p.nx || y >= p.ny) return;
     const double w = p.wd[l % n1] * p.wd[l / n1];
-    out[(long long)y * p.nx + x] = to_f<C, double>((double)C::ld(f + sidx(p, l, x, y)), w, p.rho0d);
+    out[(long long)y * p.nx + x] = to_f<C, double>((double)C::ld(f + sidx(p, l, x, y)), w, p.rho0d + p.Prefd[l]);
 }
 template <class C>
 __global__ void encode_plane_kernel(typename C::T* __restrict__ f, int l, int n1, const double* __restrict__ in,
@@ -259,7 +272,7 @@ __global__ void encode_plane_kernel(typename C::T* __restrict__ f, int l, int n1
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= p.nx || y >= p.ny) return;
     const double w = p.wd[l % n1] * p.wd[l / n1];
-    f[sidx(p, l, x, y)] = C::enc((typename C::R)from_f<C, double>(in[(long long)y * p.nx + x], w, p.rho0d));
+    f[sidx(p, l, x, y)] = C::enc((typename C::R)from_f<C, double>(in[(long long)y * p.nx + x], w, p.rho0d + p.Prefd[l]));
 }
 
 // =============================================================================================
@@ -270,10 +283,10 @@ struct Launch {
     static dim3 grid2d(const KParams& p, dim3 b) { return dim3((p.nx + b.x - 1) / b.x, (p.ny + b.y - 1) / b.y); }
 
     template <class C>
-    static cudaError_t sweep_c(int form, int cfg, const void* fin, void* fout, const void* tmap, const KParams& p,
+    static cudaError_t sweep_c(int form, int cfg, const void* fin, void* fout, const SweepMaps* maps, const KParams& p,
                                cudaStream_t s) {
         using T = typename C::T;
-        if (form == FORM_TILED) return tiled_sweep<N1, C>(cfg, (const CUtensorMap*)tmap, (T*)fout, p, s);
+        if (form == FORM_TILED) return tiled_sweep<N1, C>(cfg, maps, (T*)fout, p, s);
         const dim3 b(32, 8);
         sweep_plain_kernel<N1, C><<<grid2d(p, b), b, 0, s>>>((const T*)fin, (T*)fout, p);
         return cudaGetLastError();
@@ -308,6 +321,12 @@ struct Launch {
         return cudaGetLastError();
     }
     template <class C>
+    static cudaError_t reencode_c(void* f, const RefShift& sh, const KParams& p, cudaStream_t s) {
+        if constexpr (!C::dev) return cudaErrorInvalidValue;
+        reencode_kernel<C><<<1024, 256, 0, s>>>((typename C::T*)f, p.plane, N1 * N1, sh);
+        return cudaGetLastError();
+    }
+    template <class C>
     static cudaError_t decode_c(const void* f, int l, double* out, const KParams& p, cudaStream_t s) {
         const dim3 b(32, 8);
         decode_plane_kernel<C><<<grid2d(p, b), b, 0, s>>>((const typename C::T*)f, l, N1, out, p);
@@ -330,9 +349,9 @@ struct Launch {
         default: return cudaErrorInvalidValue;                  \
     }
 
-    static cudaError_t sweep(int storage, int form, int cfg, const void* fin, void* fout, const void* tmap,
+    static cudaError_t sweep(int storage, int form, int cfg, const void* fin, void* fout, const SweepMaps* maps,
                              const KParams& p, cudaStream_t s) {
-        TVLBM_DISPATCH(sweep_c, (form, cfg, fin, fout, tmap, p, s))
+        TVLBM_DISPATCH(sweep_c, (form, cfg, fin, fout, maps, p, s))
     }
     static cudaError_t init(int storage, const double* fields, void* f, const KParams& p, cudaStream_t s) {
         TVLBM_DISPATCH(init_c, (fields, f, p, s))
@@ -363,16 +382,29 @@ struct Launch {
     }
     static void shape(int storage, int cfg, int* tx, int* ty, int* r) {
         const int es = storage == ST_FP64 ? 8 : (storage == ST_BF16_DEV || storage == ST_FP16_DEV) ? 2 : 4;
-        const TileShape t = tile_shape(es, cfg);
+        const TileShape t = tile_shape(N1 * N1, es, cfg);
         *tx = t.tx;
         *ty = t.ty;
         *r = t.ty / t.rs;
+    }
+    static cudaError_t reencode(int storage, void* f, const RefShift& sh, const KParams& p, cudaStream_t s) {
+        TVLBM_DISPATCH(reencode_c, (f, sh, p, s))
+    }
+    static cudaError_t batch(int storage, int cfg, const BatchSrc& src, const KParams& p, cudaStream_t s) {
+        switch (storage) {
+            case ST_FP64: return batch_sweep<N1, CodecF64>(cfg, src, p, s);
+            case ST_FP32: return batch_sweep<N1, CodecF32>(cfg, src, p, s);
+            case ST_BF16_DEV: return batch_sweep<N1, CodecBF16Dev>(cfg, src, p, s);
+            case ST_FP16_DEV: return batch_sweep<N1, CodecF16Dev>(cfg, src, p, s);
+            case ST_FP32_DEV: return batch_sweep<N1, CodecF32Dev>(cfg, src, p, s);
+            default: return cudaErrorInvalidValue;
+        }
     }
 #undef TVLBM_DISPATCH
 
     static const KernelTable* table() {
         static const KernelTable t = {&sweep, &init, &moments, &reduce, &wall, &halo, &decode, &encode, &tiled_available,
-                                      &box, &shape};
+                                      &box, &shape, &reencode, &batch};
         return &t;
     }
 };

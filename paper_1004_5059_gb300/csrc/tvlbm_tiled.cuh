@@ -18,36 +18,45 @@ namespace tvlbm {
 
 // ---- tile shapes ---------------------------------------------------------------------------
 // (TX, TY, RS): tile width, tile height, row segments (threads per column); R = TY / RS rows
-// per thread.  FP64 uses half-width tiles.
-constexpr int kTileConfigs = 4;
+// per thread.  Shared memory per CTA = Q input windows.
 struct TileShape {
     int tx, ty, rs;
 };
-__host__ __device__ constexpr TileShape tile_shape(int es, int cfg) {
-    return es == 8 ? (cfg == 0   ? TileShape{32, 16, 4}
-                      : cfg == 1 ? TileShape{32, 8, 4}
-                      : cfg == 2 ? TileShape{64, 8, 2}
-                                 : TileShape{32, 16, 2})
-                   : (cfg == 0   ? TileShape{64, 16, 4}
-                      : cfg == 1 ? TileShape{64, 8, 4}
-                      : cfg == 2 ? TileShape{128, 8, 2}
+__host__ __device__ constexpr TileShape tile_shape_base(int es, int cfg) {
+    return es == 8 ? (cfg == 0   ? TileShape{32, 8, 4}
+                      : cfg == 1 ? TileShape{32, 4, 2}
+                      : cfg == 2 ? TileShape{32, 8, 2}
+                                 : TileShape{32, 4, 4})
+                   : (cfg == 0   ? TileShape{64, 8, 4}
+                      : cfg == 1 ? TileShape{64, 16, 4}
+                      : cfg == 2 ? TileShape{32, 8, 4}
                                  : TileShape{32, 16, 4});
+}
+__host__ __device__ constexpr int tile_smem(int q, int es, TileShape t) {
+    return q * (((t.tx + 16 / es) * (t.ty + 1) * es + 127) / 128 * 128) + 8 * q + 128;
+}
+// A shape whose windows do not fit in shared memory is halved in height.
+__host__ __device__ constexpr TileShape tile_shape(int q, int es, int cfg) {
+    return tile_smem(q, es, tile_shape_base(es, cfg)) <= 227 * 1024
+               ? tile_shape_base(es, cfg)
+               : TileShape{tile_shape_base(es, cfg).tx, tile_shape_base(es, cfg).ty / 2,
+                           tile_shape_base(es, cfg).rs / 2};
 }
 
 template <int N1, class C, int CFG>
 struct TileCfg {
     static constexpr int ES = (int)sizeof(typename C::T);
+    static constexpr int Q = N1 * N1;
     static constexpr int A = 16 / ES;  // TMA x coordinates must be 16-byte multiples
-    static constexpr int TX = tile_shape(ES, CFG).tx;
-    static constexpr int TY = tile_shape(ES, CFG).ty;
-    static constexpr int RS = tile_shape(ES, CFG).rs;
+    static constexpr int TX = tile_shape(Q, ES, CFG).tx;
+    static constexpr int TY = tile_shape(Q, ES, CFG).ty;
+    static constexpr int RS = tile_shape(Q, ES, CFG).rs;
     static constexpr int R = TY / RS;
     static constexpr int THREADS = TX * RS;
     static constexpr int BX = TX + A;  // window width: TX + 1 cells plus alignment slack
     static constexpr int BY = TY + 1;
     static constexpr int WIN_BYTES = (BX * BY * ES + 127) / 128 * 128;
-    static constexpr int Q = N1 * N1;
-    static constexpr int SMEM = Q * WIN_BYTES + 8 * Q + 128;  // windows, barriers, alignment slack
+    static constexpr int SMEM = Q * WIN_BYTES + 8 * Q + 128;  // windows, Q barriers, alignment slack
     static_assert(SMEM <= 227 * 1024, "tile windows exceed shared memory");
 };
 
@@ -110,84 +119,159 @@ constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s: a TMA load never takes
 
 // Periodic frame images of the value already stored at fluid cell (x, y) of plane lbase.
 template <class T>
-__device__ __forceinline__ void store_images_of(T* f, const KParams& p, long long lbase, int x, int y) {
-    const T v = f[lbase + (long long)(y + HY) * p.pitch + (x + p.hx)];
-    const int x0 = x - p.nx * ((x + FILL) / p.nx);
-    const int y0 = p.walls ? y : y - p.ny * ((y + FILL) / p.ny);
-    const int y1 = p.walls ? y + 1 : p.ny + FILL;
-    for (int yy = y0; yy < y1; yy += p.ny)
-        for (int xx = x0; xx < p.nx + FILL; xx += p.nx)
-            if (xx != x || yy != y) f[lbase + (long long)(yy + HY) * p.pitch + (xx + p.hx)] = v;
+__device__ __forceinline__ void store_images_of(T* f, const Geom& g, long long lbase, int x, int y) {
+    const T v = f[lbase + (long long)(y + HY) * g.pitch + (x + g.hx)];
+    const int x0 = x - g.nx * ((x + FILL) / g.nx);
+    const int y0 = g.walls ? y : y - g.ny * ((y + FILL) / g.ny);
+    const int y1 = g.walls ? y + 1 : g.ny + FILL;
+    for (int yy = y0; yy < y1; yy += g.ny)
+        for (int xx = x0; xx < g.nx + FILL; xx += g.nx)
+            if (xx != x || yy != y) stg(f + lbase + (long long)(yy + HY) * g.pitch + (xx + g.hx), v);
 }
 
-// Collision of one gathered cell in the codec's arithmetic.
+// Collision of one gathered cell in the codec's arithmetic, relaxation rate of the domain.
 template <int N1, class C>
-__device__ __forceinline__ void collide_cell(typename C::R (&s)[N1 * N1], const KParams& p) {
-    if constexpr (C::dev) cell_collide_dev<N1>(s, p);
-    else cell_collide<N1, false, typename C::R>(s, p);
+__device__ __forceinline__ void collide_cell(typename C::R (&s)[N1 * N1], const KParams& p, const Geom& g) {
+    if constexpr (C::dev) cell_collide_dev<N1>(s, p, g.omegaf);
+    else if constexpr (std::is_same<typename C::R, double>::value) cell_collide<N1, false, double>(s, p, g.omegad);
+    else cell_collide<N1, false, float>(s, p, g.omegaf);
 }
 
 // Store one collided cell: plain stores, then (cells within FILL of a periodic edge) the images.
 template <int N1, class C>
-__device__ __forceinline__ void store_collided(typename C::T* f, const KParams& p, int x, int y,
+__device__ __forceinline__ void store_collided(typename C::T* f, const Geom& g, int x, int y,
                                                const typename C::R (&s)[N1 * N1]) {
-    const long long c = (long long)(y + HY) * p.pitch + (x + p.hx);
+    typename C::T* q = f + ((long long)(y + HY) * g.pitch + (x + g.hx));
 #pragma unroll
-    for (int l = 0; l < N1 * N1; ++l) f[(long long)l * p.plane + c] = C::enc(s[l]);
-    const bool edge = x < FILL || x >= p.nx - FILL || (!p.walls && (y < FILL || y >= p.ny - FILL));
+    for (int l = 0; l < N1 * N1; ++l) {
+        stg(q, C::enc(s[l]));
+        q += g.plane;
+    }
+    const bool edge = x < FILL || x >= g.nx - FILL || (!g.walls && (y < FILL || y >= g.ny - FILL));
     if (edge) {
 #pragma unroll 1
-        for (int l = 0; l < N1 * N1; ++l) store_images_of(f, p, (long long)l * p.plane, x, y);
+        for (int l = 0; l < N1 * N1; ++l) store_images_of(f, g, (long long)l * g.plane, x, y);
     }
 }
 
-template <int N1, class C, int CFG>
+// ---- tile sources: where tile t lives --------------------------------------------------------
+// One domain: tiles in row-major order over a tiles_x-wide grid; the input descriptor is a
+// kernel parameter.
+struct SingleSrc {
+    CUtensorMap map_in;
+    void* fout;
+    int tiles_x, ntiles;
+    __device__ __forceinline__ void tile(int t, const KParams& p, int tx, int ty, int& x0, int& y0,
+                                         const CUtensorMap*& map, void*& out, Geom& g) const {
+        x0 = (t % tiles_x) * tx;
+        y0 = (t / tiles_x) * ty;
+        map = &map_in;
+        out = fout;
+        g = geom_of(p);
+    }
+};
+
+// Many domains (see tvlbm_batch.cu): a per-tile domain index, a per-domain table and two
+// descriptors per domain in global memory.
+struct BatchDomain {
+    long long off[2];  // element offsets of the two population buffers from the batch base
+    long long plane;
+    int nx, ny, pitch, tiles_x, tile_begin, pad;
+    float omegaf;
+    double omegad;
+};
+struct BatchSrc {
+    const BatchDomain* dom;
+    const CUtensorMap* maps;  // [domain][buffer]
+    const int* tile_dom;
+    unsigned char* base;
+    int ntiles, parity, es;
+    __device__ __forceinline__ void tile(int t, const KParams& p, int tx, int ty, int& x0, int& y0,
+                                         const CUtensorMap*& map, void*& out, Geom& g) const {
+        const int d = __ldg(tile_dom + t);
+        const BatchDomain& D = dom[d];
+        const int local = t - D.tile_begin;
+        x0 = (local % D.tiles_x) * tx;
+        y0 = (local / D.tiles_x) * ty;
+        map = maps + 2 * d + parity;
+        out = base + D.off[parity ^ 1] * es;
+        g.nx = D.nx;
+        g.ny = D.ny;
+        g.pitch = D.pitch;
+        g.hx = p.hx;
+        g.walls = 0;
+        g.plane = D.plane;
+        g.omegaf = D.omegaf;
+        g.omegad = D.omegad;
+    }
+};
+
+// Tiled sweep: CTA b owns tile b.  Thread 0 starts the Q window loads; warp 0 then waits for
+// them, lane l watching barrier l (and l + 32), while the other warps sleep at the block
+// barrier.  Each thread walks R rows of one column (x-lerp of the previous row carried in
+// registers), collides and stores straight to global memory.  Every wait is bounded; a timeout
+// sets the status word and the CTA returns after a bounded drain of its own loads.
+template <int N1, class C, int CFG, class Src>
 __global__ void __launch_bounds__(TileCfg<N1, C, CFG>::THREADS)
-    sweep_tiled_kernel(const __grid_constant__ CUtensorMap tmap, typename C::T* __restrict__ fout, const KParams p) {
+    sweep_tiled_kernel(const __grid_constant__ Src src, const KParams p) {
     using Cfg = TileCfg<N1, C, CFG>;
     using R = typename C::R;
+    using T = typename C::T;
     constexpr int Q = N1 * N1, TX = Cfg::TX, TY = Cfg::TY, RR = Cfg::R, BX = Cfg::BX, A = Cfg::A, ES = Cfg::ES;
     constexpr int WIN = Cfg::WIN_BYTES;
-    extern __shared__ unsigned char smem_raw[];
-    unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
-    uint64_t* bars = (uint64_t*)(base + Q * WIN);
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // 128-byte aligned base, derived from smem_raw by pointer arithmetic so the compiler keeps
+    // the shared address space (window reads compile to shared-memory loads)
+    unsigned char* base = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base + Q * WIN);
+    __shared__ int tile_ok;
     const int tid = threadIdx.x;
+    const int t = blockIdx.x;
+
+    int x0, y0;
+    const CUtensorMap* map;
+    void* outv;
+    Geom g;
+    src.tile(t, p, TX, TY, x0, y0, map, outv, g);
 
     if (tid == 0) {
 #pragma unroll 1
         for (int l = 0; l < Q; ++l) mbar_init(&bars[l], 1);
         fence_barrier_init();
-    }
-    __syncthreads();
-    if (tid == 0) {
-#pragma unroll 1
+#pragma unroll
         for (int l = 0; l < Q; ++l) {
             const int i = l % N1, j = l / N1;
-            const int xs = x0 + p.hx - p.sh[i] - 1;
-            const int ys = y0 + HY - p.sh[j] - 1;
             mbar_arrive_expect_tx(&bars[l], (uint32_t)(BX * Cfg::BY * ES));
-            tma_load_3d(base + l * WIN, &tmap, &bars[l], xs & ~(A - 1), ys, l);
+            tma_load_3d(base + l * WIN, map, &bars[l], (x0 + g.hx - p.sh[i] - 1) & ~(A - 1), y0 + HY - p.sh[j] - 1, l);
         }
     }
-    bool ok = true;
+    if (tid < 32) {
+        bool ok = true;
 #pragma unroll 1
-    for (int l = 0; l < Q && ok; ++l) ok = mbar_wait_bounded(&bars[l], 0, kWaitLimitNs);
-    if (!ok) {
-        // A window never arrived: report it, give the other loads a bounded chance to land
-        // (so no copy is still writing this CTA's shared memory), store nothing.
-        if (p.status) atomicOr(p.status, 1);
+        for (int l = tid; l < Q; l += 32) ok = ok && mbar_wait_bounded(&bars[l], 0, kWaitLimitNs);
+        ok = __all_sync(0xffffffffu, ok);
+        if (tid == 0) tile_ok = ok ? 1 : 0;
+    }
+    __syncthreads();
+    if (!tile_ok) {
+        // A window never arrived: report it, give the loads a bounded chance to land (so no copy
+        // still writes this CTA's shared memory), store nothing.
+        if (tid == 0) {
+            if (p.status) atomicOr(p.status, 1);
 #pragma unroll 1
-        for (int l = 0; l < Q; ++l) mbar_wait_bounded(&bars[l], 0, kWaitLimitNs);
+            for (int l = 0; l < Q; ++l) mbar_wait_bounded(&bars[l], 0, kWaitLimitNs);
+        }
         return;
     }
 
+    T* fout = reinterpret_cast<T*>(outv);
     const int cx = tid % TX, r0 = (tid / TX) * RR;
     const int x = x0 + cx;
-    // byte offset of column (cx + alignment remainder) within a window row, per x-node
+    // byte offset of column (cx + alignment remainder) within a window row, per x-node; the tile
+    // origin is a multiple of TX (>= A), so the remainder depends on the node only
     int off[N1];
 #pragma unroll
-    for (int i = 0; i < N1; ++i) off[i] = (cx + ((x0 + p.hx - p.sh[i] - 1) & (A - 1))) * ES;
+    for (int i = 0; i < N1; ++i) off[i] = (cx + ((g.hx - p.sh[i] - 1) & (A - 1))) * ES;
     const unsigned char* wrow = base + r0 * BX * ES;
     R hprev[Q];
 #pragma unroll
@@ -199,7 +283,7 @@ __global__ void __launch_bounds__(TileCfg<N1, C, CFG>::THREADS)
             hprev[i + N1 * j] = fma(ka<R>(p, i), b - a, a);
         }
 #pragma unroll 1
-    for (int k = 0; k < RR; ++k) {
+    for (int kk = 0; kk < RR; ++kk) {
         wrow += BX * ES;
         R s[Q];
 #pragma unroll
@@ -215,10 +299,10 @@ __global__ void __launch_bounds__(TileCfg<N1, C, CFG>::THREADS)
                 hprev[l] = h;
             }
         }
-        const int y = y0 + r0 + k;
-        if (x < p.nx && y < p.ny) {
-            collide_cell<N1, C>(s, p);
-            store_collided<N1, C>(fout, p, x, y, s);
+        const int y = y0 + r0 + kk;
+        if (x < g.nx && y < g.ny) {
+            collide_cell<N1, C>(s, p, g);
+            store_collided<N1, C>(fout, g, x, y, s);
         }
     }
 }
@@ -231,35 +315,68 @@ inline int tiled_supported(int storage) {
 
 template <int N1, class C>
 inline void tiled_box(int cfg, int* bx, int* by) {
-    const TileShape t = tile_shape((int)sizeof(typename C::T), cfg);
+    const TileShape t = tile_shape(N1 * N1, (int)sizeof(typename C::T), cfg);
     *bx = t.tx + 16 / (int)sizeof(typename C::T);
     *by = t.ty + 1;
 }
 
-template <int N1, class C, int CFG>
-inline cudaError_t tiled_launch(const CUtensorMap* tmap, typename C::T* fout, const KParams& p, cudaStream_t s) {
+template <int N1, class C, int CFG, class Src>
+inline cudaError_t tiled_prepare() {
     using Cfg = TileCfg<N1, C, CFG>;
     static bool attr_set[64] = {};  // per device
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-        const cudaError_t e = cudaFuncSetAttribute(sweep_tiled_kernel<N1, C, CFG>,
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!attr_set[dev]) {
+        const cudaError_t e = cudaFuncSetAttribute(sweep_tiled_kernel<N1, C, CFG, Src>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
         if (e != cudaSuccess) return e;
-        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+        attr_set[dev] = true;
     }
-    const dim3 grid((p.nx + Cfg::TX - 1) / Cfg::TX, (p.ny + Cfg::TY - 1) / Cfg::TY);
-    sweep_tiled_kernel<N1, C, CFG><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(*tmap, fout, p);
+    return cudaSuccess;
+}
+
+template <int N1, class C, int CFG>
+inline cudaError_t tiled_launch(const SweepMaps* maps, typename C::T* fout, const KParams& p, cudaStream_t s) {
+    using Cfg = TileCfg<N1, C, CFG>;
+    const cudaError_t e = tiled_prepare<N1, C, CFG, SingleSrc>();
+    if (e != cudaSuccess) return e;
+    SingleSrc src;
+    src.map_in = *(const CUtensorMap*)maps->in;
+    src.fout = fout;
+    src.tiles_x = (p.nx + Cfg::TX - 1) / Cfg::TX;
+    src.ntiles = src.tiles_x * ((p.ny + Cfg::TY - 1) / Cfg::TY);
+    sweep_tiled_kernel<N1, C, CFG, SingleSrc><<<src.ntiles, Cfg::THREADS, Cfg::SMEM, s>>>(src, p);
     return cudaGetLastError();
 }
 
 template <int N1, class C>
-inline cudaError_t tiled_sweep(int cfg, const CUtensorMap* tmap, typename C::T* fout, const KParams& p, cudaStream_t s) {
+inline cudaError_t tiled_sweep(int cfg, const SweepMaps* maps, typename C::T* fout, const KParams& p, cudaStream_t s) {
     switch (cfg) {
-        case 0: return tiled_launch<N1, C, 0>(tmap, fout, p, s);
-        case 1: return tiled_launch<N1, C, 1>(tmap, fout, p, s);
-        case 2: return tiled_launch<N1, C, 2>(tmap, fout, p, s);
-        case 3: return tiled_launch<N1, C, 3>(tmap, fout, p, s);
+        case 0: return tiled_launch<N1, C, 0>(maps, fout, p, s);
+        case 1: return tiled_launch<N1, C, 1>(maps, fout, p, s);
+        case 2: return tiled_launch<N1, C, 2>(maps, fout, p, s);
+        case 3: return tiled_launch<N1, C, 3>(maps, fout, p, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int N1, class C, int CFG>
+inline cudaError_t batch_launch(const BatchSrc& src, const KParams& p, cudaStream_t s) {
+    using Cfg = TileCfg<N1, C, CFG>;
+    const cudaError_t e = tiled_prepare<N1, C, CFG, BatchSrc>();
+    if (e != cudaSuccess) return e;
+    sweep_tiled_kernel<N1, C, CFG, BatchSrc><<<src.ntiles, Cfg::THREADS, Cfg::SMEM, s>>>(src, p);
+    return cudaGetLastError();
+}
+
+template <int N1, class C>
+inline cudaError_t batch_sweep(int cfg, const BatchSrc& src, const KParams& p, cudaStream_t s) {
+    switch (cfg) {
+        case 0: return batch_launch<N1, C, 0>(src, p, s);
+        case 1: return batch_launch<N1, C, 1>(src, p, s);
+        case 2: return batch_launch<N1, C, 2>(src, p, s);
+        case 3: return batch_launch<N1, C, 3>(src, p, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -1,0 +1,75 @@
+"""Batched domains (one persistent launch per time step over the tiles of every domain):
+each domain must evolve exactly as the same domain run alone, and, for FP64 storage, as the
+FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tv():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1004_5059_gb300 as tv
+    return tv
+
+
+SIZES = [(64, 48), (128, 64), (40, 72), (96, 96), (33, 17)]  # includes ragged tiles
+TAUS = [0.6, 0.8, 1.3, 0.55, 0.9]
+
+
+@pytest.mark.parametrize("storage", ["fp32_dev", "fp16_dev"])
+@pytest.mark.parametrize("config", [0, 1, 2, 3])
+def test_batch_equals_single_domain_runs(tv, storage, config):
+    nx = [s[0] for s in SIZES]
+    ny = [s[1] for s in SIZES]
+    b = tv.Batch(nx, ny, TAUS, "D2Q16", storage=storage)
+    b.set_tile(config)
+    fields = [workloads.random_smooth(x, y, seed=40 + d, amp_u=0.06, amp_T=0.06) for d, (x, y) in enumerate(SIZES)]
+    for d, f in enumerate(fields):
+        b.init_moments(d, *f)
+    b.step(45)  # graph replay (32) + direct launches
+    for d, (x, y) in enumerate(SIZES):
+        s = tv.Simulation(x, y, "D2Q16", tau=TAUS[d], storage=storage, form="tiled")
+        s.set_tile(config)
+        s.init_moments(*fields[d])
+        s.step(45)
+        assert np.array_equal(b.populations_f64(d), s.populations_f64()), (d, config)
+        s.close()
+    b.close()
+
+
+def test_batch_fp64_matches_oracle(tv):
+    nx = [s[0] for s in SIZES[:3]]
+    ny = [s[1] for s in SIZES[:3]]
+    b = tv.Batch(nx, ny, TAUS[:3], "D2Q36", storage="fp64")
+    fields = [workloads.random_smooth(x, y, seed=60 + d) for d, (x, y) in enumerate(SIZES[:3])]
+    for d, f in enumerate(fields):
+        b.init_moments(d, *f)
+    b.step(20)
+    for d, (x, y) in enumerate(SIZES[:3]):
+        ref = oracle.Oracle(x, y, "D2Q36", tau=TAUS[d])
+        ref.init_moments(*fields[d])
+        ref.run(20)
+        got = b.populations_f64(d)
+        assert np.max(np.abs(got - ref.f)) / np.max(np.abs(ref.f)) < 1e-11, d
+    b.close()
+
+
+def test_batch_conservation_per_domain(tv):
+    nx = [128, 256, 64]
+    ny = [128, 64, 192]
+    b = tv.Batch(nx, ny, [0.7, 1.1, 0.58], "D2Q16", storage="fp32_dev")
+    for d in range(3):
+        b.init_moments(d, *workloads.random_smooth(nx[d], ny[d], seed=70 + d, amp_u=0.1, amp_T=0.1))
+    s0 = [b.conserved_sums(d) for d in range(3)]
+    b.step(300)
+    for d in range(3):
+        s1 = b.conserved_sums(d)
+        assert np.all(np.abs(s1[:4] - s0[d][:4]) < 2e-8 * s0[d][0]), (d, s1 - s0[d])
+    b.close()
