@@ -65,6 +65,10 @@ extern "C" {
 #define TVLBM_FORM_PLAIN 0 /* one thread per cell, direct gathers from global memory           */
 #define TVLBM_FORM_TILED 1 /* 2-D tiles whose per-velocity source windows are staged in shared
                               memory by TMA; the default                                       */
+#define TVLBM_FORM_FLOW 2  /* the tiled sweep of several time steps in one persistent launch: a
+                              tile starts a step as soon as its 3 x 3 periodic neighbourhood has
+                              finished the previous one (no launch boundary between steps).
+                              Periodic domains whose size is a multiple of the tile shape only */
 
 /* ---- boundary conditions ----------------------------------------------------------------- */
 #define TVLBM_BC_PERIODIC 0
@@ -111,8 +115,13 @@ int tvlbm_destroy(tvlbm_ctx *ctx);
  * The stream must belong to the context's device. */
 int tvlbm_set_stream(tvlbm_ctx *ctx, void *stream);
 
-/* Select the sweep kernel form (TVLBM_FORM_PLAIN / TVLBM_FORM_TILED).  Both give the same
- * populations up to floating-point rounding order. */
+/* Select the sweep kernel form (TVLBM_FORM_PLAIN / TVLBM_FORM_TILED / TVLBM_FORM_FLOW).  All
+ * give the same populations up to floating-point rounding order; the tiled and dataflow forms
+ * give identical ones.  Errors: EINVAL (unknown form; a tiled form without a TMA descriptor;
+ * the dataflow form on walls or on a domain the current tile configuration does not cover
+ * exactly).  With the dataflow form, tvlbm_step(ctx, n) is one launch (captured graphs are not
+ * used) and a device-side wait that gives up is reported as ETIMEOUT by the next synchronising
+ * call. */
 int tvlbm_set_form(tvlbm_ctx *ctx, int form);
 
 /* Enable (1, default) or disable (0) replay of multi-step runs through captured CUDA graphs. */
@@ -127,7 +136,8 @@ int tvlbm_set_reference(tvlbm_ctx *ctx, double ux, double uy, double T);
 
 /* Tile configurations of the tiled form (an autotuner picks among them): their number, and
  * the shape of one -- tile width and height in cells and rows each thread walks.
- * tvlbm_set_tile selects one (synchronises the stream; default 0).  Errors: EINVAL. */
+ * tvlbm_set_tile selects one (synchronises the stream; default 0).  Errors: EINVAL (out of
+ * range; with the dataflow form, a configuration that does not cover the domain exactly). */
 int tvlbm_tile_count(const tvlbm_ctx *ctx);
 int tvlbm_tile_shape(const tvlbm_ctx *ctx, int config, int *tx, int *ty, int *rows_per_thread);
 int tvlbm_set_tile(tvlbm_ctx *ctx, int config);

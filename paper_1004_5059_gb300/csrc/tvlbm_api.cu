@@ -89,6 +89,51 @@ cudaError_t launch_step(tvlbm_ctx* c, int from, cudaStream_t s) {
     return c->kt->sweep(c->storage, c->form, c->tile_cfg, fin, fout, &maps, c->kp, s);
 }
 
+// Tile grid of configuration cfg when the dataflow form can run it: a periodic domain that the
+// tiles cover exactly, tiles of at least 4 rows.
+bool flow_tiles(const tvlbm_ctx* c, int cfg, int* tiles_x, int* tiles_y) {
+    if (!c->have_tmap || c->kp.walls) return false;
+    int tx = 0, ty = 0, r = 0;
+    c->kt->tile_shape(c->storage, cfg, &tx, &ty, &r);
+    if (tx < 32 || ty < 4 || c->nx % tx || c->ny % ty) return false;
+    const long long n = (long long)(c->nx / tx) * (c->ny / ty);
+    if ((size_t)n + kFlowDone > c->L.flow_ints) return false;
+    *tiles_x = c->nx / tx;
+    *tiles_y = c->ny / ty;
+    return true;
+}
+
+// n time steps in dataflow launches (tasks per launch kept below 2^30).
+cudaError_t launch_flow(tvlbm_ctx* c, int n, cudaStream_t s) {
+    int tiles_x = 0, tiles_y = 0;
+    if (!flow_tiles(c, c->tile_cfg, &tiles_x, &tiles_y)) return cudaErrorInvalidValue;
+    const int ntiles = tiles_x * tiles_y;
+    const int chunk_max = (1 << 30) / ntiles;
+    int* ctr = (int*)dptr(c, c->L.off_flow);
+    while (n > 0) {
+        const int chunk = n < chunk_max ? n : chunk_max;
+        FlowSrc src;
+        memset(&src, 0, sizeof(src));
+        src.map[0] = c->tmap[c->cur];
+        src.map[1] = c->tmap[1 - c->cur];
+        src.buf[0] = dptr(c, c->L.off_f[c->cur]);
+        src.buf[1] = dptr(c, c->L.off_f[1 - c->cur]);
+        src.tiles_x = tiles_x;
+        src.tiles_y = tiles_y;
+        src.ntiles = ntiles;
+        src.nsteps = chunk;
+        src.next_task = ctr;
+        src.abort = ctr + 1;
+        src.done = ctr + kFlowDone;
+        cudaError_t e = cudaMemsetAsync(ctr, 0, ((size_t)kFlowDone + ntiles) * sizeof(int), s);
+        if (e == cudaSuccess) e = c->kt->flow_sweep(c->storage, c->tile_cfg, src, c->kp, s);
+        if (e != cudaSuccess) return e;
+        c->cur ^= chunk & 1;
+        n -= chunk;
+    }
+    return cudaSuccess;
+}
+
 bool make_tensor_maps(tvlbm_ctx* c) {
     if (!c->kt->tiled_available(c->storage)) return false;
     int bx = 0, by = 0;
@@ -265,9 +310,14 @@ int tvlbm_set_stream(tvlbm_ctx* c, void* stream) {
 
 int tvlbm_set_form(tvlbm_ctx* c, int form) {
     if (!c) return TVLBM_EINVAL;
-    if (form != FORM_PLAIN && form != FORM_TILED) return fail(c, TVLBM_EINVAL, "unknown form %d", form);
-    if (form == FORM_TILED && !c->have_tmap)
-        return fail(c, TVLBM_EINVAL, "tiled form not available (no TMA descriptor for this storage/driver)");
+    if (form != FORM_PLAIN && form != FORM_TILED && form != FORM_FLOW)
+        return fail(c, TVLBM_EINVAL, "unknown form %d", form);
+    if (form != FORM_PLAIN && !c->have_tmap)
+        return fail(c, TVLBM_EINVAL, "tiled forms not available (no TMA descriptor for this storage/driver)");
+    int tiles_x = 0, tiles_y = 0;
+    if (form == FORM_FLOW && !flow_tiles(c, c->tile_cfg, &tiles_x, &tiles_y))
+        return fail(c, TVLBM_EINVAL,
+                    "dataflow form needs a periodic domain that tile configuration %d covers exactly", c->tile_cfg);
     if (form != c->form) drop_graphs(c);
     c->form = form;
     return TVLBM_OK;
@@ -310,6 +360,9 @@ int tvlbm_set_tile(tvlbm_ctx* c, int config) {
     if (!c) return TVLBM_EINVAL;
     if (config < 0 || config >= kTileConfigs) return fail(c, TVLBM_EINVAL, "tile configuration %d out of range", config);
     if (config == c->tile_cfg) return TVLBM_OK;
+    int tiles_x = 0, tiles_y = 0;
+    if (c->form == FORM_FLOW && !flow_tiles(c, config, &tiles_x, &tiles_y))
+        return fail(c, TVLBM_EINVAL, "tile configuration %d does not cover the domain exactly (dataflow form)", config);
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);  // launched work keeps its own copy of the descriptors
     const int old = c->tile_cfg;
@@ -341,6 +394,10 @@ int tvlbm_step(tvlbm_ctx* c, int n) {
     if (!c) return TVLBM_EINVAL;
     if (n < 0) return fail(c, TVLBM_EINVAL, "negative step count");
     cudaSetDevice(c->device);
+    if (c->form == FORM_FLOW) {
+        TVLBM_CUDA(c, launch_flow(c, n, c->stream), "dataflow launch");
+        return TVLBM_OK;
+    }
     int left = n;
     if (c->graphs) {
         while (left >= kGraphSteps) {

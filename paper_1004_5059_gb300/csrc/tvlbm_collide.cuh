@@ -70,7 +70,10 @@ __device__ __forceinline__ void cell_collide_dev(float (&s)[N1 * N1], const KPar
         me = fmaf(p.wf[H], rxx[H], me);
     }
     const float rho = p.rho0f + m0;
-    const float inv = __frcp_rn(rho);  // correctly rounded reciprocal
+    // hardware reciprocal (about 1 ulp): its rounding only perturbs the equilibrium velocity and
+    // temperature; the conserved sums never pass through it
+    float inv;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv) : "f"(rho));
     const float ux = (p.jreff[0] + mx) * inv, uy = (p.jreff[1] + my) * inv;
     const float th = 0.5f * ((p.ereff + me - 2.0f * m0) * inv - (ux * ux + uy * uy));
 
@@ -86,14 +89,14 @@ __device__ __forceinline__ void cell_collide_dev(float (&s)[N1 * N1], const KPar
     }
 
     // ---- first-order cancellation of the table defects -------------------------------------
-    float Dm = fmaf(2.f * p.dS[0], m0, p.refD[0]), De = fmaf(2.f * m0, p.dV[0] + p.dS[0], p.refD[3]);
-    float Dx = fmaf(rho * ux, p.dU[1] + p.dS[0], p.refD[1]), Dy = fmaf(rho * uy, p.dU[1] + p.dS[0], p.refD[2]);
+    float Dm = fmaf(2.f * p.dS[0], m0, p.refD[0]), De = fmaf(2.f * m0, p.dVS[0], p.refD[3]);
+    float Dx = fmaf(rho * ux, p.dUS, p.refD[1]), Dy = fmaf(rho * uy, p.dUS, p.refD[2]);
 #pragma unroll
     for (int a = 2; a <= N; a += 2) {  // dS, dV vanish for odd orders (mirror symmetry)
-        Dm = fmaf(rho * p.dS[a], hx[a] + hy[a], Dm);
-        De = fmaf(rho * (p.dV[a] + p.dS[a]), hx[a] + hy[a], De);
+        const float hs = rho * (hx[a] + hy[a]);
+        Dm = fmaf(p.dS[a], hs, Dm);
+        De = fmaf(p.dVS[a], hs, De);  // includes the dS[0] (h_2) term for a = 2
     }
-    if (N >= 2) De = fmaf(rho * p.dS[0], hx[2] + hy[2], De);
 #pragma unroll
     for (int a = 3; a <= N; a += 2) {  // dU vanishes for even orders
         Dx = fmaf(rho * p.dU[a], hx[a], Dx);

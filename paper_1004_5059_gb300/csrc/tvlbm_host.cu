@@ -179,7 +179,11 @@ Layout make_layout(int nx, int ny, int Q, int storage) {
     L.off_part = L.off_mom + L.mom_bytes;
     L.off_sums = L.off_part + L.part_bytes;
     L.off_status = L.off_sums + 128;
-    L.total = L.off_sums + 256;
+    // dataflow counters: task counter, abort word, then one completion counter per tile of at
+    // least 32 x 4 cells (the smallest tile of any configuration)
+    L.off_flow = L.off_sums + 256;
+    L.flow_ints = (size_t)kFlowDone + (size_t)((nx + 31) / 32) * (size_t)((ny + 3) / 4);
+    L.total = L.off_flow + align_up(L.flow_ints * sizeof(int), 256);
     return L;
 }
 
@@ -274,6 +278,9 @@ void fill_kparams(KParams& p, const Rule& r, int N, double dt, double tau, doubl
         p.dU[a] = (float)(U - (a == 1 ? 1.0L : 0.0L));
         p.dV[a] = (float)(V - (a == 0 ? 1.0L : 0.0L) - (a == 2 ? 1.0L : 0.0L));
     }
+    p.dUS = (float)((long double)p.dU[1] + p.dS[0]);
+    for (int a = 0; a < kMaxN1; ++a)
+        p.dVS[a] = (float)((long double)p.dV[a] + p.dS[a] + (a == 2 ? (long double)p.dS[0] : 0.0L));
     p.omegad = dt / tau;
     p.omegaf = (float)p.omegad;
     p.rho0d = rho0;

@@ -35,6 +35,7 @@ struct Layout {
     long long plane;
     size_t buf_bytes, mom_bytes, part_bytes, total;
     size_t off_f[2], off_mom, off_part, off_sums, off_status;
+    size_t off_flow, flow_ints;  // counters of the multi-step dataflow launch
 };
 size_t align_up(size_t v, size_t a);
 Layout make_layout(int nx, int ny, int Q, int storage);

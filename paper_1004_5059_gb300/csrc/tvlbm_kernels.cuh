@@ -4,12 +4,14 @@
 // (3, 4, 6 -> D2Q9, D2Q16, D2Q36) and on the storage codec.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <type_traits>
+#include <utility>
 
 namespace tvlbm {
 
@@ -21,10 +23,11 @@ constexpr int kMaxQ = kMaxN1 * kMaxN1;
 constexpr int HY = 4;
 constexpr int FILL = 4;
 constexpr int kRedBlocks = 1024;  // fixed partial count of the FP64 reduction (deterministic)
-constexpr int kTileConfigs = 4;   // tile shapes of the tiled form
+constexpr int kTileConfigs = 4;  // tile shapes of the tiled form
+constexpr int kFlowDone = 16;    // first per-tile counter in the dataflow scratch (64-byte aligned)
 
 enum Storage { ST_FP64 = 0, ST_FP32 = 1, ST_BF16_DEV = 2, ST_FP16_DEV = 3, ST_FP32_DEV = 4 };
-enum Form { FORM_PLAIN = 0, FORM_TILED = 1 };
+enum Form { FORM_PLAIN = 0, FORM_TILED = 1, FORM_FLOW = 2 };
 
 // Everything a kernel needs, passed by value (lands in the constant bank).
 struct KParams {
@@ -43,6 +46,9 @@ struct KParams {
     //   dS[a] = sum_i wf_i E_ia - [a=0],  dU[a] = sum_i wxf_i E_ia - [a=1],
     //   dV[a] = sum_i wx2f_i E_ia - [a=0] - [a=2].
     float dS[kMaxN1], dU[kMaxN1], dV[kMaxN1];
+    // combinations of those defects the FP32 collision uses directly: dUS = dU[1] + dS[0],
+    // dVS[a] = dV[a] + dS[a] (+ dS[0] for a = 2, the h_2 term of the energy defect)
+    float dUS, dVS[kMaxN1];
     int sh[kMaxN1];
     float omegaf, rho0f;
     double omegad, rho0d;
@@ -266,6 +272,29 @@ __device__ __forceinline__ void cell_collide(R (&s)[N1 * N1], const KParams& p, 
     for (int l = 0; l < N1 * N1; ++l) s[l] = fma(om, eq[l] - s[l], s[l]);
 }
 
+// Programmatic dependent launch: a sweep lets the next launch on its stream be scheduled while
+// its own tail runs (launch_dependents), and reads its input only after the previous grid's
+// writes are complete and visible (wait).  Both are no-ops when launched without the attribute.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Launch a kernel with programmatic stream serialization (see pdl_wait).
+template <class... KArgs, class... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // Explicit global-space stores and loads: the population buffers are always global memory, and
 // saying so keeps generic accesses (which could alias shared memory) out of the sweeps.
 __device__ __forceinline__ void stg(float* p, float v) { asm volatile("st.global.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory"); }
@@ -302,6 +331,17 @@ struct SweepMaps {
     const void* out;
 };
 
+// Work of one multi-step dataflow launch (sweep_flow_kernel): tiles_x x tiles_y tiles, nsteps
+// time steps, tasks (step, tile) handed out in step-major order.
+struct FlowSrc {
+    CUtensorMap map[2];  // input descriptors: [0] the buffer holding the state at launch, [1] the other
+    void* buf[2];        // the same two buffers
+    int tiles_x, tiles_y, ntiles, nsteps;
+    int* done;       // [ntiles] steps completed in this launch (zeroed before it)
+    int* next_task;  // task counter (zeroed before the launch)
+    int* abort;      // raised by a CTA whose bounded wait gave up (zeroed before the launch)
+};
+
 struct BatchSrc;  // tile source of the batched sweep (tvlbm_tiled.cuh)
 
 // Per-velocity change of the deviation reference: d_l += delta_l re-expresses stored
@@ -327,6 +367,8 @@ struct KernelTable {
     void (*tile_shape)(int storage, int cfg, int* tx, int* ty, int* rows_per_thread);
     // re-express every stored element of buffer f against a new deviation reference
     cudaError_t (*reencode)(int storage, void* f, const RefShift& shift, const KParams& p, cudaStream_t s);
+    // n time steps of one periodic domain in a single dataflow launch
+    cudaError_t (*flow_sweep)(int storage, int cfg, const FlowSrc& src, const KParams& p, cudaStream_t s);
     // one time step of every domain of a batch (persistent launch over all tiles)
     cudaError_t (*batch_sweep)(int storage, int cfg, const BatchSrc& src, const KParams& p, cudaStream_t s);
 };

@@ -21,8 +21,10 @@ __global__ void __launch_bounds__(256) sweep_plain_kernel(const typename C::T* _
     using R = typename C::R;
     using T = typename C::T;
     constexpr int Q = N1 * N1;
+    pdl_launch_dependents();
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    pdl_wait();  // the previous step's populations are complete from here on
     if (x >= p.nx || y >= p.ny) return;
     R s[Q];
 #pragma unroll
@@ -288,8 +290,7 @@ struct Launch {
         using T = typename C::T;
         if (form == FORM_TILED) return tiled_sweep<N1, C>(cfg, maps, (T*)fout, p, s);
         const dim3 b(32, 8);
-        sweep_plain_kernel<N1, C><<<grid2d(p, b), b, 0, s>>>((const T*)fin, (T*)fout, p);
-        return cudaGetLastError();
+        return launch_pdl(sweep_plain_kernel<N1, C>, grid2d(p, b), b, 0, s, (const T*)fin, (T*)fout, p);
     }
     template <class C>
     static cudaError_t init_c(const double* fields, void* f, const KParams& p, cudaStream_t s) {
@@ -390,6 +391,16 @@ struct Launch {
     static cudaError_t reencode(int storage, void* f, const RefShift& sh, const KParams& p, cudaStream_t s) {
         TVLBM_DISPATCH(reencode_c, (f, sh, p, s))
     }
+    static cudaError_t flow(int storage, int cfg, const FlowSrc& src, const KParams& p, cudaStream_t s) {
+        switch (storage) {
+            case ST_FP64: return flow_sweep<N1, CodecF64>(cfg, src, p, s);
+            case ST_FP32: return flow_sweep<N1, CodecF32>(cfg, src, p, s);
+            case ST_BF16_DEV: return flow_sweep<N1, CodecBF16Dev>(cfg, src, p, s);
+            case ST_FP16_DEV: return flow_sweep<N1, CodecF16Dev>(cfg, src, p, s);
+            case ST_FP32_DEV: return flow_sweep<N1, CodecF32Dev>(cfg, src, p, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     static cudaError_t batch(int storage, int cfg, const BatchSrc& src, const KParams& p, cudaStream_t s) {
         switch (storage) {
             case ST_FP64: return batch_sweep<N1, CodecF64>(cfg, src, p, s);
@@ -404,7 +415,7 @@ struct Launch {
 
     static const KernelTable* table() {
         static const KernelTable t = {&sweep, &init, &moments, &reduce, &wall, &halo, &decode, &encode, &tiled_available,
-                                      &box, &shape, &reencode, &batch};
+                                      &box, &shape, &reencode, &flow, &batch};
         return &t;
     }
 };

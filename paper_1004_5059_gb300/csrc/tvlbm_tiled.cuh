@@ -27,10 +27,10 @@ __host__ __device__ constexpr TileShape tile_shape_base(int es, int cfg) {
                       : cfg == 1 ? TileShape{32, 4, 2}
                       : cfg == 2 ? TileShape{32, 8, 2}
                                  : TileShape{32, 4, 4})
-                   : (cfg == 0   ? TileShape{64, 8, 4}
-                      : cfg == 1 ? TileShape{64, 16, 4}
-                      : cfg == 2 ? TileShape{32, 8, 4}
-                                 : TileShape{32, 16, 4});
+                   : (cfg == 0   ? TileShape{32, 16, 4}
+                      : cfg == 1 ? TileShape{32, 8, 4}
+                      : cfg == 2 ? TileShape{64, 8, 4}
+                                 : TileShape{64, 16, 4});
 }
 __host__ __device__ constexpr int tile_smem(int q, int es, TileShape t) {
     return q * (((t.tx + 16 / es) * (t.ty + 1) * es + 127) / 128 * 128) + 8 * q + 128;
@@ -73,14 +73,16 @@ __device__ __forceinline__ void fence_barrier_init() {
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
 }
+// One test of the phase, letting the hardware suspend the thread up to ~1 ms while it is not
+// complete (so waiting threads do not spin through issue slots).
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(done)
-        : "r"(smem_addr(bar)), "r"(parity)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(1000000u)
         : "memory");
     return done != 0;
 }
@@ -206,65 +208,14 @@ struct BatchSrc {
     }
 };
 
-// Tiled sweep: CTA b owns tile b.  Thread 0 starts the Q window loads; warp 0 then waits for
-// them, lane l watching barrier l (and l + 32), while the other warps sleep at the block
-// barrier.  Each thread walks R rows of one column (x-lerp of the previous row carried in
-// registers), collides and stores straight to global memory.  Every wait is bounded; a timeout
-// sets the status word and the CTA returns after a bounded drain of its own loads.
-template <int N1, class C, int CFG, class Src>
-__global__ void __launch_bounds__(TileCfg<N1, C, CFG>::THREADS)
-    sweep_tiled_kernel(const __grid_constant__ Src src, const KParams p) {
+// Gather, collide and store one tile whose Q windows are in shared memory at base.
+template <int N1, class C, int CFG>
+__device__ __forceinline__ void tile_compute(const unsigned char* base, int x0, int y0, const Geom& g,
+                                             typename C::T* fout, const KParams& p, int tid) {
     using Cfg = TileCfg<N1, C, CFG>;
     using R = typename C::R;
-    using T = typename C::T;
-    constexpr int Q = N1 * N1, TX = Cfg::TX, TY = Cfg::TY, RR = Cfg::R, BX = Cfg::BX, A = Cfg::A, ES = Cfg::ES;
+    constexpr int Q = N1 * N1, TX = Cfg::TX, RR = Cfg::R, BX = Cfg::BX, A = Cfg::A, ES = Cfg::ES;
     constexpr int WIN = Cfg::WIN_BYTES;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    // 128-byte aligned base, derived from smem_raw by pointer arithmetic so the compiler keeps
-    // the shared address space (window reads compile to shared-memory loads)
-    unsigned char* base = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(base + Q * WIN);
-    __shared__ int tile_ok;
-    const int tid = threadIdx.x;
-    const int t = blockIdx.x;
-
-    int x0, y0;
-    const CUtensorMap* map;
-    void* outv;
-    Geom g;
-    src.tile(t, p, TX, TY, x0, y0, map, outv, g);
-
-    if (tid == 0) {
-#pragma unroll 1
-        for (int l = 0; l < Q; ++l) mbar_init(&bars[l], 1);
-        fence_barrier_init();
-#pragma unroll
-        for (int l = 0; l < Q; ++l) {
-            const int i = l % N1, j = l / N1;
-            mbar_arrive_expect_tx(&bars[l], (uint32_t)(BX * Cfg::BY * ES));
-            tma_load_3d(base + l * WIN, map, &bars[l], (x0 + g.hx - p.sh[i] - 1) & ~(A - 1), y0 + HY - p.sh[j] - 1, l);
-        }
-    }
-    if (tid < 32) {
-        bool ok = true;
-#pragma unroll 1
-        for (int l = tid; l < Q; l += 32) ok = ok && mbar_wait_bounded(&bars[l], 0, kWaitLimitNs);
-        ok = __all_sync(0xffffffffu, ok);
-        if (tid == 0) tile_ok = ok ? 1 : 0;
-    }
-    __syncthreads();
-    if (!tile_ok) {
-        // A window never arrived: report it, give the loads a bounded chance to land (so no copy
-        // still writes this CTA's shared memory), store nothing.
-        if (tid == 0) {
-            if (p.status) atomicOr(p.status, 1);
-#pragma unroll 1
-            for (int l = 0; l < Q; ++l) mbar_wait_bounded(&bars[l], 0, kWaitLimitNs);
-        }
-        return;
-    }
-
-    T* fout = reinterpret_cast<T*>(outv);
     const int cx = tid % TX, r0 = (tid / TX) * RR;
     const int x = x0 + cx;
     // byte offset of column (cx + alignment remainder) within a window row, per x-node; the tile
@@ -307,6 +258,70 @@ __global__ void __launch_bounds__(TileCfg<N1, C, CFG>::THREADS)
     }
 }
 
+// Tiled sweep: CTA b owns tile b.  It lets the next step's launch be scheduled at once, and
+// thread 0 waits for the previous grid before starting the Q window loads; warp 0 then waits for
+// them, lane l watching barrier l (and l + 32), while the other warps sleep at the block
+// barrier.  Each thread walks R rows of one column (x-lerp of the previous row carried in
+// registers), collides and stores straight to global memory.  Every wait is bounded; a timeout
+// sets the status word and the CTA returns after a bounded drain of its own loads.
+template <int N1, class C, int CFG, class Src>
+__global__ void __launch_bounds__(TileCfg<N1, C, CFG>::THREADS)
+    sweep_tiled_kernel(const __grid_constant__ Src src, const KParams p) {
+    using Cfg = TileCfg<N1, C, CFG>;
+    using R = typename C::R;
+    using T = typename C::T;
+    constexpr int Q = N1 * N1, TX = Cfg::TX, TY = Cfg::TY, RR = Cfg::R, BX = Cfg::BX, A = Cfg::A, ES = Cfg::ES;
+    constexpr int WIN = Cfg::WIN_BYTES;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // 128-byte aligned base, derived from smem_raw by pointer arithmetic so the compiler keeps
+    // the shared address space (window reads compile to shared-memory loads)
+    unsigned char* base = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base + Q * WIN);
+    __shared__ int tile_ok;
+    const int tid = threadIdx.x;
+    const int t = blockIdx.x;
+
+    pdl_launch_dependents();
+    int x0, y0;
+    const CUtensorMap* map;
+    void* outv;
+    Geom g;
+    src.tile(t, p, TX, TY, x0, y0, map, outv, g);
+
+    if (tid == 0) {
+#pragma unroll 1
+        for (int l = 0; l < Q; ++l) mbar_init(&bars[l], 1);
+        fence_barrier_init();
+        pdl_wait();  // the previous step's populations are complete from here on
+#pragma unroll
+        for (int l = 0; l < Q; ++l) {
+            const int i = l % N1, j = l / N1;
+            mbar_arrive_expect_tx(&bars[l], (uint32_t)(BX * Cfg::BY * ES));
+            tma_load_3d(base + l * WIN, map, &bars[l], (x0 + g.hx - p.sh[i] - 1) & ~(A - 1), y0 + HY - p.sh[j] - 1, l);
+        }
+    }
+    if (tid < 32) {
+        bool ok = true;
+#pragma unroll 1
+        for (int l = tid; l < Q; l += 32) ok = ok && mbar_wait_bounded(&bars[l], 0, kWaitLimitNs);
+        ok = __all_sync(0xffffffffu, ok);
+        if (tid == 0) tile_ok = ok ? 1 : 0;
+    }
+    __syncthreads();
+    if (!tile_ok) {
+        // A window never arrived: report it, give the loads a bounded chance to land (so no copy
+        // still writes this CTA's shared memory), store nothing.
+        if (tid == 0) {
+            if (p.status) atomicOr(p.status, 1);
+#pragma unroll 1
+            for (int l = 0; l < Q; ++l) mbar_wait_bounded(&bars[l], 0, kWaitLimitNs);
+        }
+        return;
+    }
+
+    tile_compute<N1, C, CFG>(base, x0, y0, g, reinterpret_cast<T*>(outv), p, tid);
+}
+
 template <int N1>
 inline int tiled_supported(int storage) {
     (void)storage;
@@ -346,8 +361,8 @@ inline cudaError_t tiled_launch(const SweepMaps* maps, typename C::T* fout, cons
     src.fout = fout;
     src.tiles_x = (p.nx + Cfg::TX - 1) / Cfg::TX;
     src.ntiles = src.tiles_x * ((p.ny + Cfg::TY - 1) / Cfg::TY);
-    sweep_tiled_kernel<N1, C, CFG, SingleSrc><<<src.ntiles, Cfg::THREADS, Cfg::SMEM, s>>>(src, p);
-    return cudaGetLastError();
+    return launch_pdl(sweep_tiled_kernel<N1, C, CFG, SingleSrc>, dim3(src.ntiles), dim3(Cfg::THREADS), Cfg::SMEM, s,
+                      src, p);
 }
 
 template <int N1, class C>
@@ -366,8 +381,8 @@ inline cudaError_t batch_launch(const BatchSrc& src, const KParams& p, cudaStrea
     using Cfg = TileCfg<N1, C, CFG>;
     const cudaError_t e = tiled_prepare<N1, C, CFG, BatchSrc>();
     if (e != cudaSuccess) return e;
-    sweep_tiled_kernel<N1, C, CFG, BatchSrc><<<src.ntiles, Cfg::THREADS, Cfg::SMEM, s>>>(src, p);
-    return cudaGetLastError();
+    return launch_pdl(sweep_tiled_kernel<N1, C, CFG, BatchSrc>, dim3(src.ntiles), dim3(Cfg::THREADS), Cfg::SMEM, s,
+                      src, p);
 }
 
 template <int N1, class C>
@@ -377,6 +392,153 @@ inline cudaError_t batch_sweep(int cfg, const BatchSrc& src, const KParams& p, c
         case 1: return batch_launch<N1, C, 1>(src, p, s);
         case 2: return batch_launch<N1, C, 2>(src, p, s);
         case 3: return batch_launch<N1, C, 3>(src, p, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// ---- multi-step dataflow sweep ----------------------------------------------------------------
+// One persistent launch advances n time steps of a periodic domain.  Tasks (step k, tile t) are
+// handed out in step-major order from a global counter; a task starts once the 3 x 3 periodic
+// neighbourhood of its tile has finished step k - 1 (per-tile counters written with release
+// semantics after the tile's stores), which covers both the windows it reads and the region its
+// own stores overwrite (that region was the neighbours' step k - 1 input).  A task only waits on
+// tasks handed out before it, which are held by running CTAs, so the launch always progresses
+// (whether or not all CTAs are resident at once).
+// Every wait is bounded: a CTA that gives up raises the abort word and the status bit, and the
+// others stop at their next wait.  Requires tiles of at least 4 rows (a source is at most 4 cells
+// away, so it lies in a neighbouring tile) and no ragged tiles (a frame image then lies next to a
+// tile that neighbours, periodically, the tile that writes it).
+__device__ __forceinline__ int ld_relaxed_gpu(const int* p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu(int* p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void fence_acquire_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+// Generic-proxy global writes (made visible by the acquire) become visible to TMA reads.
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+
+template <int N1, class C, int CFG>
+__global__ void __launch_bounds__(TileCfg<N1, C, CFG>::THREADS)
+    sweep_flow_kernel(const __grid_constant__ FlowSrc src, const KParams p) {
+    using Cfg = TileCfg<N1, C, CFG>;
+    using T = typename C::T;
+    constexpr int Q = N1 * N1, TX = Cfg::TX, TY = Cfg::TY, BX = Cfg::BX, A = Cfg::A, ES = Cfg::ES;
+    constexpr int WIN = Cfg::WIN_BYTES;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char* base = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base + Q * WIN);
+    __shared__ int s_task, s_ok;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+#pragma unroll 1
+        for (int l = 0; l < Q; ++l) mbar_init(&bars[l], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    const Geom g = geom_of(p);
+    const int total = src.ntiles * src.nsteps;
+    uint32_t parity = 0;
+    for (;;) {
+        if (tid == 0) s_task = atomicAdd(src.next_task, 1);
+        __syncthreads();
+        const int task = s_task;
+        if (task >= total) break;
+        // step k visits tile rows starting at row k: the first rows of step k + 1 then depend on
+        // the first rows that step k finished
+        const int k = task / src.ntiles, r = task - k * src.ntiles;
+        const int tx = r % src.tiles_x, ty = (r / src.tiles_x + k) % src.tiles_y;
+        const int t = ty * src.tiles_x + tx;
+        const int x0 = tx * TX, y0 = ty * TY;
+        if (tid == 0) {
+            bool ok = true, issued = false;
+            // wait until the 3 x 3 periodic neighbourhood has completed step k - 1
+            const int* nb[9];
+#pragma unroll
+            for (int d = 0; d < 9; ++d) {
+                const int xx = (tx + d % 3 - 1 + src.tiles_x) % src.tiles_x;
+                const int yy = (ty + d / 3 - 1 + src.tiles_y) % src.tiles_y;
+                nb[d] = src.done + yy * src.tiles_x + xx;
+            }
+            const uint64_t t0 = global_ns();
+            for (;;) {
+                int ready = 0;
+#pragma unroll
+                for (int d = 0; d < 9; ++d) ready += ld_relaxed_gpu(nb[d]) >= k ? 1 : 0;
+                if (ready == 9) break;
+                if (*(volatile int*)src.abort || global_ns() - t0 > kWaitLimitNs) {
+                    ok = false;
+                    break;
+                }
+                __nanosleep(100);
+            }
+            if (ok) {
+                fence_acquire_gpu();
+                fence_proxy_async_global();
+                const CUtensorMap* map = &src.map[k & 1];
+#pragma unroll
+                for (int l = 0; l < Q; ++l) {
+                    const int i = l % N1, j = l / N1;
+                    mbar_arrive_expect_tx(&bars[l], (uint32_t)(BX * Cfg::BY * ES));
+                    tma_load_3d(base + l * WIN, map, &bars[l], (x0 + g.hx - p.sh[i] - 1) & ~(A - 1),
+                                y0 + HY - p.sh[j] - 1, l);
+                }
+                issued = true;
+#pragma unroll 1
+                for (int l = 0; l < Q && ok; ++l) ok = mbar_wait_bounded(&bars[l], parity, kWaitLimitNs);
+            }
+            if (!ok) {
+                atomicExch(src.abort, 1);
+                if (p.status) atomicOr(p.status, 1);
+                if (issued) {
+#pragma unroll 1
+                    for (int l = 0; l < Q; ++l) mbar_wait_bounded(&bars[l], parity, kWaitLimitNs);
+                }
+            }
+            s_ok = ok ? 1 : 0;
+        }
+        __syncthreads();
+        if (!s_ok) break;
+        parity ^= 1u;
+        tile_compute<N1, C, CFG>(base, x0, y0, g, reinterpret_cast<T*>(src.buf[(k + 1) & 1]), p, tid);
+        fence_proxy_async_global();  // this thread's stores, visible to the TMA reads of later tasks
+        __syncthreads();             // the tile's stores are issued and its windows are free
+        if (tid == 0) st_release_gpu(src.done + t, k + 1);
+    }
+}
+
+template <int N1, class C, int CFG>
+inline cudaError_t flow_launch(const FlowSrc& src, const KParams& p, cudaStream_t s) {
+    using Cfg = TileCfg<N1, C, CFG>;
+    static int grid_of[64] = {};  // per device: SMs x resident CTAs
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!grid_of[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(sweep_flow_kernel<N1, C, CFG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             Cfg::SMEM);
+        if (e != cudaSuccess) return e;
+        int nb = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_flow_kernel<N1, C, CFG>, Cfg::THREADS, Cfg::SMEM);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        grid_of[dev] = (nb > 0 ? nb : 1) * sms;
+    }
+    const int grid = src.ntiles * src.nsteps < grid_of[dev] ? src.ntiles * src.nsteps : grid_of[dev];
+    sweep_flow_kernel<N1, C, CFG><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(src, p);
+    return cudaGetLastError();
+}
+
+template <int N1, class C>
+inline cudaError_t flow_sweep(int cfg, const FlowSrc& src, const KParams& p, cudaStream_t s) {
+    switch (cfg) {
+        case 0: return flow_launch<N1, C, 0>(src, p, s);
+        case 1: return flow_launch<N1, C, 1>(src, p, s);
+        case 2: return flow_launch<N1, C, 2>(src, p, s);
+        case 3: return flow_launch<N1, C, 3>(src, p, s);
         default: return cudaErrorInvalidValue;
     }
 }
