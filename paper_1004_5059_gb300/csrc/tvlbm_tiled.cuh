@@ -420,115 +420,193 @@ __device__ __forceinline__ void fence_acquire_gpu() { asm volatile("fence.acq_re
 // Generic-proxy global writes (made visible by the acquire) become visible to TMA reads.
 __device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 
+// Layout of the dataflow kernel: the tiled form's compute threads plus one producer warp, and two
+// stages of Q windows so that the next task's windows load while the current task is computed.
 template <int N1, class C, int CFG>
-__global__ void __launch_bounds__(TileCfg<N1, C, CFG>::THREADS)
+struct FlowCfg {
+    using Tile = TileCfg<N1, C, CFG>;
+    static constexpr int STAGE_BYTES = Tile::Q * Tile::WIN_BYTES;
+    // two stages where they fit (one otherwise: the producer then only overlaps the next
+    // task's dependency wait with the current compute)
+    static constexpr int STAGES = 2 * STAGE_BYTES + 256 <= 227 * 1024 ? 2 : 1;
+    static constexpr int CONSUMERS = Tile::THREADS;          // compute threads (whole warps)
+    static constexpr int THREADS = CONSUMERS + 32;           // + the producer warp
+    static constexpr uint32_t TX_BYTES = (uint32_t)(Tile::Q * Tile::BX * Tile::BY * Tile::ES);
+    static constexpr int SMEM = STAGES * STAGE_BYTES + 128 + 128;  // stages, barriers + task slots, alignment
+    static_assert(STAGES * 16 + 2 * STAGES * 4 <= 128, "barriers and slots exceed their area");
+    // resident CTAs per SM to compile for: as many as shared memory holds (228 KB per SM, 1 KB
+    // reserved per CTA), but not so many that a thread gets fewer registers than the cell's
+    // state needs: 96 for D2Q9/D2Q16 in FP32 (72 measured slower at five CTAs per SM than 96
+    // at four), 128 in FP64, 168 for D2Q36 (255 in FP64)
+    static constexpr int FIT = (228 * 1024) / (SMEM + 1024);
+    static constexpr int REG_FLOOR = N1 >= 6 ? (Tile::ES == 8 ? 255 : 168) : (Tile::ES == 8 ? 128 : 96);
+    static constexpr int REG_FIT = 65536 / (THREADS * REG_FLOOR);
+    static constexpr int MINB = FIT < 1 ? 1 : (FIT < REG_FIT ? FIT : (REG_FIT < 1 ? 1 : REG_FIT));
+    static_assert(CONSUMERS % 32 == 0, "compute threads must be whole warps");
+    static_assert(SMEM <= 227 * 1024, "dataflow stages exceed shared memory");
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+// Barrier `id` over the first `n` threads of the block that also returns whether `pred` held in
+// every one of them.
+__device__ __forceinline__ bool bar_and(int id, int n, bool pred) {
+    int out;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.s32 p, %1, 0;\n\t"
+        "barrier.cta.red.and.pred q, %2, %3, p;\n\t"
+        "selp.s32 %0, 1, 0, q;\n\t}"
+        : "=r"(out)
+        : "r"(pred ? 1 : 0), "r"(id), "r"(n)
+        : "memory");
+    return out != 0;
+}
+__device__ __forceinline__ void bar_sync(int id, int n) { asm volatile("barrier.cta.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+
+// Producer (lane 0 of the last warp): take a task, wait for its neighbourhood, wait for a free
+// stage, publish the task in the stage's slot and start its Q window loads.  A negative slot
+// value ends the consumers' loop (-1: no tasks left, -2: a wait gave up).  Consumers (the tiled
+// form's threads): wait for a stage, compute the tile, free the stage, and publish the tile's
+// completion.  Every wait is bounded; a consumer's wait allows for the producer's own ones.
+template <int N1, class C, int CFG>
+__global__ void __launch_bounds__(FlowCfg<N1, C, CFG>::THREADS, FlowCfg<N1, C, CFG>::MINB)
     sweep_flow_kernel(const __grid_constant__ FlowSrc src, const KParams p) {
     using Cfg = TileCfg<N1, C, CFG>;
+    using F = FlowCfg<N1, C, CFG>;
     using T = typename C::T;
-    constexpr int Q = N1 * N1, TX = Cfg::TX, TY = Cfg::TY, BX = Cfg::BX, A = Cfg::A, ES = Cfg::ES;
-    constexpr int WIN = Cfg::WIN_BYTES;
+    constexpr int Q = N1 * N1, TX = Cfg::TX, TY = Cfg::TY, A = Cfg::A;
+    constexpr int WIN = Cfg::WIN_BYTES, NCW = F::CONSUMERS / 32;
+    constexpr uint64_t kConsumerLimitNs = 3 * kWaitLimitNs;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(base + Q * WIN);
-    __shared__ int s_task, s_ok;
+    uint64_t* full = reinterpret_cast<uint64_t*>(base + F::STAGES * F::STAGE_BYTES);
+    uint64_t* empty = full + F::STAGES;
+    volatile int* slot = reinterpret_cast<volatile int*>(empty + F::STAGES);
     const int tid = threadIdx.x;
     if (tid == 0) {
-#pragma unroll 1
-        for (int l = 0; l < Q; ++l) mbar_init(&bars[l], 1);
+#pragma unroll
+        for (int st = 0; st < F::STAGES; ++st) {
+            mbar_init(&full[st], 1);
+            mbar_init(&empty[st], NCW);
+        }
         fence_barrier_init();
     }
     __syncthreads();
     const Geom g = geom_of(p);
     const int total = src.ntiles * src.nsteps;
-    uint32_t parity = 0;
-    for (;;) {
-        if (tid == 0) s_task = atomicAdd(src.next_task, 1);
-        __syncthreads();
-        const int task = s_task;
-        if (task >= total) break;
-        // step k visits tile rows starting at row k: the first rows of step k + 1 then depend on
-        // the first rows that step k finished
-        const int k = task / src.ntiles, r = task - k * src.ntiles;
-        const int tx = r % src.tiles_x, ty = (r / src.tiles_x + k) % src.tiles_y;
-        const int t = ty * src.tiles_x + tx;
-        const int x0 = tx * TX, y0 = ty * TY;
-        if (tid == 0) {
-            bool ok = true, issued = false;
-            // wait until the 3 x 3 periodic neighbourhood has completed step k - 1
-            const int* nb[9];
+
+    if (tid >= F::CONSUMERS) {  // ---- producer warp ----
+        if (tid != F::CONSUMERS) return;
+        for (int n = 0;; ++n) {
+            const int st = n % F::STAGES;
+            const uint32_t par = ((n / F::STAGES) & 1) ^ 1;  // first use of each stage passes at once
+            const int task = atomicAdd(src.next_task, 1);
+            int code = task < total ? 0 : -1;
+            int k = 0, t = 0, x0 = 0, y0 = 0;
+            if (!code) {
+                // step k visits tile rows starting at row k: the first rows of step k + 1 then
+                // depend on the first rows that step k finished
+                k = task / src.ntiles;
+                const int r = task - k * src.ntiles;
+                const int tx = r % src.tiles_x, ty = (r / src.tiles_x + k) % src.tiles_y;
+                t = ty * src.tiles_x + tx;
+                x0 = tx * TX;
+                y0 = ty * TY;
+                const int* nb[9];
 #pragma unroll
-            for (int d = 0; d < 9; ++d) {
-                const int xx = (tx + d % 3 - 1 + src.tiles_x) % src.tiles_x;
-                const int yy = (ty + d / 3 - 1 + src.tiles_y) % src.tiles_y;
-                nb[d] = src.done + yy * src.tiles_x + xx;
-            }
-            const uint64_t t0 = global_ns();
-            for (;;) {
-                int ready = 0;
-#pragma unroll
-                for (int d = 0; d < 9; ++d) ready += ld_relaxed_gpu(nb[d]) >= k ? 1 : 0;
-                if (ready == 9) break;
-                if (*(volatile int*)src.abort || global_ns() - t0 > kWaitLimitNs) {
-                    ok = false;
-                    break;
+                for (int d = 0; d < 9; ++d) {
+                    const int xx = (tx + d % 3 - 1 + src.tiles_x) % src.tiles_x;
+                    const int yy = (ty + d / 3 - 1 + src.tiles_y) % src.tiles_y;
+                    nb[d] = src.done + yy * src.tiles_x + xx;
                 }
-                __nanosleep(100);
-            }
-            if (ok) {
-                fence_acquire_gpu();
-                fence_proxy_async_global();
-                const CUtensorMap* map = &src.map[k & 1];
+                const uint64_t t0 = global_ns();
+                for (;;) {
+                    int ready = 0;
 #pragma unroll
-                for (int l = 0; l < Q; ++l) {
-                    const int i = l % N1, j = l / N1;
-                    mbar_arrive_expect_tx(&bars[l], (uint32_t)(BX * Cfg::BY * ES));
-                    tma_load_3d(base + l * WIN, map, &bars[l], (x0 + g.hx - p.sh[i] - 1) & ~(A - 1),
-                                y0 + HY - p.sh[j] - 1, l);
+                    for (int d = 0; d < 9; ++d) ready += ld_relaxed_gpu(nb[d]) >= k ? 1 : 0;
+                    if (ready == 9) break;
+                    if (*(volatile int*)src.abort || global_ns() - t0 > kWaitLimitNs) {
+                        code = -2;
+                        break;
+                    }
+                    __nanosleep(64);
                 }
-                issued = true;
-#pragma unroll 1
-                for (int l = 0; l < Q && ok; ++l) ok = mbar_wait_bounded(&bars[l], parity, kWaitLimitNs);
             }
-            if (!ok) {
+            if (!mbar_wait_bounded(&empty[st], par, kWaitLimitNs)) code = -2;
+            if (code == -2) {
                 atomicExch(src.abort, 1);
                 if (p.status) atomicOr(p.status, 1);
-                if (issued) {
-#pragma unroll 1
-                    for (int l = 0; l < Q; ++l) mbar_wait_bounded(&bars[l], parity, kWaitLimitNs);
-                }
             }
-            s_ok = ok ? 1 : 0;
+            if (code) {
+                slot[st] = code;
+                mbar_arrive(&full[st]);  // release: the consumers see the slot
+                return;
+            }
+            fence_acquire_gpu();
+            fence_proxy_async_global();
+            slot[st] = t;  // slots: [stage] tile (>= 0) or end code, [STAGES + stage] step
+            slot[F::STAGES + st] = k;
+            mbar_arrive_expect_tx(&full[st], F::TX_BYTES);
+            unsigned char* sb = base + st * F::STAGE_BYTES;
+            const CUtensorMap* map = &src.map[k & 1];
+#pragma unroll
+            for (int l = 0; l < Q; ++l) {
+                const int i = l % N1, j = l / N1;
+                tma_load_3d(sb + l * WIN, map, &full[st], (x0 + g.hx - p.sh[i] - 1) & ~(A - 1), y0 + HY - p.sh[j] - 1,
+                            l);
+            }
         }
-        __syncthreads();
-        if (!s_ok) break;
-        parity ^= 1u;
-        tile_compute<N1, C, CFG>(base, x0, y0, g, reinterpret_cast<T*>(src.buf[(k + 1) & 1]), p, tid);
+    }
+
+    // ---- compute threads ----
+    for (int n = 0;; ++n) {
+        const int st = n % F::STAGES;
+        const uint32_t par = (n / F::STAGES) & 1;
+        const bool ok = mbar_wait_bounded(&full[st], par, kConsumerLimitNs);
+        if (!bar_and(1, F::CONSUMERS, ok)) {
+            if (tid == 0) {
+                atomicExch(src.abort, 1);
+                if (p.status) atomicOr(p.status, 1);
+            }
+            return;
+        }
+        const int code = slot[st];
+        if (code < 0) return;  // no tasks left, or the producer gave up
+        const int t = code, k = slot[F::STAGES + st];
+        const int x0 = (t % src.tiles_x) * TX, y0 = (t / src.tiles_x) * TY;
+        tile_compute<N1, C, CFG>(base + st * F::STAGE_BYTES, x0, y0, g, reinterpret_cast<T*>(src.buf[(k + 1) & 1]), p,
+                                 tid);
         fence_proxy_async_global();  // this thread's stores, visible to the TMA reads of later tasks
-        __syncthreads();             // the tile's stores are issued and its windows are free
+        __syncwarp();
+        if ((tid & 31) == 0) mbar_arrive(&empty[st]);  // this warp is done with the stage
+        bar_sync(1, F::CONSUMERS);
         if (tid == 0) st_release_gpu(src.done + t, k + 1);
     }
 }
 
 template <int N1, class C, int CFG>
 inline cudaError_t flow_launch(const FlowSrc& src, const KParams& p, cudaStream_t s) {
-    using Cfg = TileCfg<N1, C, CFG>;
+    using F = FlowCfg<N1, C, CFG>;
     static int grid_of[64] = {};  // per device: SMs x resident CTAs
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!grid_of[dev]) {
         cudaError_t e = cudaFuncSetAttribute(sweep_flow_kernel<N1, C, CFG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             Cfg::SMEM);
+                                             F::SMEM);
         if (e != cudaSuccess) return e;
         int nb = 0, sms = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_flow_kernel<N1, C, CFG>, Cfg::THREADS, Cfg::SMEM);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_flow_kernel<N1, C, CFG>, F::THREADS, F::SMEM);
         if (e != cudaSuccess) return e;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
         grid_of[dev] = (nb > 0 ? nb : 1) * sms;
     }
-    const int grid = src.ntiles * src.nsteps < grid_of[dev] ? src.ntiles * src.nsteps : grid_of[dev];
-    sweep_flow_kernel<N1, C, CFG><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(src, p);
+    const long long tasks = (long long)src.ntiles * src.nsteps;
+    const int grid = tasks < grid_of[dev] ? (int)tasks : grid_of[dev];
+    sweep_flow_kernel<N1, C, CFG><<<grid, F::THREADS, F::SMEM, s>>>(src, p);
     return cudaGetLastError();
 }
 
