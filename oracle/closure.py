@@ -20,7 +20,11 @@ definition written out, numpy in FP64:
 * neighbourhood -- the normalised features of the 3 x 3 periodic neighbourhood, 54 per cell.
 * MLP 54 -> 128 -> 128 -> 12 with the exact GELU z Phi(z); forward, mean squared loss and its
   gradient by the chain rule.
-* closure_step -- one coarse step with the learned correction added after the BGK collision.
+* noneq_coefficients -- n_k = sum_l (f - f_eq)_l psi_k(c_l), f_eq at each cell's own moments:
+  the non-equilibrium part of a state in the basis (the closure's training target).
+* closure_step -- one learned coarse step: stream, then every cell's post-collision state is
+  f_eq(rho, u, T) + w sum_k o_k psi_k with the network's o (the non-conserved moments come
+  from the network, the conserved ones from the streaming).
 * bf16_round -- round to the nearest bfloat16 (ties to even), the encoding the GPU network's
   operands use.
 """
@@ -227,6 +231,22 @@ def bf16_round(a) -> np.ndarray:
 # One learned coarse step
 # ----------------------------------------------------------------------------------------------
 
+def equilibrium_field(oracle, f: np.ndarray) -> np.ndarray:
+    """f_eq(rho, u, T) of every cell, at the cell's own moments (the oracle's equilibrium)."""
+    rho, ux, uy, T = oracle.moments(f)
+    out = np.empty_like(f)
+    for y in range(f.shape[1]):
+        for x in range(f.shape[2]):
+            out[:, y, x] = oracle.equilibrium(rho[y, x], ux[y, x], uy[y, x], T[y, x])
+    return out
+
+
+def noneq_coefficients(oracle, f=None) -> np.ndarray:
+    """n[ny * nx, 12]: projection of f - f_eq(moments of f) on the basis."""
+    f = oracle.f if f is None else f
+    return project(f - equilibrium_field(oracle, f), oracle.vs).reshape(-1, N_OUT)
+
+
 def closure_coefficients(oracle, p: dict, mu, inv_sigma, out_scale, f=None) -> np.ndarray:
     """o[ny * nx, 12] = out_scale * MLP(normalised 3 x 3 features of the stored state f)."""
     f = oracle.f if f is None else f
@@ -236,10 +256,11 @@ def closure_coefficients(oracle, p: dict, mu, inv_sigma, out_scale, f=None) -> n
 
 
 def closure_step(oracle, p: dict, mu, inv_sigma, out_scale) -> np.ndarray:
-    """Advance oracle.f by one coarse step: stream, BGK collision, then the learned correction
-    whose coefficients come from the state before the step.  Returns the coefficients used."""
+    """Advance oracle.f by one learned coarse step: the coefficients come from the state before
+    the step; stream; each cell becomes f_eq(its moments) + the correction.  Returns the
+    coefficients used."""
     o = closure_coefficients(oracle, p, mu, inv_sigma, out_scale)
-    nxt = oracle.collide_only(oracle.stream_only())
-    nxt += correction(o.reshape(oracle.ny, oracle.nx, N_OUT), oracle.vs)
+    streamed = oracle.stream_only()
+    nxt = equilibrium_field(oracle, streamed) + correction(o.reshape(oracle.ny, oracle.nx, N_OUT), oracle.vs)
     oracle.f[...] = nxt
     return o

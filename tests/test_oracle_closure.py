@@ -200,3 +200,33 @@ def test_closure_step_conserves_mass_momentum_energy():
     assert np.max(np.abs(coeffs)) > 1e-5  # the correction is not trivially zero
     s1 = o.conserved_sums()
     assert np.max(np.abs(s1 - s0)) < 1e-12 * max(1.0, abs(s0[0]))
+
+
+def test_noneq_coefficients_of_constructed_states(vs):
+    nx, ny = 3, 2
+    o = oracle.Oracle(nx, ny, "D2Q16")
+    rng = np.random.default_rng(12)
+    f = np.zeros((16, ny, nx))
+    for y in range(ny):
+        for x in range(nx):
+            f[:, y, x] = o.equilibrium(1 + 0.05 * rng.normal(), 0.05 * rng.normal(), 0.05 * rng.normal(),
+                                       1 + 0.05 * rng.normal())
+    assert np.max(np.abs(cl.noneq_coefficients(o, f))) < 1e-15
+    a = rng.normal(size=(ny, nx, 12)) * 1e-3
+    g = f + cl.correction(a, vs)
+    assert np.max(np.abs(cl.noneq_coefficients(o, g) - a.reshape(-1, 12))) < 1e-15
+
+
+def test_closure_step_with_zero_network_is_bgk_with_unit_relaxation():
+    """All-zero network output: the learned step reduces to stream + BGK with dt / tau = 1."""
+    import workloads
+    nx, ny = 10, 6
+    fields = workloads.random_smooth(nx, ny, seed=13, amp_u=0.05, amp_T=0.03)
+    a = oracle.Oracle(nx, ny, "D2Q16", tau=0.7)
+    a.init_moments(*fields)
+    b = oracle.Oracle(nx, ny, "D2Q16", tau=1.0)
+    b.set_populations(a.f)
+    p = {name: np.zeros(shape) for name, shape in cl.PARAM_SHAPES}
+    cl.closure_step(a, p, np.zeros(6), np.ones(6), np.ones(12))
+    b.run(1)
+    assert np.max(np.abs(a.f - b.f)) < 1e-15
