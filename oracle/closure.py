@@ -22,8 +22,9 @@ definition written out, numpy in FP64:
   gradient by the chain rule.
 * noneq_coefficients -- n_k = sum_l (f - f_eq)_l psi_k(c_l), f_eq at each cell's own moments:
   the non-equilibrium part of a state in the basis.
-* closure_step -- one learned coarse step: stream, BGK collision, then the network's
-  correction, its coefficients taken from the state before the step.
+* closure_step -- one learned coarse step: stream, then every cell becomes f_eq(rho, u, T)
+  + w sum_k o_k psi_k with the network's o computed from the streamed state (the conserved
+  moments come from the streaming, the non-conserved ones from the network).
 * bf16_round -- round to the nearest bfloat16 (ties to even), the encoding the GPU network's
   operands use.
 """
@@ -255,10 +256,11 @@ def closure_coefficients(oracle, p: dict, mu, inv_sigma, out_scale, f=None) -> n
 
 
 def closure_step(oracle, p: dict, mu, inv_sigma, out_scale) -> np.ndarray:
-    """Advance oracle.f by one learned coarse step: the coefficients come from the state before
-    the step; stream, BGK collision, add the correction.  Returns the coefficients used."""
-    o = closure_coefficients(oracle, p, mu, inv_sigma, out_scale)
-    nxt = oracle.collide_only(oracle.stream_only())
-    nxt += correction(o.reshape(oracle.ny, oracle.nx, N_OUT), oracle.vs)
+    """Advance oracle.f by one learned coarse step: stream; the coefficients come from the
+    streamed state; each cell becomes f_eq(its moments) + the correction.  Returns the
+    coefficients used."""
+    streamed = oracle.stream_only()
+    o = closure_coefficients(oracle, p, mu, inv_sigma, out_scale, f=streamed)
+    nxt = equilibrium_field(oracle, streamed) + correction(o.reshape(oracle.ny, oracle.nx, N_OUT), oracle.vs)
     oracle.f[...] = nxt
     return o

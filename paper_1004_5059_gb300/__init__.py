@@ -28,6 +28,8 @@ TVLBM_ENONFINITE = -6
 TVLBM_D2Q9, TVLBM_D2Q16, TVLBM_D2Q36 = 9, 16, 36
 TVLBM_FP64, TVLBM_FP32, TVLBM_BF16_DEV, TVLBM_FP16_DEV, TVLBM_FP32_DEV = 0, 1, 2, 3, 4
 TVLBM_FORM_PLAIN, TVLBM_FORM_TILED, TVLBM_FORM_FLOW = 0, 1, 2
+TVLBM_MLP_IN, TVLBM_MLP_IN_PAD, TVLBM_MLP_HIDDEN = 54, 64, 128
+TVLBM_MLP_OUT, TVLBM_MLP_OUT_PAD, TVLBM_MLP_PARAMS = 12, 16, 25100
 TVLBM_BC_PERIODIC, TVLBM_BC_WALLS = 0, 1
 
 VELSETS = {"D2Q9": TVLBM_D2Q9, "D2Q16": TVLBM_D2Q16, "D2Q36": TVLBM_D2Q36}
@@ -55,6 +57,7 @@ _D = ctypes.c_double
 _DP = ctypes.POINTER(ctypes.c_double)
 _IP = ctypes.POINTER(ctypes.c_int)
 _SZ = ctypes.c_size_t
+_FP = ctypes.POINTER(ctypes.c_float)
 
 
 def _load_library() -> ctypes.CDLL:
@@ -104,6 +107,23 @@ def _load_library() -> ctypes.CDLL:
         "tvlbm_batch_last_error": (ctypes.c_char_p, [_P]),
         "tvlbm_last_error": (ctypes.c_char_p, [_P]),
         "tvlbm_strerror": (ctypes.c_char_p, [_I]),
+        # learned closure (include/tvlbm_closure.h)
+        "tvlbm_mlp_create": (_I, [_I, ctypes.POINTER(_P)]),
+        "tvlbm_mlp_destroy": (_I, [_P]),
+        "tvlbm_mlp_set_stream": (_I, [_P, _P]),
+        "tvlbm_mlp_set_params": (_I, [_P, _FP]),
+        "tvlbm_mlp_get_params": (_I, [_P, _FP]),
+        "tvlbm_mlp_forward": (_I, [_P, _P, _I, _P]),
+        "tvlbm_mlp_loss_grad": (_I, [_P, _P, _P, _I, _DP, _FP]),
+        "tvlbm_mlp_adam": (_I, [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
+        "tvlbm_mlp_last_error": (ctypes.c_char_p, [_P]),
+        "tvlbm_closure_moments": (_I, [_P, _P]),
+        "tvlbm_closure_features": (_I, [_P, _FP, _FP, _P]),
+        "tvlbm_closure_project": (_I, [_P, _P, _FP, _P]),
+        "tvlbm_closure_noneq": (_I, [_P, _FP, _P]),
+        "tvlbm_downsample": (_I, [_P, _P]),
+        "tvlbm_copy_state": (_I, [_P, _P]),
+        "tvlbm_step_closure": (_I, [_P, _P, _FP, _FP, _FP, _I]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -438,3 +458,129 @@ class Batch:
 
     def bytes_per_cell(self) -> float:
         return float(_lib.tvlbm_batch_bytes_per_cell(self.handle))
+
+
+# ----------------------------------------------------------------------------------------------
+# Learned coarse-grid closure (include/tvlbm_closure.h)
+# ----------------------------------------------------------------------------------------------
+
+def _fp(a: np.ndarray):
+    assert a.dtype == np.float32 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_FP)
+
+
+def _f32(a, n):
+    out = np.ascontiguousarray(np.asarray(a, dtype=np.float32).ravel())
+    assert out.size == n
+    return out
+
+
+def _mcheck(rc: int, m=None):
+    if rc != TVLBM_OK:
+        msg = _lib.tvlbm_mlp_last_error(m).decode() if m else ""
+        raise TvlbmError(rc, msg or _lib.tvlbm_strerror(rc).decode())
+
+
+def _dev_ptr(t, dtype=None, shape=None):
+    """Device address of a contiguous CUDA tensor (checked dtype / shape)."""
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError("expected dtype %s, got %s" % (dtype, t.dtype))
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError("expected shape %s, got %s" % (shape, tuple(t.shape)))
+    return _P(t.data_ptr())
+
+
+class Mlp:
+    """The closure network (54 -> 128 -> 128 -> 12, GELU) on the library's tensor-core kernels.
+    Inputs are BF16 torch tensors [rows][64]; outputs and targets FP32 [rows][16]."""
+
+    def __init__(self, max_rows: int, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("the closure network needs a CUDA GPU")
+        h = _P()
+        _mcheck(_lib.tvlbm_mlp_create(int(max_rows), ctypes.byref(h)))
+        self.handle = h
+        self.max_rows = int(max_rows)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = s
+        _mcheck(_lib.tvlbm_mlp_set_stream(h, _P(s.cuda_stream)), h)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.tvlbm_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, theta):
+        _mcheck(_lib.tvlbm_mlp_set_params(self.handle, _fp(_f32(theta, TVLBM_MLP_PARAMS))), self.handle)
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(TVLBM_MLP_PARAMS, dtype=np.float32)
+        _mcheck(_lib.tvlbm_mlp_get_params(self.handle, _fp(out)), self.handle)
+        return out
+
+    def forward(self, x, y):
+        import torch
+        rows = x.shape[0]
+        _mcheck(_lib.tvlbm_mlp_forward(self.handle, _dev_ptr(x, torch.bfloat16, (rows, TVLBM_MLP_IN_PAD)), rows,
+                                       _dev_ptr(y, torch.float32, (rows, TVLBM_MLP_OUT_PAD))), self.handle)
+
+    def loss_grad(self, x, ystar, want_loss=True, want_grad=False):
+        import torch
+        rows = x.shape[0]
+        loss = ctypes.c_double(0.0)
+        grad = np.zeros(TVLBM_MLP_PARAMS, dtype=np.float32) if want_grad else None
+        _mcheck(_lib.tvlbm_mlp_loss_grad(self.handle, _dev_ptr(x, torch.bfloat16, (rows, TVLBM_MLP_IN_PAD)),
+                                         _dev_ptr(ystar, torch.float32, (rows, TVLBM_MLP_OUT_PAD)), rows,
+                                         ctypes.byref(loss) if want_loss else None,
+                                         _fp(grad) if want_grad else None), self.handle)
+        return (loss.value if want_loss else None), grad
+
+    def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        _mcheck(_lib.tvlbm_mlp_adam(self.handle, float(lr), float(beta1), float(beta2), float(eps)), self.handle)
+
+
+def closure_moments(sim, m6):
+    import torch
+    _check(_lib.tvlbm_closure_moments(sim.ctx, _dev_ptr(m6, torch.float32, (6, sim.ny, sim.nx))), sim.ctx)
+
+
+def closure_features(sim, mu, inv_sigma, x):
+    import torch
+    _check(_lib.tvlbm_closure_features(sim.ctx, _fp(_f32(mu, 6)), _fp(_f32(inv_sigma, 6)),
+                                       _dev_ptr(x, torch.bfloat16, (sim.nx * sim.ny, TVLBM_MLP_IN_PAD))), sim.ctx)
+
+
+def closure_project(a, b, o, inv_scale=None):
+    import torch
+    isc = _fp(_f32(inv_scale, TVLBM_MLP_OUT)) if inv_scale is not None else None
+    _check(_lib.tvlbm_closure_project(a.ctx, b.ctx, isc,
+                                      _dev_ptr(o, torch.float32, (a.nx * a.ny, TVLBM_MLP_OUT_PAD))), a.ctx)
+
+
+def closure_noneq(sim, o, inv_scale=None):
+    import torch
+    isc = _fp(_f32(inv_scale, TVLBM_MLP_OUT)) if inv_scale is not None else None
+    _check(_lib.tvlbm_closure_noneq(sim.ctx, isc, _dev_ptr(o, torch.float32, (sim.nx * sim.ny, TVLBM_MLP_OUT_PAD))),
+           sim.ctx)
+
+
+def downsample(fine, coarse):
+    _check(_lib.tvlbm_downsample(fine.ctx, coarse.ctx), coarse.ctx)
+
+
+def copy_state(src, dst):
+    _check(_lib.tvlbm_copy_state(src.ctx, dst.ctx), dst.ctx)
+
+
+def step_closure(sim, mlp, mu, inv_sigma, out_scale, n=1):
+    _check(_lib.tvlbm_step_closure(sim.ctx, mlp.handle, _fp(_f32(mu, 6)), _fp(_f32(inv_sigma, 6)),
+                                   _fp(_f32(out_scale, TVLBM_MLP_OUT)), int(n)), sim.ctx)

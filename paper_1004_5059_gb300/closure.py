@@ -1,0 +1,402 @@
+"""Learned coarse-grid closure: training data from fine runs, training, evaluation.
+
+Every arithmetic step runs in the library's kernels (include/tvlbm_closure.h): fine and coarse
+time steps, block averaging, features, projections, the network's forward and backward passes
+and Adam.  PyTorch only holds device buffers and gathers training rows; numpy only computes the
+normalisation statistics from a sample copied to the host.
+
+Recipe (D2Q16, periodic, FP32 deviation storage):
+  * fine run nf x nf, tau_f, seeded C3-style fields (Gaussian temperature bump + random
+    Fourier flow of the seed's Mach number);
+  * coarse grid nc = nf / m, coarse step = m fine steps (dx and dt both m times larger, so the
+    velocity set and dt = 1 are unchanged) and tau_c - 1/2 = (tau_f - 1/2) / m (the same
+    physical viscosity apart from the schemes' numerical diffusion, which the closure learns);
+  * learned coarse step: stream, then every cell becomes f_eq(rho, u, T) + w sum_k o_k psi_k,
+    o predicted by the network from the 3 x 3 features of the streamed state; so the state
+    after step t is S(t) = f_eq(M(t)) + w psi o(t);
+  * target o*(t): the coefficients that make the streaming of f_eq(M(t)) + w psi o reproduce
+    the block-averaged fine run's conserved fields M(t + 1).  Streaming is linear, so those
+    fields are the streamed equilibrium's plus K o, K the streaming of the basis vectors'
+    moments; per wavevector, o(k) = K^H (K K^H + lambda s I)^-1 r(k), r the mismatch
+    (Tikhonov-regularised minimum-norm solution, s = mean tr(K K^H) / 4);
+  * inputs: the features of the streamed state P(t) = stream(S(t - 1)), S(t - 1) built from the
+    fine run's M(t - 1) and the previous target o*(t - 1) (teacher forcing), the form the
+    network meets when it runs.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+import time
+
+import numpy as np
+
+import paper_1004_5059_gb300 as tv
+import workloads
+
+
+@dataclasses.dataclass
+class ClosureConfig:
+    nf: int = 1024            # fine grid side
+    m: int = 4                # coarse-graining factor
+    tau_f: float = 0.8
+    snapshots: int = 48       # coarse steps of training data per seed
+    warm: int = 8             # coarse steps skipped before the first sample (fields develop Pi^neq)
+    train_seeds: tuple = (101, 102, 103, 104, 105, 106)
+    test_seeds: tuple = (201, 202)
+    mach: tuple = (0.05, 0.3)
+    batch: int = 16384
+    iters: int = 3000
+    lr: float = 2e-3
+    init_seed: int = 7
+    lam: float = 1e-2         # Tikhonov weight of the target solve
+    active: int = 6           # corrected basis vectors: the first `active` (2: stress, 6: + order 3)
+
+    @property
+    def nc(self) -> int:
+        return self.nf // self.m
+
+    @property
+    def tau_c(self) -> float:
+        return 0.5 + (self.tau_f - 0.5) / self.m
+
+
+def mach_of(seed: int, lo: float, hi: float) -> float:
+    return float(np.random.default_rng(seed).uniform(lo, hi))
+
+
+def fine_fields(cfg: ClosureConfig, seed: int):
+    return workloads.gaussian_bump_random_flow(cfg.nf, cfg.nf, seed=seed, amp_u=mach_of(seed, *cfg.mach),
+                                               sigma=cfg.nf / 16.0)
+
+
+def _fine_sim(cfg, seed, stream=None):
+    s = tv.Simulation(cfg.nf, cfg.nf, "D2Q16", tau=cfg.tau_f, storage="fp32_dev", stream=stream)
+    try:
+        s.set_form("flow")
+    except tv.TvlbmError:
+        pass
+    s.init_moments(*fine_fields(cfg, seed))
+    return s
+
+
+def _coarse_sim(cfg, stream=None):
+    return tv.Simulation(cfg.nc, cfg.nc, "D2Q16", tau=cfg.tau_c, storage="fp32_dev", stream=stream)
+
+
+def nonconserved_basis_host():
+    """psi[12][16] from the library's D2Q16 nodes, in the order of include/tvlbm_closure.h."""
+    cx, cy, w, _ = tv.tvlbm_velocity_set(tv.TVLBM_D2Q16)
+
+    def he(n, x):
+        a, b = np.ones_like(x), np.array(x, dtype=np.float64)
+        if n == 0:
+            return a
+        for k in range(1, n):
+            a, b = b, x * b - k * a
+        return b
+    pairs = [(-1, -1), (1, 1), (3, 0), (2, 1), (1, 2), (0, 3), (3, 1), (2, 2), (1, 3), (3, 2), (2, 3), (3, 3)]
+    psi = np.zeros((12, 16))
+    for k, (a, b) in enumerate(pairs):
+        psi[k] = 0.5 * (he(2, cx) - he(2, cy)) if a < 0 else he(a, cx) * he(b, cy) / math.sqrt(
+            math.factorial(a) * math.factorial(b))
+    return cx, cy, w, psi
+
+
+class TargetSolver:
+    """Correction coefficients from the conserved-field mismatch after the next coarse step:
+    delta(k) = K^H (K K^H + lambda s I)^-1 r(k) per wavevector of the periodic nc x nc grid."""
+
+    def __init__(self, nc: int, lam: float, active: int = 12):
+        cx, cy, w, psi = nonconserved_basis_host()
+        psi = psi[:active]
+        self.active = active
+        sx, sy, ax, ay = tv.tvlbm_stream_table(tv.TVLBM_D2Q16, 1.0)
+        k = 2.0 * np.pi * np.fft.fftfreq(nc)
+        KX, KY = np.meshgrid(k, k)  # arrays are [y][x]
+        phi = np.stack([np.ones(16), cx, cy, 0.5 * (cx * cx + cy * cy)])
+        K = np.zeros((nc, nc, 4, active), dtype=complex)
+        for l in range(16):
+            # the pull-gather moves population l by s = n + alpha per axis:
+            # g(x) = (1 - alpha) f(x - n) + alpha f(x - n - 1)
+            gx = (1 - ax[l]) * np.exp(-1j * KX * sx[l]) + ax[l] * np.exp(-1j * KX * (sx[l] + 1))
+            gy = (1 - ay[l]) * np.exp(-1j * KY * sy[l]) + ay[l] * np.exp(-1j * KY * (sy[l] + 1))
+            K += (gx * gy)[:, :, None, None] * (phi[:, l][:, None] * w[l] * psi[:, l][None, :])[None, None]
+        KH = np.conj(np.swapaxes(K, -1, -2))
+        A = K @ KH
+        s = float(np.mean(np.trace(A, axis1=-2, axis2=-1).real)) / 4.0
+        self.P = KH @ np.linalg.inv(A + lam * s * np.eye(4))  # [ny][nx][active][4]
+
+    def solve(self, r: np.ndarray) -> np.ndarray:
+        """r[4][ny][nx] (mass, x and y momentum, energy) -> delta[12][ny][nx] (zero beyond the
+        active vectors)."""
+        rh = np.fft.fft2(r, axes=(1, 2))
+        dh = np.einsum("yxkm,myx->kyx", self.P, rh)
+        out = np.zeros((12,) + r.shape[1:])
+        out[:self.active] = np.real(np.fft.ifft2(dh, axes=(1, 2)))
+        return out
+
+
+def conserved_of(rho, ux, uy, T) -> np.ndarray:
+    """(rho, rho u_x, rho u_y, rho (|u|^2 / 2 + T)) from primitive fields."""
+    return np.stack([rho, rho * ux, rho * uy, rho * (0.5 * (ux * ux + uy * uy) + T)])
+
+
+def conserved_fields(sim) -> np.ndarray:
+    """Conserved fields of a context, FP64 on the host."""
+    return conserved_of(*sim.moments())
+
+
+def correction_host(o: np.ndarray, w: np.ndarray, psi: np.ndarray) -> np.ndarray:
+    """Delta f[16][ny][nx] = w_l sum_k o_k psi_k(c_l) for o[12][ny][nx]."""
+    return np.einsum("kl,kyx->lyx", psi, o) * w[:, None, None]
+
+
+class _Samples:
+    """Walks one fine run; each call of next() returns (P, o*) for the next coarse time t: a
+    context holding the streamed state P(t) = stream(f_eq(M(t - 1)) + w psi o*(t - 1)) and the
+    target o*(t) [12][ny][nx]."""
+
+    def __init__(self, cfg: ClosureConfig, seed: int, solver: TargetSolver):
+        self.cfg, self.solver = cfg, solver
+        _, _, self.w, self.psi = nonconserved_basis_host()
+        self.fine = _fine_sim(cfg, seed)
+        self.D = _coarse_sim(cfg)
+        # collisionless contexts: their step is the streaming alone
+        self.E = tv.Simulation(cfg.nc, cfg.nc, "D2Q16", tau=float("inf"), storage="fp32_dev")
+        self.P = tv.Simulation(cfg.nc, cfg.nc, "D2Q16", tau=float("inf"), storage="fp32_dev")
+        self.fine.step(cfg.m * cfg.warm)
+        self.prims = [self._fields()]  # M(t - 1), M(t), M(t + 1)
+        for _ in range(2):
+            self.fine.step(cfg.m)
+            self.prims.append(self._fields())
+        # o*(t - 1) from M(t - 1) -> M(t)
+        self.o_prev = self._target(self.prims[0], self.prims[1])
+
+    def _fields(self):
+        tv.downsample(self.fine, self.D)
+        return self.D.moments()
+
+    def _target(self, now, nxt):
+        """o* taking the streaming of f_eq(now) onto the conserved fields of nxt."""
+        self.E.init_moments(*now)
+        self.E.step(1)
+        return self.solver.solve(conserved_of(*nxt) - conserved_fields(self.E))
+
+    def next(self):
+        o = self._target(self.prims[1], self.prims[2])
+        self.P.init_moments(*self.prims[0])
+        f = self.P.populations_f64()
+        self.P.set_populations_f64(f + correction_host(self.o_prev, self.w, self.psi))
+        self.P.step(1)
+        return self.P, o
+
+    def advance(self, o):
+        self.o_prev = o
+        self.fine.step(self.cfg.m)
+        self.prims = self.prims[1:] + [self._fields()]
+
+    def close(self):
+        for s in (self.fine, self.D, self.E, self.P):
+            s.close()
+
+
+@dataclasses.dataclass
+class Normalisation:
+    mu: np.ndarray         # [6]
+    inv_sigma: np.ndarray  # [6]
+    out_scale: np.ndarray  # [12]
+
+
+def statistics(cfg: ClosureConfig, seed: int, solver: TargetSolver, samples: int = 8) -> Normalisation:
+    """Feature means / spreads and target spreads from `samples` snapshots of one training run."""
+    import torch
+    nc = cfg.nc
+    m6 = torch.zeros((6, nc, nc), dtype=torch.float32, device="cuda")
+    walk = _Samples(cfg, seed, solver)
+    feats, targs = [], []
+    stride = max(1, cfg.snapshots // samples)
+    for n in range(cfg.snapshots):
+        S, o = walk.next()
+        if n % stride == 0:
+            tv.closure_moments(S, m6)
+            feats.append(m6.cpu().numpy().reshape(6, -1).astype(np.float64))
+            targs.append(o.reshape(12, -1))
+        walk.advance(o)
+    walk.close()
+    F = np.concatenate(feats, axis=1)
+    Y = np.concatenate(targs, axis=1)
+    mu = F.mean(axis=1)
+    sd = F.std(axis=1)
+    ys = Y.std(axis=1)
+    return Normalisation(mu=mu, inv_sigma=1.0 / np.maximum(sd, 1e-12), out_scale=np.maximum(ys, 1e-12))
+
+
+def generate(cfg: ClosureConfig, seeds, norm: Normalisation, solver: TargetSolver):
+    """Device tensors X (BF16 [rows][64]) and Y (FP32 [rows][16]) of every sample of `seeds`."""
+    import torch
+    cells = cfg.nc * cfg.nc
+    rows = len(seeds) * cfg.snapshots * cells
+    X = torch.zeros((rows, 64), dtype=torch.bfloat16, device="cuda")
+    Y = torch.zeros((rows, 16), dtype=torch.float32, device="cuda")
+    yh = np.zeros((cells, 16), dtype=np.float32)
+    r = 0
+    for seed in seeds:
+        walk = _Samples(cfg, seed, solver)
+        for _ in range(cfg.snapshots):
+            S, o = walk.next()
+            tv.closure_features(S, norm.mu, norm.inv_sigma, X[r:r + cells])
+            yh[:, :12] = (o.reshape(12, -1) / norm.out_scale[:, None]).T
+            Y[r:r + cells].copy_(torch.from_numpy(yh))
+            walk.advance(o)
+            r += cells
+        walk.close()
+    torch.cuda.synchronize()
+    return X, Y
+
+
+def initial_params(seed: int) -> np.ndarray:
+    """Uniform fan-in scaled weights, zero biases, a small last layer (the correction starts
+    near zero)."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for shape, fan_in, s in [((128, 54), 54, 1.0), ((128,), 1, 0.0), ((128, 128), 128, 1.0), ((128,), 1, 0.0),
+                             ((12, 128), 128, 0.1), ((12,), 1, 0.0)]:
+        parts.append((rng.uniform(-1, 1, size=shape) * s * math.sqrt(3.0 / fan_in)).ravel())
+    return np.concatenate(parts).astype(np.float32)
+
+
+def train(cfg: ClosureConfig, X, Y, log_every: int = 0):
+    """Adam on random batches of 128-row blocks; returns the network and the loss history."""
+    import torch
+    rows = X.shape[0]
+    blocks = rows // 128
+    bb = cfg.batch // 128
+    net = tv.Mlp(max(cfg.batch, cfg.nc * cfg.nc))  # the same network later steps the whole coarse grid
+    net.set_params(initial_params(cfg.init_seed))
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(cfg.init_seed)
+    xb = torch.empty((cfg.batch, 64), dtype=torch.bfloat16, device="cuda")
+    yb = torch.empty((cfg.batch, 16), dtype=torch.float32, device="cuda")
+    Xv, Yv = X.view(blocks, 128, 64), Y.view(blocks, 128, 16)
+    history = []
+    for it in range(cfg.iters):
+        idx = torch.randint(0, blocks, (bb,), device="cuda", generator=gen)
+        torch.index_select(Xv, 0, idx, out=xb.view(bb, 128, 64))
+        torch.index_select(Yv, 0, idx, out=yb.view(bb, 128, 16))
+        want = log_every and (it % log_every == 0 or it == cfg.iters - 1)
+        loss, _ = net.loss_grad(xb, yb, want_loss=bool(want))
+        if want:
+            history.append((it, loss))
+        lr = cfg.lr * 0.5 * (1.0 + math.cos(math.pi * it / cfg.iters))  # cosine decay
+        net.adam(lr)
+    return net, history
+
+
+def field_errors(got, want):
+    """Max relative errors of (rho, u, T): |a - b|_max / |b|_max per field, u over both components."""
+    e_rho = float(np.max(np.abs(got[0] - want[0])) / np.max(np.abs(want[0])))
+    umax = max(np.max(np.abs(want[1])), np.max(np.abs(want[2])))
+    e_u = float(max(np.max(np.abs(got[1] - want[1])), np.max(np.abs(got[2] - want[2]))) / umax)
+    e_T = float(np.max(np.abs(got[3] - want[3])) / np.max(np.abs(want[3])))
+    return {"rho": e_rho, "u": e_u, "T": e_T}
+
+
+def rms_errors(got, want):
+    """RMS errors of (rho - rho_ref, u, T - T_ref) relative to the reference's RMS deviation."""
+    out = {}
+    for k, name in enumerate(["rho", "ux", "uy", "T"]):
+        ref = want[k] - (want[k].mean() if name in ("rho", "T") else 0.0)
+        out[name] = float(np.sqrt(np.mean((got[k] - want[k]) ** 2)) / max(np.sqrt(np.mean(ref ** 2)), 1e-300))
+    return out
+
+
+def evaluate(cfg: ClosureConfig, net, norm: Normalisation, seed: int, steps: int):
+    """Fine run (the judge), plain coarse run and learned coarse run from the same start, `steps`
+    coarse steps after `warm`; errors of both coarse runs against the block-averaged fine run."""
+    fine = _fine_sim(cfg, seed)
+    fine.step(cfg.m * cfg.warm)
+    plain, learned, truth = _coarse_sim(cfg), _coarse_sim(cfg), _coarse_sim(cfg)
+    tv.downsample(fine, plain)
+    learned.init_moments(*plain.moments())  # the learned run starts from the equilibrium state
+    fine.step(cfg.m * steps)
+    tv.downsample(fine, truth)
+    plain.step(steps)
+    tv.step_closure(learned, net, norm.mu, norm.inv_sigma, norm.out_scale, steps)
+    want = truth.moments()
+    res = {"plain_coarse": rms_errors(plain.moments(), want), "learned_coarse": rms_errors(learned.moments(), want),
+           "plain_coarse_max": field_errors(plain.moments(), want),
+           "learned_coarse_max": field_errors(learned.moments(), want)}
+    sums = [s.conserved_sums() for s in (truth, plain, learned)]
+    res["mass_drift_learned"] = float(abs(sums[2][0] - sums[1][0]) / sums[1][0])
+    for s in (fine, plain, learned, truth):
+        s.close()
+    return res
+
+
+def trajectory(cfg: ClosureConfig, net, norm: Normalisation, seed: int, checkpoints=(1, 2, 4, 8, 16, 32)):
+    """RMS errors of the plain and learned coarse runs against the block-averaged fine run at
+    each checkpoint (coarse steps after `warm`)."""
+    fine = _fine_sim(cfg, seed)
+    fine.step(cfg.m * cfg.warm)
+    plain, learned, truth = _coarse_sim(cfg), _coarse_sim(cfg), _coarse_sim(cfg)
+    tv.downsample(fine, plain)
+    learned.init_moments(*plain.moments())  # the learned run starts from the equilibrium state
+    out, done = [], 0
+    for n in checkpoints:
+        k = n - done
+        fine.step(cfg.m * k)
+        tv.downsample(fine, truth)
+        plain.step(k)
+        tv.step_closure(learned, net, norm.mu, norm.inv_sigma, norm.out_scale, k)
+        done = n
+        want = truth.moments()
+        out.append({"steps": n, "plain": rms_errors(plain.moments(), want),
+                    "learned": rms_errors(learned.moments(), want)})
+    for s in (fine, plain, learned, truth):
+        s.close()
+    return out
+
+
+def time_runs(cfg: ClosureConfig, net, norm: Normalisation, seed: int, steps: int, repeats: int = 3):
+    """Seconds for `steps` learned coarse steps and for the m * steps fine steps they stand for."""
+    import torch
+    fine = _fine_sim(cfg, seed)
+    learned = _coarse_sim(cfg)
+    tv.downsample(fine, learned)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        fn()
+        ts = []
+        for _ in range(repeats):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b) / 1e3)
+        return sorted(ts)[len(ts) // 2]
+
+    t_learned = timed(lambda: tv.step_closure(learned, net, norm.mu, norm.inv_sigma, norm.out_scale, steps))
+    t_fine = timed(lambda: fine.step(cfg.m * steps))
+    fine.close()
+    learned.close()
+    return t_learned, t_fine
+
+
+def run(cfg: ClosureConfig, eval_steps: int = 32, log_every: int = 500):
+    """Statistics, data, training and evaluation on every test seed; returns a report dict."""
+    t0 = time.perf_counter()
+    solver = TargetSolver(cfg.nc, cfg.lam, cfg.active)
+    norm = statistics(cfg, cfg.train_seeds[0], solver)
+    X, Y = generate(cfg, cfg.train_seeds, norm, solver)
+    t1 = time.perf_counter()
+    net, hist = train(cfg, X, Y, log_every=log_every)
+    t2 = time.perf_counter()
+    del X, Y
+    evals = {seed: evaluate(cfg, net, norm, seed, eval_steps) for seed in cfg.test_seeds}
+    t_learned, t_fine = time_runs(cfg, net, norm, cfg.test_seeds[0], eval_steps)
+    return {"config": dataclasses.asdict(cfg), "norm": {k: v.tolist() for k, v in dataclasses.asdict(norm).items()},
+            "loss_history": hist, "evaluation": evals, "data_seconds": t1 - t0, "train_seconds": t2 - t1,
+            "learned_coarse_seconds": t_learned, "fine_seconds": t_fine, "eval_steps": eval_steps, "net": net}

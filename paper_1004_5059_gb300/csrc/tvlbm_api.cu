@@ -13,6 +13,7 @@
 #include "tvlbm.h"
 #include "tvlbm_host.h"
 #include "tvlbm_kernels.cuh"
+#include "tvlbm_ctx.h"
 
 using namespace tvlbm;
 using namespace tvlbm::host;
@@ -23,26 +24,7 @@ namespace {
 constexpr int kGraphSteps = 32;  // steps per captured graph (even: buffer parity is preserved)
 }  // namespace
 
-struct tvlbm_ctx {
-    int nx, ny, velset, n1, Q, N, storage, form, graphs;
-    double tau, dt, rho0;
-    tvlbm_bc bc;
-    Rule rule;
-    Layout L;
-    KParams kp;
-    const KernelTable* kt;
-    int device;
-    unsigned char* mem;
-    bool own_mem;
-    int cur;
-    cudaStream_t stream;
-    cudaStream_t capture_stream;
-    cudaGraphExec_t graph[2];
-    int have_tmap;
-    int tile_cfg;                     // tiled-form tile configuration
-    alignas(64) CUtensorMap tmap[2];  // TMA descriptors: input windows of buffer b
-    char err[512];
-};
+
 
 namespace {
 

@@ -1,0 +1,31 @@
+// Private: the single-domain context behind the opaque tvlbm_ctx handle of include/tvlbm.h,
+// shared by the translation units that launch work on it (tvlbm_api.cu, tvlbm_closure.cu).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "tvlbm.h"
+#include "tvlbm_host.h"
+#include "tvlbm_kernels.cuh"
+
+struct tvlbm_ctx {
+    int nx, ny, velset, n1, Q, N, storage, form, graphs;
+    double tau, dt, rho0;
+    tvlbm_bc bc;
+    tvlbm::host::Rule rule;
+    tvlbm::host::Layout L;
+    tvlbm::KParams kp;
+    const tvlbm::KernelTable* kt;
+    int device;
+    unsigned char* mem;
+    bool own_mem;
+    int cur;
+    cudaStream_t stream;
+    cudaStream_t capture_stream;
+    cudaGraphExec_t graph[2];
+    int have_tmap;
+    int tile_cfg;                     // tiled-form tile configuration
+    alignas(64) CUtensorMap tmap[2];  // TMA descriptors: input windows of buffer b
+    char err[512];
+};

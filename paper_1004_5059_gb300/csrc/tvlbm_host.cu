@@ -22,6 +22,8 @@ long double hermite_he(int n, long double x) {
     return b;
 }
 
+}  // namespace
+
 // The driver's cuTensorMapEncodeTiled, looked up once through the runtime (the library does
 // not link libcuda).
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
@@ -37,8 +39,6 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     }
     return fn;
 }
-
-}  // namespace
 
 // =============================================================================================
 // Velocity sets: n-point Gauss quadrature for the weight exp(-x^2/2)/sqrt(2 pi).  The nodes

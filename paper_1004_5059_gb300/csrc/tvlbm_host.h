@@ -56,6 +56,8 @@ void set_reference_params(KParams& p, const Rule& r, double rho0, double ux, dou
 
 // TMA descriptor of one population buffer: a 3-D view [Q][rows][pitch], box bx x by x 1.
 bool encode_tensor_map(CUtensorMap* m, void* base, int storage, const Layout& L, int Q, int bx, int by);
+// The driver's cuTensorMapEncodeTiled (null if the driver does not provide it).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 
 }  // namespace host
 }  // namespace tvlbm

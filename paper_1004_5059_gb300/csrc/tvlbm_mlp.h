@@ -1,0 +1,17 @@
+// Private: what the closure step needs from the network (tvlbm_mlp.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "tvlbm_closure.h"
+
+namespace tvlbm {
+// Forward pass of `rows` rows of x (device BF16 [rows][64]) into y (device FP32 [rows][16]),
+// queued on the network's stream.  TVLBM_* status.
+int mlp_forward_async(tvlbm_mlp* m, const void* x, int rows, float* y);
+int mlp_max_rows(const tvlbm_mlp* m);
+float* mlp_ybuf(tvlbm_mlp* m);  // the network's own [max_rows][16] output buffer
+void* mlp_xbuf(tvlbm_mlp* m);   // max_rows x 64 BF16 of scratch (training reuses it)
+int mlp_set_stream(tvlbm_mlp* m, cudaStream_t s);
+int mlp_status(tvlbm_mlp* m);  // synchronises; ETIMEOUT if a device wait gave up
+}  // namespace tvlbm

@@ -217,14 +217,14 @@ def test_noneq_coefficients_of_constructed_states(vs):
     assert np.max(np.abs(cl.noneq_coefficients(o, g) - a.reshape(-1, 12))) < 1e-15
 
 
-def test_closure_step_with_zero_network_is_the_plain_step():
-    """All-zero network output: the learned step is the method's own step."""
+def test_closure_step_with_zero_network_is_bgk_with_unit_relaxation():
+    """All-zero network output: the learned step reduces to stream + BGK with dt / tau = 1."""
     import workloads
     nx, ny = 10, 6
     fields = workloads.random_smooth(nx, ny, seed=13, amp_u=0.05, amp_T=0.03)
     a = oracle.Oracle(nx, ny, "D2Q16", tau=0.7)
     a.init_moments(*fields)
-    b = oracle.Oracle(nx, ny, "D2Q16", tau=0.7)
+    b = oracle.Oracle(nx, ny, "D2Q16", tau=1.0)
     b.set_populations(a.f)
     p = {name: np.zeros(shape) for name, shape in cl.PARAM_SHAPES}
     cl.closure_step(a, p, np.zeros(6), np.ones(6), np.ones(12))
