@@ -7,7 +7,7 @@ stream+collide sweep over the grid).  Inputs are resident in HBM when a timed st
 L2 is flushed (a 512 MiB write) between timed steps, outside the timed events.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload c1|c1_4096|c0|c2|c3] [--form tiled|flow|plain] [--no-cpu-baseline]
+                  [--workload c1|c1_4096|c0|c2|c3|c4] [--form tiled|flow|plain] [--no-cpu-baseline]
 
 Prints one JSON line.  --impl reference times the FP64 CPU oracle on this machine's host
 cores on the same workload (each step a bounded sample of the time steps).  Under torchrun
@@ -51,6 +51,11 @@ BATCH = dict(desc="256 independent periodic D2Q16 domains, sides drawn from {128
                    "Mach~U[0.05,0.3], seeded fields, FP32 populations; one persistent launch per time step over all "
                    "tiles, CUDA-graph replay, autotuned tile shape; 20 time steps per bench step",
              count=256, seed=3, velset="D2Q16", storage="fp32_dev", tsteps=20)
+
+CLOSURE = dict(desc="learned closure: D2Q16 256x256 periodic coarse run with the 54-128-128-12 GELU network "
+                    "(BF16 tcgen05 kernels, FP32 accumulate), trained on 1024x1024 runs (tau=0.8) downsampled 4x "
+                    "from C3-style seeded fields (random Fourier flow |k| <= 32, Mach U[0.05,0.3]); 32 coarse steps "
+                    "(= 128 fine steps) per bench step; MLUPS counted as fine-grid cell updates represented", nf=1024, m=4, coarse_steps=32)
 
 METRIC = "MLUPS (million lattice-cell updates per second) of the fused TVLBM sweep"
 UNIT = "MLUPS"
@@ -137,6 +142,16 @@ class Clocks:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak_bf16():
+    """Dense BF16 tensor peak in TFLOP/s: the measured burst figure, else the fallback."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["bf16_tflops"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "fallback"
 
 
 def measured_peak_hbm():
@@ -533,19 +548,210 @@ def run_batch_reference(args, rank):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def _closure_setup():
+    from paper_1004_5059_gb300 import closure as C
+    cfg = C.ClosureConfig(nf=CLOSURE["nf"], m=CLOSURE["m"])
+    return C, cfg
+
+
+def run_closure(args, rank, world, local_rank):
+    """Learned coarse run (network trained here first, untimed) against the plain fine run it
+    replaces: fine-equivalent MLUPS, the network's tensor throughput, and the errors of the
+    plain and learned coarse runs against the block-averaged fine run on held-out seeds."""
+    import torch
+    import paper_1004_5059_gb300 as tv
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    C, cfg = _closure_setup()
+    nsteps = CLOSURE["coarse_steps"]
+    t0 = time.perf_counter()
+    solver = C.TargetSolver(cfg.nc, cfg.lam, cfg.active)
+    norm = C.statistics(cfg, cfg.train_seeds[0], solver)
+    X, Y = C.generate(cfg, cfg.train_seeds, norm, solver)
+    t1 = time.perf_counter()
+    net, hist = C.train(cfg, X, Y, log_every=max(1, cfg.iters // 4))
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    del X, Y
+    errors = {str(seed): C.evaluate(cfg, net, norm, seed, nsteps) for seed in cfg.test_seeds}
+    # beyond the bench horizon (the training data cover coarse steps warm .. warm + snapshots)
+    horizon = C.trajectory(cfg, net, norm, cfg.test_seeds[0], checkpoints=(32, 64, 128))
+
+    stream = torch.cuda.current_stream(dev)
+    seed = cfg.test_seeds[0]
+    fine = C._fine_sim(cfg, seed)
+    fine.step(cfg.m * cfg.warm)
+    learned, start = C._coarse_sim(cfg), C._coarse_sim(cfg)
+    tv.downsample(fine, start)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def timed(fn, K, W, reset=None):
+        """K timed calls of fn after W untimed ones; reset() runs before each, outside the events."""
+        for _ in range(W):
+            if reset:
+                reset()
+            fn()
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        evs = []
+        for _ in range(K):
+            if reset:
+                reset()
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs)
+
+    # every bench step: the 32 learned coarse steps from the block-averaged start
+    clocks = Clocks(local_rank)
+    clocks.start()
+    ms = timed(lambda: tv.step_closure(learned, net, norm.mu, norm.inv_sigma, norm.out_scale, nsteps),
+               args.steps, args.warmup, reset=lambda: tv.copy_state(start, learned))
+    clk = clocks.stop()
+    ms_max = max_over_ranks(ms, world, dev)
+    fine_cells = cfg.nf * cfg.nf
+    value = aggregate_mlups(world, fine_cells, cfg.m * nsteps, args.steps, ms_max / 1e3)
+    # the plain fine run over the same physical time (what the learned run replaces)
+    kf = max(1, args.steps // 2)
+    ms_fine = timed(lambda: fine.step(cfg.m * nsteps), kf, 1)
+    fine_value = fine_cells * cfg.m * nsteps * kf / (ms_fine / 1e3) / 1e6
+    # the network alone on the whole coarse grid: the tensor-core kernels' throughput
+    cells = cfg.nc * cfg.nc
+    xb = torch.zeros((cells, 64), dtype=torch.bfloat16, device=dev)
+    yb = torch.zeros((cells, 16), dtype=torch.float32, device=dev)
+    tv.closure_features(start, norm.mu, norm.inv_sigma, xb)
+    reps = 20
+    ms_net = timed(lambda: [net.forward(xb, yb) for _ in range(reps)], 3, 2) / (3 * reps)
+    flops = 2.0 * cells * (64 * 128 + 128 * 128 + 128 * 16)
+    peak, peak_kind = measured_peak_bf16()
+    achieved = flops / (ms_net / 1e3) / 1e12
+    # end to end: host fields in (pinned), the learned steps, host moments out
+    prims = start.moments()
+    pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in prims]
+    out = [torch.empty((cfg.nc, cfg.nc), dtype=torch.float64).pin_memory().numpy() for _ in range(4)]
+    e2e_steps = 3
+    torch.cuda.synchronize()
+    te = time.perf_counter()
+    for _ in range(e2e_steps):
+        learned.init_moments(*pinned)
+        tv.step_closure(learned, net, norm.mu, norm.inv_sigma, norm.out_scale, nsteps)
+        tv.tvlbm_moments(learned.ctx, cfg.nc, cfg.nc, out=out)
+    torch.cuda.synchronize()
+    e2e = aggregate_mlups(world, fine_cells, cfg.m * nsteps, e2e_steps, max_over_ranks(time.perf_counter() - te, world, dev))
+    line = {
+        "metric": METRIC + " (fine-grid cell updates represented by the learned coarse run)", "value": value,
+        "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (bf16 network operands)",
+        "data": "synthetic (seeded C3-style fields)",
+        "config": {"workload": CLOSURE["desc"], "fine": [cfg.nf, cfg.nf], "coarse": [cfg.nc, cfg.nc], "factor": cfg.m,
+                   "tau_fine": cfg.tau_f, "tau_coarse_plain": cfg.tau_c, "coarse_steps_per_bench_step": nsteps,
+                   "train_seeds": list(cfg.train_seeds), "test_seeds": list(cfg.test_seeds),
+                   "samples": len(cfg.train_seeds) * cfg.snapshots * cells, "iters": cfg.iters, "batch": cfg.batch,
+                   "loss_history": hist, "data_seconds": round(t1 - t0, 2), "train_seconds": round(t2 - t1, 2),
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "L2 flushed (512 MiB write) between timed steps"},
+        "errors_vs_block_averaged_fine_run": errors,
+        "rms_errors_longer_horizon": horizon,
+        "plain_fine": {"value": fine_value, "unit": UNIT, "form": "flow", "storage": "fp32_dev",
+                       "note": "the 1024x1024 run over the same physical time"},
+        "speedup_vs_plain_fine": value / fine_value,
+        "roofline": {"bound": "tensor", "kernel": "network forward (3 tcgen05 GEMMs + epilogues) on 65536 rows",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "peak_kind": peak_kind, "flops_per_launch": flops, "traffic": None},
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 4 * 8 * cells, "d2h_bytes_per_step": 4 * 8 * cells},
+        "gpu_launches": args.steps * nsteps * 6,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = closure_cpu_baseline(cfg, net, norm, start)
+    for s_ in (fine, learned, start):
+        s_.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return line if rank == 0 else None
+
+
+def closure_cpu_baseline(cfg, net, norm, coarse, target_s=12.0):
+    """The oracle's learned coarse step (FP64, the trained parameters) on the host cores."""
+    import oracle
+    from oracle import closure as cl
+    cores = _oracle_threads()
+    theta = net.get_params().astype(np.float64)
+    p = cl.unpack(theta)
+    p = {k: cl.bf16_round(v) if k.startswith("W") else v for k, v in p.items()}
+    o = oracle.Oracle(cfg.nc, cfg.nc, "D2Q16", tau=cfg.tau_c, threads=cores)
+    o.set_populations(coarse.populations_f64())
+    t0 = time.perf_counter()
+    cl.closure_step(o, p, norm.mu, norm.inv_sigma, norm.out_scale)
+    one = time.perf_counter() - t0
+    n = int(max(1, min(8, target_s / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    for _ in range(n):
+        cl.closure_step(o, p, norm.mu, norm.inv_sigma, norm.out_scale)
+    dt = time.perf_counter() - t0
+    return {"value": cfg.nf * cfg.nf * cfg.m * n / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d learned coarse steps of the 256x256 grid (fine-equivalent cell updates)" % n}
+
+
+def run_closure_reference(args, rank):
+    """The oracle's learned coarse step with a seeded (untrained) network, timed on the host."""
+    if rank != 0:
+        return None
+    import oracle
+    from oracle import closure as cl
+    C, cfg = _closure_setup()
+    cores = _oracle_threads()
+    o = oracle.Oracle(cfg.nc, cfg.nc, "D2Q16", tau=cfg.tau_c, threads=cores)
+    f = workloads.gaussian_bump_random_flow(cfg.nc, cfg.nc, seed=cfg.test_seeds[0], sigma=cfg.nc / 16.0)
+    o.init_moments(*f)
+    p = cl.init_params(cfg.init_seed, scale=0.5)
+    mu, isg, sc = np.array([1.0, 0, 0, 1.0, 0, 0]), np.array([30.0, 20, 20, 30, 500, 500]), np.full(12, 1e-4)
+    for _ in range(args.warmup):
+        cl.closure_step(o, p, mu, isg, sc)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        cl.closure_step(o, p, mu, isg, sc)
+    dt = time.perf_counter() - t0
+    value = cfg.nf * cfg.nf * cfg.m * args.steps / dt / 1e6
+    return {"impl": "reference", "metric": METRIC + " (fine-grid cell updates represented by the learned coarse run)",
+            "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": CLOSURE["desc"], "sample": "one learned coarse step per bench step (oracle)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "one learned coarse step of the 256x256 grid per bench step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c1", choices=sorted(WORKLOADS) + ["c3"])
+    ap.add_argument("--workload", default="c1", choices=sorted(WORKLOADS) + ["c3", "c4"])
     ap.add_argument("--form", default=None, choices=["tiled", "flow", "plain"],
                     help="sweep form (default: the fastest of tiled and, on periodic domains, flow)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile", type=int, default=-1, help="tile configuration of the tiled form (-1: autotune)")
     args = ap.parse_args()
     rank, world, local_rank = dist_env()
+    if args.workload == "c4":
+        line = run_closure(args, rank, world, local_rank) if args.impl == "ours" else run_closure_reference(args, rank)
+        if rank == 0 and line is not None:
+            print(json.dumps(line))
+        return
     if args.workload == "c3":
         line = run_batch(args, rank, world, local_rank) if args.impl == "ours" else run_batch_reference(args, rank)
         if rank == 0 and line is not None:

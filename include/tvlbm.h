@@ -70,6 +70,13 @@ extern "C" {
                               finished the previous one (no launch boundary between steps).
                               Periodic domains whose size is a multiple of the tile shape only */
 
+/* ---- evolution schemes ------------------------------------------------------------------- */
+#define TVLBM_SCHEME_VOLUMETRIC 0 /* fused BGK collide + area-overlap pull-gather stream (default)   */
+#define TVLBM_SCHEME_FVLB 1       /* the paper's finite-volume update (Sec. "The TVLBM Evolution
+                                     scheme", Eq. FVLB): explicit Euler step of length dt with the
+                                     second-order 9-point stencils for c . grad f and the weighted
+                                     9-point average of the collision term of Eq. OMEGAFVLB         */
+
 /* ---- boundary conditions ----------------------------------------------------------------- */
 #define TVLBM_BC_PERIODIC 0
 #define TVLBM_BC_WALLS 1 /* periodic in x; diffuse walls on the faces y = -1/2 and y = ny - 1/2 */
@@ -123,6 +130,18 @@ int tvlbm_set_stream(tvlbm_ctx *ctx, void *stream);
  * used) and a device-side wait that gives up is reported as ETIMEOUT by the next synchronising
  * call. */
 int tvlbm_set_form(tvlbm_ctx *ctx, int form);
+
+/* Select the evolution scheme.  TVLBM_SCHEME_FVLB: f(t + dt) = f + dt (Omega_bar - c . grad f)
+ * on the unit grid, Omega_l = -(f_l - f_eq_l) / tau + (1 / tau_g) f_eq_l / (rho T^2)
+ * Pi : (c_l - u)(c_l - u) with Pi_ij = sum_l (f_l - f_eq_l)(c_l - u)_i (c_l - u)_j (Eq.
+ * OMEGAFVLB; the Prandtl-number term is applied without its components along the collision
+ * invariants, which an exact Maxwellian would not have; tau_g = +inf leaves it out).  It
+ * shifts the viscosity to T tau tau_g / (tau_g - 2 tau) (the Prandtl number to
+ * tau_g / (tau_g - 2 tau)).  The scheme is explicit: it needs |c| dt well below one cell and
+ * dt well below tau.  Periodic domains, FP64 or FP32 storage; allocates one extra population-
+ * sized buffer (also for contexts created in caller memory).  Errors: EINVAL (walls, storage,
+ * unknown scheme, tau_g = 0 or NaN), ENOMEM. */
+int tvlbm_set_scheme(tvlbm_ctx *ctx, int scheme, double tau_g);
 
 /* Enable (1, default) or disable (0) replay of multi-step runs through captured CUDA graphs. */
 int tvlbm_set_graphs(tvlbm_ctx *ctx, int enable);

@@ -28,6 +28,7 @@ TVLBM_ENONFINITE = -6
 TVLBM_D2Q9, TVLBM_D2Q16, TVLBM_D2Q36 = 9, 16, 36
 TVLBM_FP64, TVLBM_FP32, TVLBM_BF16_DEV, TVLBM_FP16_DEV, TVLBM_FP32_DEV = 0, 1, 2, 3, 4
 TVLBM_FORM_PLAIN, TVLBM_FORM_TILED, TVLBM_FORM_FLOW = 0, 1, 2
+TVLBM_SCHEME_VOLUMETRIC, TVLBM_SCHEME_FVLB = 0, 1
 TVLBM_MLP_IN, TVLBM_MLP_IN_PAD, TVLBM_MLP_HIDDEN = 54, 64, 128
 TVLBM_MLP_OUT, TVLBM_MLP_OUT_PAD, TVLBM_MLP_PARAMS = 12, 16, 25100
 TVLBM_BC_PERIODIC, TVLBM_BC_WALLS = 0, 1
@@ -73,6 +74,7 @@ def _load_library() -> ctypes.CDLL:
         "tvlbm_set_stream": (_I, [_P, _P]),
         "tvlbm_set_form": (_I, [_P, _I]),
         "tvlbm_set_graphs": (_I, [_P, _I]),
+        "tvlbm_set_scheme": (_I, [_P, _I, _D]),
         "tvlbm_set_reference": (_I, [_P, _D, _D, _D]),
         "tvlbm_tile_count": (_I, [_P]),
         "tvlbm_tile_shape": (_I, [_P, _I, _IP, _IP, _IP]),
@@ -321,6 +323,12 @@ class Simulation:
             self.close()
         except Exception:
             pass
+
+    def set_scheme(self, scheme, tau_g=float("inf")):
+        """"volumetric" (default) or "fvlb" (the paper's finite-volume update, Prandtl time tau_g)."""
+        code = {"volumetric": TVLBM_SCHEME_VOLUMETRIC, "fvlb": TVLBM_SCHEME_FVLB}[scheme] if isinstance(scheme, str) \
+            else int(scheme)
+        _check(_lib.tvlbm_set_scheme(self.ctx, code, float(tau_g)), self.ctx)
 
     def set_form(self, form):
         tvlbm_set_form(self.ctx, FORMS[form] if isinstance(form, str) else int(form))

@@ -179,6 +179,8 @@ int create_common(int nx, int ny, int velset, double tau, double dt, const tvlbm
     c->graphs = 1;
     c->tau = tau;
     c->dt = dt;
+    c->scheme = TVLBM_SCHEME_VOLUMETRIC;
+    c->tau_g = INFINITY;
     c->rho0 = rho0;
     if (bc) c->bc = *bc; else c->bc.kind = TVLBM_BC_PERIODIC;
     gauss_hermite_rule(c->n1, &c->rule);
@@ -278,6 +280,7 @@ int tvlbm_destroy(tvlbm_ctx* c) {
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     drop_graphs(c);
+    if (c->fv_omega) cudaFree(c->fv_omega);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     if (c->own_mem && c->mem) cudaFree(c->mem);
     delete c;
@@ -376,6 +379,7 @@ int tvlbm_step(tvlbm_ctx* c, int n) {
     if (!c) return TVLBM_EINVAL;
     if (n < 0) return fail(c, TVLBM_EINVAL, "negative step count");
     cudaSetDevice(c->device);
+    if (c->scheme == TVLBM_SCHEME_FVLB) return fvlb_steps(c, n);
     if (c->form == FORM_FLOW) {
         TVLBM_CUDA(c, launch_flow(c, n, c->stream), "dataflow launch");
         return TVLBM_OK;

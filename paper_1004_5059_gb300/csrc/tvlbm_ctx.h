@@ -27,5 +27,11 @@ struct tvlbm_ctx {
     int have_tmap;
     int tile_cfg;                     // tiled-form tile configuration
     alignas(64) CUtensorMap tmap[2];  // TMA descriptors: input windows of buffer b
+    int scheme;                       // TVLBM_SCHEME_VOLUMETRIC or TVLBM_SCHEME_FVLB
+    double tau_g;                     // Prandtl-term time of the finite-volume scheme (inf: none)
+    void* fv_omega;                   // finite-volume scheme: collision-term buffer (own allocation)
     char err[512];
 };
+
+// Finite-volume scheme (tvlbm_fvlb.cu): n explicit steps of the context's state.
+int fvlb_steps(tvlbm_ctx* c, int n);

@@ -285,6 +285,166 @@ __global__ void __launch_bounds__(128) gemm_kernel(const __grid_constant__ CUten
     if (warp == 0) tmem_free(tmem, Cfg::TMEM_COLS);
 }
 
+// ---- fused inference: the three layers of one 128-row tile in one CTA ---------------------------
+// X, W1, W2, W3 arrive by TMA (128-byte swizzle); H1 and H2 never leave shared memory: the
+// epilogue threads write them in the same swizzled K-major layout the next MMA reads.  TMEM:
+// columns [0, 128) hold layer 1, [128, 256) layer 2, [0, 16) then layer 3.
+struct FusedCfg {
+    static constexpr int X_OFF = 0, W1_OFF = 16384, W2_OFF = 32768, W3_OFF = 65536, H_OFF = 69632;
+    static constexpr int BYTES = H_OFF + 32768;  // 100 KB
+    static constexpr int SMEM = BYTES + 1024;
+    static constexpr uint32_t TX = 16384 + 16384 + 32768 + 4096;
+    static constexpr uint32_t TMEM_COLS = 256;
+};
+
+// Row r of a [128][128] BF16 tile stored as two 128-byte-swizzled K-major chunks of 64 columns:
+// columns c0 .. c0 + 15 (c0 a multiple of 16) from 16 FP32 values.
+__device__ __forceinline__ void store_h_sw128(unsigned char* h, int r, int c0, const float (&v)[16]) {
+    const int kc = c0 >> 6, j0 = (c0 & 63) >> 3;  // chunk, first 16-byte unit in the row
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+        alignas(16) __nv_bfloat16 b[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) b[q] = __float2bfloat16_rn(v[8 * half + q]);
+        const int j = (j0 + half) ^ (r & 7);
+        *reinterpret_cast<uint4*>(h + kc * 16384 + r * 128 + j * 16) = *reinterpret_cast<const uint4*>(b);
+    }
+}
+
+__global__ void __launch_bounds__(128) mlp_fused_forward_kernel(const __grid_constant__ CUtensorMap mx,
+                                                                const __grid_constant__ CUtensorMap mw1,
+                                                                const __grid_constant__ CUtensorMap mw2,
+                                                                const __grid_constant__ CUtensorMap mw3,
+                                                                const float* __restrict__ theta, float* __restrict__ y,
+                                                                int* status) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = smem_raw + ((1024u - (saddr(smem_raw) & 1023u)) & 1023u);
+    __shared__ uint64_t load_bar, mma_bar;
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * BM;
+    const float* b1 = theta + OFF_B1;
+    const float* b2 = theta + OFF_B2;
+    const float* b3 = theta + OFF_B3;
+    if (tid == 0) {
+        bar_init(&load_bar, 1);
+        bar_init(&mma_bar, 1);
+        bar_init_fence();
+    }
+    if (warp == 0) tmem_alloc(&tmem_slot, FusedCfg::TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    unsigned char* xs = base + FusedCfg::X_OFF;
+    unsigned char* w1 = base + FusedCfg::W1_OFF;
+    unsigned char* w2 = base + FusedCfg::W2_OFF;
+    unsigned char* w3 = base + FusedCfg::W3_OFF;
+    unsigned char* hs = base + FusedCfg::H_OFF;
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+    const int r = warp * 32 + lane;  // this thread's row of the tile (= its TMEM lane)
+
+    bool ok = true;
+    if (tid == 0) {
+        bar_expect_tx(&load_bar, FusedCfg::TX);
+        tma_load_2d(xs, &mx, &load_bar, 0, m0);
+        tma_load_2d(w1, &mw1, &load_bar, 0, 0);
+        tma_load_2d(w2, &mw2, &load_bar, 0, 0);
+        tma_load_2d(w2 + 16384, &mw2, &load_bar, BK, 0);
+        tma_load_2d(w3, &mw3, &load_bar, 0, 0);
+        tma_load_2d(w3 + 2048, &mw3, &load_bar, BK, 0);
+        ok = bar_wait(&load_bar, 0);
+        if (ok) {
+            tc_fence_after();
+            const uint32_t idesc = idesc_bf16_f32(BM, NH);
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk)
+                mma_bf16(tmem, sw128_desc(saddr(xs) + kk * 32), sw128_desc(saddr(w1) + kk * 32), idesc, kk > 0);
+        }
+        mma_commit(&mma_bar);
+    }
+    // layer 1 epilogue: H1 = g(Z1 + b1) into shared memory
+    ok = __syncthreads_and((tid != 0 || ok) && bar_wait(&mma_bar, 0)) != 0;
+    tc_fence_after();
+    if (ok) {
+#pragma unroll 1
+        for (int c0 = 0; c0 < NH; c0 += 16) {
+            float v[16];
+            __syncwarp();
+            tmem_ld16(taddr + (uint32_t)c0, v);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) v[k] = gelu_f(v[k] + b1[c0 + k]);
+            store_h_sw128(hs, r, c0, v);
+        }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> MMA reads
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+        if (ok) {
+            tc_fence_after();
+            const uint32_t idesc = idesc_bf16_f32(BM, NH);
+#pragma unroll
+            for (int kc = 0; kc < 2; ++kc)
+#pragma unroll
+                for (int kk = 0; kk < BK / 16; ++kk)
+                    mma_bf16(tmem + NH, sw128_desc(saddr(hs) + kc * 16384 + kk * 32),
+                             sw128_desc(saddr(w2) + kc * 16384 + kk * 32), idesc, kc > 0 || kk > 0);
+        }
+        mma_commit(&mma_bar);
+    }
+    // layer 2 epilogue: H2 = g(Z2 + b2) over H1 (the MMA that read H1 has completed)
+    ok = __syncthreads_and(ok && bar_wait(&mma_bar, 1)) != 0;
+    tc_fence_after();
+    if (ok) {
+#pragma unroll 1
+        for (int c0 = 0; c0 < NH; c0 += 16) {
+            float v[16];
+            __syncwarp();
+            tmem_ld16(taddr + (uint32_t)(NH + c0), v);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) v[k] = gelu_f(v[k] + b2[c0 + k]);
+            store_h_sw128(hs, r, c0, v);
+        }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+        if (ok) {
+            tc_fence_after();
+            const uint32_t idesc = idesc_bf16_f32(BM, NOUTP);
+#pragma unroll
+            for (int kc = 0; kc < 2; ++kc)
+#pragma unroll
+                for (int kk = 0; kk < BK / 16; ++kk)
+                    mma_bf16(tmem, sw128_desc(saddr(hs) + kc * 16384 + kk * 32),
+                             sw128_desc(saddr(w3) + kc * 2048 + kk * 32), idesc, kc > 0 || kk > 0);
+        }
+        mma_commit(&mma_bar);
+    }
+    ok = __syncthreads_and(ok && bar_wait(&mma_bar, 0)) != 0;
+    tc_fence_after();
+    if (ok) {
+        float v[16];
+        __syncwarp();
+        tmem_ld16(taddr, v);
+        float4* d = reinterpret_cast<float4*>(y + (size_t)(m0 + r) * NOUTP);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float o[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) o[e] = 4 * q + e < NOUT ? v[4 * q + e] + b3[4 * q + e] : 0.0f;
+            d[q] = make_float4(o[0], o[1], o[2], o[3]);
+        }
+    } else if (tid == 0 && status) {
+        atomicOr(status, 1);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_free(tmem, FusedCfg::TMEM_COLS);
+}
+
 // ---- small kernels ---------------------------------------------------------------------------
 
 // x [rows][64] -> xt [64][rows]
@@ -464,12 +624,19 @@ int mlp_forward_async(tvlbm_mlp* m, const void* x, int rows, float* y) {
         !bf16_map(&mh2, m->h2, NH, rows, NH, BM) || !bf16_map(&mw3, m->w3p, NH, NOUTP, NH, NOUTP))
         return mfail(m, TVLBM_EINVAL, "TMA descriptor rejected (alignment of x?)");
     const int tiles = rows / BM;
-    EpiHidden e1{m->theta + OFF_B1, m->h1, nullptr, nullptr, rows};
-    MLP_CUDA(m, (gemm<NH, 2>(mx, mw1, tiles, NINP / BK, 1, NINP / BK, e1, m->status, m->stream)), "layer 1");
-    EpiHidden e2{m->theta + OFF_B2, m->h2, nullptr, nullptr, rows};
-    MLP_CUDA(m, (gemm<NH, 2>(mh1, mw2, tiles, NH / BK, 1, NH / BK, e2, m->status, m->stream)), "layer 2");
-    EpiOut e3{m->theta + OFF_B3, y, nullptr, nullptr, nullptr, nullptr, nullptr, 0.0f, rows};
-    MLP_CUDA(m, (gemm<NOUTP, 2>(mh2, mw3, tiles, NH / BK, 1, NH / BK, e3, m->status, m->stream)), "layer 3");
+    (void)mh1;
+    (void)mh2;
+    static bool attr_set[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+        MLP_CUDA(m, cudaFuncSetAttribute(mlp_fused_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         FusedCfg::SMEM),
+                 "fused forward attribute");
+        attr_set[dev] = true;
+    }
+    mlp_fused_forward_kernel<<<tiles, 128, FusedCfg::SMEM, m->stream>>>(mx, mw1, mw2, mw3, m->theta, y, m->status);
+    MLP_CUDA(m, cudaGetLastError(), "fused forward");
     return TVLBM_OK;
 }
 int mlp_max_rows(const tvlbm_mlp* m) { return m->max_rows; }
