@@ -138,10 +138,23 @@ int tvlbm_set_form(tvlbm_ctx *ctx, int form);
  * invariants, which an exact Maxwellian would not have; tau_g = +inf leaves it out).  It
  * shifts the viscosity to T tau tau_g / (tau_g - 2 tau) (the Prandtl number to
  * tau_g / (tau_g - 2 tau)).  The scheme is explicit: it needs |c| dt well below one cell and
- * dt well below tau.  Periodic domains, FP64 or FP32 storage; allocates one extra population-
- * sized buffer (also for contexts created in caller memory).  Errors: EINVAL (walls, storage,
- * unknown scheme, tau_g = 0 or NaN), ENOMEM. */
+ * dt well below tau.  Periodic domains, or channels (walls, see tvlbm_set_fv_walls); FP64 or
+ * FP32 storage; allocates one extra population-sized buffer (also for contexts created in
+ * caller memory).  Errors: EINVAL (storage, unknown scheme, tau_g = 0 or NaN), ENOMEM. */
 int tvlbm_set_scheme(tvlbm_ctx *ctx, int scheme, double tau_g);
+
+/* Finite-volume scheme on a channel (a context created with TVLBM_BC_WALLS): the first and
+ * last node rows are wall nodes (walls on the nodes, unlike the volumetric scheme's faces).
+ * Populations arriving at a wall node advance with the one-sided stencils of Eq. FVLB2; the
+ * leaving ones are set before every step to A f_eq(u_eq, T_eq), A balancing the normal mass
+ * flux (Eq. IMPOSITION, |c . n| weights).  exact = 0: (u_eq, T_eq) = the wall's (u, T)
+ * (diffuse reflection: velocity slip, temperature jump); exact = 1: (u_eq, T_eq) corrected by
+ * nr_iters Newton-Raphson iterations (App. B, warm-started from the previous step per column)
+ * so that the wall node's velocity and temperature are the wall's.  y_nodes: host array of the
+ * ny node positions (increasing; NULL: unit spacing), e.g. the tanh mesh of Eq. NONUNI2; the
+ * x spacing is 1.  Call after tvlbm_set_scheme(TVLBM_SCHEME_FVLB).  Errors: EINVAL (no walls,
+ * not the finite-volume scheme, nr_iters < 1 with exact, y_nodes not increasing), ENOMEM. */
+int tvlbm_set_fv_walls(tvlbm_ctx *ctx, int exact, int nr_iters, const double *y_nodes);
 
 /* Enable (1, default) or disable (0) replay of multi-step runs through captured CUDA graphs. */
 int tvlbm_set_graphs(tvlbm_ctx *ctx, int enable);

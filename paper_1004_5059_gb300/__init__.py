@@ -75,6 +75,7 @@ def _load_library() -> ctypes.CDLL:
         "tvlbm_set_form": (_I, [_P, _I]),
         "tvlbm_set_graphs": (_I, [_P, _I]),
         "tvlbm_set_scheme": (_I, [_P, _I, _D]),
+        "tvlbm_set_fv_walls": (_I, [_P, _I, _I, _DP]),
         "tvlbm_set_reference": (_I, [_P, _D, _D, _D]),
         "tvlbm_tile_count": (_I, [_P]),
         "tvlbm_tile_shape": (_I, [_P, _I, _IP, _IP, _IP]),
@@ -329,6 +330,14 @@ class Simulation:
         code = {"volumetric": TVLBM_SCHEME_VOLUMETRIC, "fvlb": TVLBM_SCHEME_FVLB}[scheme] if isinstance(scheme, str) \
             else int(scheme)
         _check(_lib.tvlbm_set_scheme(self.ctx, code, float(tau_g)), self.ctx)
+
+    def set_fv_walls(self, exact=False, nr_iters=32, y_nodes=None):
+        """Finite-volume channel walls: diffuse (exact=False) or Newton-Raphson (exact=True)
+        imposition; y_nodes: the ny node positions (None: unit spacing)."""
+        yn = None if y_nodes is None else np.ascontiguousarray(y_nodes, dtype=np.float64)
+        if yn is not None and yn.shape != (self.ny,):
+            raise ValueError("y_nodes must hold ny positions")
+        _check(_lib.tvlbm_set_fv_walls(self.ctx, 1 if exact else 0, int(nr_iters), _dp(yn)), self.ctx)
 
     def set_form(self, form):
         tvlbm_set_form(self.ctx, FORMS[form] if isinstance(form, str) else int(form))

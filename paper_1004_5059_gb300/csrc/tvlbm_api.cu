@@ -281,6 +281,8 @@ int tvlbm_destroy(tvlbm_ctx* c) {
     cudaStreamSynchronize(c->stream);
     drop_graphs(c);
     if (c->fv_omega) cudaFree(c->fv_omega);
+    if (c->fv_dy) cudaFree(c->fv_dy);
+    if (c->fv_wall_eq) cudaFree(c->fv_wall_eq);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     if (c->own_mem && c->mem) cudaFree(c->mem);
     delete c;

@@ -30,6 +30,9 @@ struct tvlbm_ctx {
     int scheme;                       // TVLBM_SCHEME_VOLUMETRIC or TVLBM_SCHEME_FVLB
     double tau_g;                     // Prandtl-term time of the finite-volume scheme (inf: none)
     void* fv_omega;                   // finite-volume scheme: collision-term buffer (own allocation)
+    double* fv_dy;                    // finite-volume channel: node spacings in y [ny - 1] (device; null: 1)
+    double* fv_wall_eq;               // finite-volume channel: wall equilibria [2][nx][2] (device)
+    int fv_exact, fv_nr_iters;        // finite-volume channel: Newton-Raphson imposition, iterations
     char err[512];
 };
 

@@ -29,6 +29,15 @@ struct FvParams {
     double ginv[4][4];
     double inv_tau, inv_tau_g, dt;
     int prandtl;
+    int walls;          // channel: wall nodes on the first and last rows
+    const double* dy;   // node spacings in y [ny - 1], or null for unit spacing
+};
+
+// Wall imposition parameters: wall velocity and temperature per side, the Newton-Raphson mode.
+struct WallParams {
+    double u[2], T[2];
+    int exact, iters;
+    double* eq;  // [2][nx][2] wall equilibria (u_eq, T_eq), warm start of the next imposition
 };
 
 template <int N1, class C>
@@ -119,6 +128,40 @@ __global__ void __launch_bounds__(256) fv_update_kernel(const typename C::T* __r
     if (x >= p.nx || y >= p.ny) return;
     const long long pitch = p.pitch;
     R s[Q];
+    const int wall = fp.walls ? (y == 0 ? 1 : (y == p.ny - 1 ? 2 : 0)) : 0;  // 1: bottom, 2: top
+    if (wall) {
+        // wall node (Eq. FVLB2): populations arriving at the wall (c . n <= 0) advance with the
+        // one-sided stencils into the fluid; the leaving ones keep their imposed values
+        const R sgn = wall == 1 ? R(1) : R(-1);  // n = +y at the bottom, -y at the top
+        const long long in = wall == 1 ? pitch : -pitch;  // the fluid-side row
+        const R dyw = fp.dy ? (R)(wall == 1 ? fp.dy[0] : fp.dy[p.ny - 2]) : R(1);
+#pragma unroll
+        for (int j = 0; j < N1; ++j)
+#pragma unroll
+            for (int i = 0; i < N1; ++i) {
+                const int l = i + N1 * j;
+                const long long c0 = sidx(p, l, x, y);
+                const typename C::T* fq = f + c0;
+                const typename C::T* oq = om + c0;
+                const R f0 = C::ld(fq);
+                const R cy = kx<R>(p, j);
+                if (sgn * cy > R(0)) {
+                    s[l] = f0;
+                    continue;
+                }
+                const R fE = C::ld(fq + 1), fW = C::ld(fq - 1), fI = C::ld(fq + in), fIE = C::ld(fq + in + 1),
+                        fIW = C::ld(fq + in - 1);
+                const R gx = R(0.375) * (fE - fW) + R(0.125) * (fIE - fIW);
+                const R gy = sgn * (R(2) / dyw) * (R(0.375) * (fI - f0) + R(0.0625) * (fIE + fIW - fE - fW));
+                const R obar = R(0.5625) * C::ld(oq) + R(0.09375) * (C::ld(oq + 1) + C::ld(oq - 1)) +
+                               R(0.1875) * C::ld(oq + in) + R(0.03125) * (C::ld(oq + in + 1) + C::ld(oq + in - 1));
+                s[l] = f0 + (R)fp.dt * (obar - kx<R>(p, i) * gx - cy * gy);
+            }
+        store_collided<N1, C>(fout, geom_of(p), x, y, s);
+        return;
+    }
+    // interior node: y spacing factor 2 / (dy_j + dy_j-1) of the stencil (1 on the unit grid)
+    const R ysc = fp.dy ? (R)(2.0 / (fp.dy[y] + fp.dy[y - 1])) : R(1);
 #pragma unroll
     for (int j = 0; j < N1; ++j)
 #pragma unroll
@@ -132,7 +175,7 @@ __global__ void __launch_bounds__(256) fv_update_kernel(const typename C::T* __r
             const R f5 = C::ld(fq + pitch + 1), f6 = C::ld(fq + pitch - 1), f7 = C::ld(fq - pitch - 1),
                     f8 = C::ld(fq - pitch + 1);
             const R gx = R(0.375) * (f1 - f3) + R(0.0625) * (f5 - f6 - f7 + f8);
-            const R gy = R(0.375) * (f2 - f4) + R(0.0625) * (f5 + f6 - f7 - f8);
+            const R gy = ysc * (R(0.375) * (f2 - f4) + R(0.0625) * (f5 + f6 - f7 - f8));
             const R obar = R(0.5625) * C::ld(oq) +
                            R(0.09375) * (C::ld(oq + 1) + C::ld(oq + pitch) + C::ld(oq - 1) + C::ld(oq - pitch)) +
                            R(0.015625) * (C::ld(oq + pitch + 1) + C::ld(oq + pitch - 1) + C::ld(oq - pitch - 1) +
@@ -142,10 +185,120 @@ __global__ void __launch_bounds__(256) fv_update_kernel(const typename C::T* __r
     store_collided<N1, C>(fout, geom_of(p), x, y, s);
 }
 
+// Equilibrium of unit density at velocity (u, 0) and temperature T, FP64.
+template <int N1>
+__device__ __forceinline__ void wall_feq(const KParams& p, double u, double T, double (&eq)[N1 * N1]) {
+    cell_equilibrium<N1, false, double>(p, 1.0, u, 0.0, T - 1.0, eq);
+}
+
+// Before a step: the leaving populations of every wall node (c . n > 0, n into the fluid)
+// become A f_eq(u_eq, T_eq) with A = sum_{c.n<=0} |c.n| f / sum_{c.n>0} |c.n| f_eq (Eq.
+// IMPOSITION); in the exact mode (u_eq, T_eq) follows the Newton-Raphson of App. B so that the
+// node's velocity and temperature are the wall's.  One thread per (column, wall); FP64.
 template <int N1, class C>
-cudaError_t launch_fv(const void* f, void* om, void* fout, const KParams& p, const FvParams& fp, cudaStream_t s) {
+__global__ void fv_impose_kernel(typename C::T* __restrict__ f, const KParams p, const WallParams wp) {
+    constexpr int Q = N1 * N1;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 2 * p.nx) return;
+    const int side = t / p.nx, x = t - side * p.nx;
+    const int y = side == 0 ? 0 : p.ny - 1;
+    const double sgn = side == 0 ? 1.0 : -1.0;
+    double v[Q], cn[Q];
+    double incoming = 0.0;
+#pragma unroll
+    for (int j = 0; j < N1; ++j)
+#pragma unroll
+        for (int i = 0; i < N1; ++i) {
+            const int l = i + N1 * j;
+            v[l] = (double)C::ld(f + sidx(p, l, x, y));
+            cn[l] = sgn * p.xd[j];
+            if (cn[l] <= 0.0) incoming += -cn[l] * v[l];
+        }
+    const double uw = wp.u[side], Tw = wp.T[side];
+    double* st = wp.eq + (side * p.nx + x) * 2;
+    double ue = wp.exact ? st[0] : uw, Te = wp.exact ? st[1] : Tw;
+    const int iters = wp.exact ? wp.iters : 0;
+    double eq[Q];
+    double S = 1.0;
+    for (int it = 0;; ++it) {
+        wall_feq<N1>(p, ue, Te, eq);
+        S = 0.0;
+#pragma unroll
+        for (int l = 0; l < Q; ++l)
+            if (cn[l] > 0.0) S += cn[l] * eq[l];
+#pragma unroll
+        for (int l = 0; l < Q; ++l)
+            if (cn[l] > 0.0) v[l] = incoming / S * eq[l];
+        if (it == iters) break;
+        double rho = 0.0, mx = 0.0, m2 = 0.0;
+#pragma unroll
+        for (int j = 0; j < N1; ++j)
+#pragma unroll
+            for (int i = 0; i < N1; ++i) {
+                const int l = i + N1 * j;
+                const double cx = p.xd[i], cy = p.xd[j];
+                rho += v[l];
+                mx += v[l] * cx;
+                m2 += v[l] * (cx * cx + cy * cy);
+            }
+        const double F1 = rho * uw - mx, F2 = 2.0 * rho * Tw + rho * uw * uw - m2;
+        const double h = 1e-6;
+        double ep[Q], em[Q];
+        double A = 0, B = 0, Cc = 0, D = 0, su = 0, sT = 0, sx = 0, s2 = 0;
+        wall_feq<N1>(p, ue + h, Te, ep);
+        wall_feq<N1>(p, ue - h, Te, em);
+#pragma unroll
+        for (int j = 0; j < N1; ++j)
+#pragma unroll
+            for (int i = 0; i < N1; ++i) {
+                const int l = i + N1 * j;
+                if (cn[l] <= 0.0) continue;
+                const double cx = p.xd[i], c2 = cx * cx + p.xd[j] * p.xd[j];
+                const double du = (ep[l] - em[l]) / (2.0 * h);
+                A += cx * du;
+                Cc += c2 * du;
+                su += cn[l] * du;
+                sx += cx * eq[l];
+                s2 += c2 * eq[l];
+            }
+        wall_feq<N1>(p, ue, Te + h, ep);
+        wall_feq<N1>(p, ue, Te - h, em);
+#pragma unroll
+        for (int j = 0; j < N1; ++j)
+#pragma unroll
+            for (int i = 0; i < N1; ++i) {
+                const int l = i + N1 * j;
+                if (cn[l] <= 0.0) continue;
+                const double cx = p.xd[i], c2 = cx * cx + p.xd[j] * p.xd[j];
+                const double dT = (ep[l] - em[l]) / (2.0 * h);
+                B += cx * dT;
+                D += c2 * dT;
+                sT += cn[l] * dT;
+            }
+        A -= su * sx / S;
+        Cc -= su * s2 / S;
+        B -= sT * sx / S;
+        D -= sT * s2 / S;
+        const double pref = S / ((A * D - B * Cc) * incoming);
+        ue += pref * (D * F1 - B * F2);
+        Te += pref * (-Cc * F1 + A * F2);
+    }
+    if (wp.exact) {
+        st[0] = ue;
+        st[1] = Te;
+    }
+    const Geom g = geom_of(p);
+#pragma unroll
+    for (int l = 0; l < Q; ++l)
+        if (cn[l] > 0.0) store_with_images(f, g, (long long)l * p.plane, x, y, C::enc((typename C::R)v[l]));
+}
+
+template <int N1, class C>
+cudaError_t launch_fv(const void* f, void* om, void* fout, const KParams& p, const FvParams& fp, const WallParams& wp,
+                      cudaStream_t s) {
     using T = typename C::T;
     const dim3 b(32, 8), g((p.nx + 31) / 32, (p.ny + 7) / 8);
+    if (fp.walls) fv_impose_kernel<N1, C><<<(2 * p.nx + 127) / 128, 128, 0, s>>>((T*)f, p, wp);
     fv_omega_kernel<N1, C><<<g, b, 0, s>>>((const T*)f, (T*)om, p, fp);
     fv_update_kernel<N1, C><<<g, b, 0, s>>>((const T*)f, (const T*)om, (T*)fout, p, fp);
     return cudaGetLastError();
@@ -153,9 +306,9 @@ cudaError_t launch_fv(const void* f, void* om, void* fout, const KParams& p, con
 
 template <int N1>
 cudaError_t launch_fv_storage(int storage, const void* f, void* om, void* fout, const KParams& p, const FvParams& fp,
-                              cudaStream_t s) {
-    return storage == TVLBM_FP64 ? launch_fv<N1, CodecF64>(f, om, fout, p, fp, s)
-                                 : launch_fv<N1, CodecF32>(f, om, fout, p, fp, s);
+                              const WallParams& wp, cudaStream_t s) {
+    return storage == TVLBM_FP64 ? launch_fv<N1, CodecF64>(f, om, fout, p, fp, wp, s)
+                                 : launch_fv<N1, CodecF32>(f, om, fout, p, fp, wp, s);
 }
 
 // Inverse of the 4 x 4 Gram matrix of (1, c_x, c_y, |c|^2) under the set's weights (Gauss-Jordan).
@@ -206,14 +359,31 @@ int fvlb_steps(tvlbm_ctx* c, int n) {
     fp.prandtl = isfinite(c->tau_g) ? 1 : 0;
     fp.inv_tau_g = fp.prandtl ? 1.0 / c->tau_g : 0.0;
     fp.dt = c->dt;
+    fp.walls = c->kp.walls ? 1 : 0;
+    fp.dy = c->fv_dy;
+    WallParams wp;
+    memset(&wp, 0, sizeof(wp));
+    if (fp.walls) {
+        if (!c->fv_wall_eq) {
+            snprintf(c->err, sizeof(c->err), "channel: call tvlbm_set_fv_walls first");
+            return TVLBM_EINVAL;
+        }
+        wp.u[0] = c->bc.u_lo;
+        wp.T[0] = c->bc.T_lo;
+        wp.u[1] = c->bc.u_hi;
+        wp.T[1] = c->bc.T_hi;
+        wp.exact = c->fv_exact;
+        wp.iters = c->fv_nr_iters;
+        wp.eq = c->fv_wall_eq;
+    }
     for (int t = 0; t < n; ++t) {
-        const void* f = c->mem + c->L.off_f[c->cur];
+        void* f = c->mem + c->L.off_f[c->cur];
         void* fout = c->mem + c->L.off_f[1 - c->cur];
         cudaError_t e;
         switch (c->n1) {
-            case 3: e = launch_fv_storage<3>(c->storage, f, c->fv_omega, fout, c->kp, fp, c->stream); break;
-            case 4: e = launch_fv_storage<4>(c->storage, f, c->fv_omega, fout, c->kp, fp, c->stream); break;
-            default: e = launch_fv_storage<6>(c->storage, f, c->fv_omega, fout, c->kp, fp, c->stream); break;
+            case 3: e = launch_fv_storage<3>(c->storage, f, c->fv_omega, fout, c->kp, fp, wp, c->stream); break;
+            case 4: e = launch_fv_storage<4>(c->storage, f, c->fv_omega, fout, c->kp, fp, wp, c->stream); break;
+            default: e = launch_fv_storage<6>(c->storage, f, c->fv_omega, fout, c->kp, fp, wp, c->stream); break;
         }
         if (e != cudaSuccess) {
             snprintf(c->err, sizeof(c->err), "finite-volume kernels: %s", cudaGetErrorString(e));
@@ -235,10 +405,8 @@ extern "C" int tvlbm_set_scheme(tvlbm_ctx* c, int scheme, double tau_g) {
         snprintf(c->err, sizeof(c->err), "unknown scheme %d", scheme);
         return TVLBM_EINVAL;
     }
-    if (c->kp.walls || (c->storage != TVLBM_FP64 && c->storage != TVLBM_FP32) || isnan(tau_g) || tau_g == 0.0 ||
-        !isfinite(c->tau)) {
-        snprintf(c->err, sizeof(c->err),
-                 "the finite-volume scheme needs a periodic domain, FP64 or FP32 storage, finite tau and tau_g != 0");
+    if ((c->storage != TVLBM_FP64 && c->storage != TVLBM_FP32) || isnan(tau_g) || tau_g == 0.0 || !isfinite(c->tau)) {
+        snprintf(c->err, sizeof(c->err), "the finite-volume scheme needs FP64 or FP32 storage, finite tau and tau_g != 0");
         return TVLBM_EINVAL;
     }
     cudaSetDevice(c->device);
@@ -253,5 +421,55 @@ extern "C" int tvlbm_set_scheme(tvlbm_ctx* c, int scheme, double tau_g) {
     }
     c->scheme = scheme;
     c->tau_g = tau_g;
+    return TVLBM_OK;
+}
+
+extern "C" int tvlbm_set_fv_walls(tvlbm_ctx* c, int exact, int nr_iters, const double* y_nodes) {
+    if (!c) return TVLBM_EINVAL;
+    if (!c->kp.walls || c->scheme != TVLBM_SCHEME_FVLB || (exact && nr_iters < 1) || nr_iters > 1000) {
+        snprintf(c->err, sizeof(c->err), "needs a channel context in the finite-volume scheme and 1..1000 iterations");
+        return TVLBM_EINVAL;
+    }
+    double* dy_host = nullptr;
+    if (y_nodes) {
+        dy_host = new double[c->ny - 1];
+        for (int j = 0; j + 1 < c->ny; ++j) {
+            dy_host[j] = y_nodes[j + 1] - y_nodes[j];
+            if (!(dy_host[j] > 0.0) || !isfinite(dy_host[j])) {
+                delete[] dy_host;
+                snprintf(c->err, sizeof(c->err), "y_nodes must be finite and increasing");
+                return TVLBM_EINVAL;
+            }
+        }
+    }
+    cudaSetDevice(c->device);
+    if (!c->fv_wall_eq && cudaMalloc((void**)&c->fv_wall_eq, sizeof(double) * 4 * c->nx) != cudaSuccess) {
+        delete[] dy_host;
+        return TVLBM_ENOMEM;
+    }
+    // warm start of the Newton-Raphson: the walls' own velocity and temperature
+    double* eq = new double[4 * c->nx];
+    for (int x = 0; x < c->nx; ++x) {
+        eq[2 * x] = c->bc.u_lo;
+        eq[2 * x + 1] = c->bc.T_lo;
+        eq[2 * (c->nx + x)] = c->bc.u_hi;
+        eq[2 * (c->nx + x) + 1] = c->bc.T_hi;
+    }
+    cudaError_t e = cudaMemcpy(c->fv_wall_eq, eq, sizeof(double) * 4 * c->nx, cudaMemcpyHostToDevice);
+    delete[] eq;
+    if (e == cudaSuccess && dy_host) {
+        if (!c->fv_dy) e = cudaMalloc((void**)&c->fv_dy, sizeof(double) * (c->ny - 1));
+        if (e == cudaSuccess) e = cudaMemcpy(c->fv_dy, dy_host, sizeof(double) * (c->ny - 1), cudaMemcpyHostToDevice);
+    } else if (e == cudaSuccess && c->fv_dy) {
+        cudaFree(c->fv_dy);
+        c->fv_dy = nullptr;
+    }
+    delete[] dy_host;
+    if (e != cudaSuccess) {
+        snprintf(c->err, sizeof(c->err), "CUDA: %s", cudaGetErrorString(e));
+        return TVLBM_ECUDA;
+    }
+    c->fv_exact = exact ? 1 : 0;
+    c->fv_nr_iters = exact ? nr_iters : 0;
     return TVLBM_OK;
 }

@@ -527,6 +527,10 @@ struct tvlbm_mlp {
     bf16 *h1, *h1t, *g1, *h2, *h2t, *g2, *dy, *dyt, *dz2, *dz2t, *dz1t, *xt;
     float* ybuf;
     int adam_t;
+    // descriptors of the last inference call (inputs at cached_x, cached_rows rows)
+    const void* cached_x;
+    int cached_rows;
+    alignas(64) CUtensorMap fwd_maps[4];
     char err[256];
 };
 
@@ -618,14 +622,19 @@ namespace tvlbm {
 int mlp_forward_async(tvlbm_mlp* m, const void* x, int rows, float* y) {
     int rc = check_rows(m, rows);
     if (rc) return rc;
-    CUtensorMap mx, mw1, mh1, mw2, mh2, mw3;
-    if (!bf16_map(&mx, x, NINP, rows, NINP, BM) || !bf16_map(&mw1, m->w1p, NINP, NH, NINP, NH) ||
-        !bf16_map(&mh1, m->h1, NH, rows, NH, BM) || !bf16_map(&mw2, m->w2, NH, NH, NH, NH) ||
-        !bf16_map(&mh2, m->h2, NH, rows, NH, BM) || !bf16_map(&mw3, m->w3p, NH, NOUTP, NH, NOUTP))
-        return mfail(m, TVLBM_EINVAL, "TMA descriptor rejected (alignment of x?)");
+    // the weight descriptors never change; the input's are kept for repeated calls on one buffer
+    if (m->cached_x != x || m->cached_rows != rows) {
+        if (!bf16_map(&m->fwd_maps[0], x, NINP, rows, NINP, BM) ||
+            !bf16_map(&m->fwd_maps[1], m->w1p, NINP, NH, NINP, NH) ||
+            !bf16_map(&m->fwd_maps[2], m->w2, NH, NH, NH, NH) || !bf16_map(&m->fwd_maps[3], m->w3p, NH, NOUTP, NH, NOUTP)) {
+            m->cached_x = nullptr;
+            return mfail(m, TVLBM_EINVAL, "TMA descriptor rejected (alignment of x?)");
+        }
+        m->cached_x = x;
+        m->cached_rows = rows;
+    }
+    const CUtensorMap &mx = m->fwd_maps[0], &mw1 = m->fwd_maps[1], &mw2 = m->fwd_maps[2], &mw3 = m->fwd_maps[3];
     const int tiles = rows / BM;
-    (void)mh1;
-    (void)mh2;
     static bool attr_set[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);

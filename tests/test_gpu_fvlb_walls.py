@@ -1,0 +1,91 @@
+"""GPU parity of the finite-volume channel (tvlbm_set_fv_walls) against the FP64 oracle
+(oracle/fvlb.py: FVLBChannel): wall nodes with the one-sided stencils, diffuse and
+Newton-Raphson imposition, uniform and tanh meshes, element by element in FP64 storage; the
+exact mode's wall velocity and temperature."""
+import numpy as np
+import pytest
+
+from oracle import fvlb
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tv():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1004_5059_gb300 as tv
+    return tv
+
+
+def fields(nx, ny):
+    yy = np.linspace(0, 1, ny).reshape(-1, 1) * np.ones((1, nx))
+    xx = np.linspace(0, 1, nx, endpoint=False).reshape(1, -1) * np.ones((ny, 1))
+    rho = 1.0 + 0.01 * np.cos(2 * np.pi * xx) * yy
+    ux = 0.03 * np.sin(3 * yy) + 0.01 * np.sin(2 * np.pi * xx)
+    uy = 0.005 * np.sin(np.pi * yy) * np.cos(2 * np.pi * xx)
+    T = 1.0 + 0.02 * yy
+    return rho, ux, uy, T
+
+
+@pytest.mark.parametrize("exact", [False, True])
+@pytest.mark.parametrize("mesh", ["uniform", "tanh"])
+def test_channel_matches_oracle(tv, exact, mesh):
+    nx, ny = 8, 13
+    y = np.linspace(0.0, 6.0, ny) if mesh == "uniform" else fvlb.tanh_nodes(ny, 6.0, 1.5)
+    walls = (0.02, 1.0, -0.03, 1.05)
+    sim = tv.Simulation(nx, ny, "D2Q16", tau=0.5, dt=0.01, walls=walls, storage="fp64")
+    sim.set_scheme("fvlb", 2.0)
+    sim.set_fv_walls(exact=exact, nr_iters=32, y_nodes=y)
+    ref = fvlb.FVLBChannel(nx, ny, y, walls, tau=0.5, tau_g=2.0, dt=0.01, exact=exact, nr_iters=32)
+    f = fields(nx, ny)
+    sim.init_moments(*f)
+    ref.init_moments(*f)
+    sim.step(30)
+    ref.step(30)
+    got = sim.populations_f64()
+    assert np.max(np.abs(got - ref.f)) <= 1e-11 * np.max(np.abs(ref.f))
+    sim.close()
+
+
+def test_exact_walls_move_with_the_walls(tv):
+    nx, ny = 4, 13
+    y = fvlb.tanh_nodes(ny, 6.0, 1.5)
+    walls = (-0.05, 1.0, 0.05, 1.1)
+    sim = tv.Simulation(nx, ny, "D2Q16", tau=0.5, dt=0.02, walls=walls, storage="fp64")
+    sim.set_scheme("fvlb")
+    sim.set_fv_walls(exact=True, nr_iters=32, y_nodes=y)
+    sim.init_moments(*fields(nx, ny))
+    sim.step(200)
+    # the next imposition's wall nodes: run the imposition by one more step and read the rows
+    # the update left untouched for the leaving populations -- simplest: compare the oracle
+    ref = fvlb.FVLBChannel(nx, ny, y, walls, tau=0.5, dt=0.02, exact=True, nr_iters=32)
+    ref.init_moments(*fields(nx, ny))
+    ref.step(200)
+    ref.impose()
+    rho, ux, uy, T = ref.moments()
+    assert np.max(np.abs(ux[0] + 0.05)) < 1e-10 and np.max(np.abs(T[-1] - 1.1)) < 1e-10
+    got = sim.populations_f64()
+    ref2 = fvlb.FVLBChannel(nx, ny, y, walls, tau=0.5, dt=0.02, exact=True, nr_iters=32)
+    ref2.init_moments(*fields(nx, ny))
+    ref2.step(200)
+    assert np.max(np.abs(got - ref2.f)) <= 1e-11 * np.max(np.abs(ref2.f))
+    sim.close()
+
+
+def test_channel_rejections(tv):
+    s = tv.Simulation(16, 16, "D2Q16", storage="fp64")
+    s.set_scheme("fvlb")
+    with pytest.raises(tv.TvlbmError):
+        s.set_fv_walls()  # periodic context
+    s.close()
+    s = tv.Simulation(16, 16, "D2Q16", storage="fp64", walls=(0.0, 1.0, 0.0, 1.0))
+    with pytest.raises(tv.TvlbmError):
+        s.set_fv_walls()  # not the finite-volume scheme yet
+    s.set_scheme("fvlb")
+    with pytest.raises(tv.TvlbmError):
+        s.set_fv_walls(y_nodes=np.linspace(1.0, 0.0, 16))  # decreasing
+    s.set_fv_walls(exact=True)
+    s.step(3)
+    s.close()
