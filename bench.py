@@ -7,7 +7,7 @@ stream+collide sweep over the grid).  Inputs are resident in HBM when a timed st
 L2 is flushed (a 512 MiB write) between timed steps, outside the timed events.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload c1|c1_4096|c0|c2|c3|c4] [--form tiled|flow|plain] [--no-cpu-baseline]
+                  [--workload c1|c1_4096|c0|c2|c3|c4|fv] [--form tiled|flow|plain] [--no-cpu-baseline]
 
 Prints one JSON line.  --impl reference times the FP64 CPU oracle on this machine's host
 cores on the same workload (each step a bounded sample of the time steps).  Under torchrun
@@ -548,6 +548,113 @@ def run_batch_reference(args, rank):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+FV = dict(desc="the paper's finite-volume scheme (Eq. FVLB + Prandtl term, tau_g = 2 tau): D2Q16 1024x1024 "
+               "periodic FP32, tau = 0.5, dt = 0.02, C1 fields; 200 explicit steps per bench step",
+          nx=1024, ny=1024, tau=0.5, tau_g=1.0, dt=0.02, tsteps=200)
+
+
+def run_fv(args, rank, world, local_rank):
+    """Throughput of the finite-volume scheme (two kernels per step: collision term, update)."""
+    import torch
+    import paper_1004_5059_gb300 as tv
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    nx, ny, tsteps = FV["nx"], FV["ny"], FV["tsteps"]
+    fields = workloads.gaussian_bump_random_flow(nx, ny, seed=1)
+    stream = torch.cuda.current_stream(dev)
+    sim = tv.Simulation(nx, ny, "D2Q16", tau=FV["tau"], dt=FV["dt"], storage="fp32", stream=stream)
+    sim.set_scheme("fvlb", FV["tau_g"])
+    sim.init_moments(*fields)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        sim.step(tsteps)
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    clocks = Clocks(local_rank)
+    clocks.start()
+    evs = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sim.step(tsteps)
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    ms_max = max_over_ranks(ms, world, dev)
+    cells = nx * ny
+    value = aggregate_mlups(world, cells, tsteps, args.steps, ms_max / 1e3)
+    # algorithmic bytes per cell update: collision term reads Q and writes Q values, the update
+    # reads 2 Q distinct values (f and the collision term; the 3 x 3 neighbours come from cache)
+    # and writes Q: 5 Q x 4 bytes
+    bpc = 5 * 16 * 4
+    peak, peak_kind = measured_peak_hbm()
+    achieved = bpc * cells / (ms / 1e3 / (args.steps * tsteps)) / 1e9
+    pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in fields]
+    out = [torch.empty((ny, nx), dtype=torch.float64).pin_memory().numpy() for _ in range(4)]
+    torch.cuda.synchronize()
+    te = time.perf_counter()
+    for _ in range(2):
+        sim.init_moments(*pinned)
+        sim.step(tsteps)
+        tv.tvlbm_moments(sim.ctx, nx, ny, out=out)
+    e2e = aggregate_mlups(world, cells, tsteps, 2, max_over_ranks(time.perf_counter() - te, world, dev))
+    line = {"metric": METRIC + " (finite-volume scheme)", "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (C1 fields)",
+            "config": {"workload": FV["desc"], "nx": nx, "ny": ny, "time_steps_per_bench_step": tsteps,
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "L2 flushed (512 MiB write) between timed steps"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_kind": peak_kind, "bytes_per_cell": bpc, "traffic": None},
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 32 * cells, "d2h_bytes_per_step": 32 * cells},
+            "gpu_launches": args.steps * tsteps * 2, "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        from oracle import fvlb
+        cores = _oracle_threads()
+        o = fvlb.FVLB(256, 256, "D2Q16", tau=FV["tau"], tau_g=FV["tau_g"], dt=FV["dt"])
+        o.init_moments(*workloads.gaussian_bump_random_flow(256, 256, seed=1, sigma=16.0))
+        t0 = time.perf_counter()
+        o.step(5)
+        dt_ = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": 256 * 256 * 5 / dt_ / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": "5 finite-volume steps of a 256x256 grid (numpy, one core)"}
+    sim.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return line if rank == 0 else None
+
+
+def run_fv_reference(args, rank):
+    if rank != 0:
+        return None
+    from oracle import fvlb
+    o = fvlb.FVLB(256, 256, "D2Q16", tau=FV["tau"], tau_g=FV["tau_g"], dt=FV["dt"])
+    o.init_moments(*workloads.gaussian_bump_random_flow(256, 256, seed=1, sigma=16.0))
+    for _ in range(args.warmup):
+        o.step(1)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt_ = time.perf_counter() - t0
+    value = 256 * 256 * args.steps / dt_ / 1e6
+    return {"impl": "reference", "metric": METRIC + " (finite-volume scheme)", "value": value, "unit": UNIT,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt_ * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": FV["desc"], "sample": "one step of a 256x256 grid per bench step (oracle)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "one finite-volume step of a 256x256 grid per bench step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
 def _closure_setup():
     from paper_1004_5059_gb300 import closure as C
     cfg = C.ClosureConfig(nf=CLOSURE["nf"], m=CLOSURE["m"])
@@ -740,13 +847,18 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c1", choices=sorted(WORKLOADS) + ["c3", "c4"])
+    ap.add_argument("--workload", default="c1", choices=sorted(WORKLOADS) + ["c3", "c4", "fv"])
     ap.add_argument("--form", default=None, choices=["tiled", "flow", "plain"],
                     help="sweep form (default: the fastest of tiled and, on periodic domains, flow)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile", type=int, default=-1, help="tile configuration of the tiled form (-1: autotune)")
     args = ap.parse_args()
     rank, world, local_rank = dist_env()
+    if args.workload == "fv":
+        line = run_fv(args, rank, world, local_rank) if args.impl == "ours" else run_fv_reference(args, rank)
+        if rank == 0 and line is not None:
+            print(json.dumps(line))
+        return
     if args.workload == "c4":
         line = run_closure(args, rank, world, local_rank) if args.impl == "ours" else run_closure_reference(args, rank)
         if rank == 0 and line is not None:

@@ -280,6 +280,8 @@ int tvlbm_destroy(tvlbm_ctx* c) {
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     drop_graphs(c);
+    for (int k = 0; k < 2; ++k)
+        if (c->cl_graph[k]) cudaGraphExecDestroy(c->cl_graph[k]);
     if (c->fv_omega) cudaFree(c->fv_omega);
     if (c->fv_dy) cudaFree(c->fv_dy);
     if (c->fv_wall_eq) cudaFree(c->fv_wall_eq);

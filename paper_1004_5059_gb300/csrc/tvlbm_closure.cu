@@ -490,30 +490,93 @@ int tvlbm_step_closure(tvlbm_ctx* c, tvlbm_mlp* m, const float* mu, const float*
     BasisF bf;
     make_basis(c->rule, &bd, &bf);
     mlp_set_stream(m, c->stream);
-    float* m6 = (float*)(c->mem + c->L.off_mom);
-    void* x = mlp_xbuf(m);
-    float* y = mlp_ybuf(m);
-    const dim3 b(32, 8), g = grid_of(c->nx, c->ny, b);
-    for (int t = 0; t < n; ++t) {
-        // stream into the other buffer, which becomes the current state
+    const long long ncell = cells;
+    // one learned step on stream s: stream, features of the streamed state, network, collision
+    auto one_step = [&](cudaStream_t st) -> int {
+        float* m6 = (float*)(c->mem + c->L.off_mom);
+        void* x = mlp_xbuf(m);
+        float* y = mlp_ybuf(m);
+        const dim3 b(32, 8), g = grid_of(c->nx, c->ny, b);
         switch (c->storage) {
-            case TVLBM_FP64: closure_stream_kernel<CodecF64><<<g, b, 0, c->stream>>>((const double*)cur_buf(c), (double*)other_buf(c), c->kp); break;
-            case TVLBM_FP32: closure_stream_kernel<CodecF32><<<g, b, 0, c->stream>>>((const float*)cur_buf(c), (float*)other_buf(c), c->kp); break;
-            default: closure_stream_kernel<CodecF32Dev><<<g, b, 0, c->stream>>>((const float*)cur_buf(c), (float*)other_buf(c), c->kp); break;
+            case TVLBM_FP64: closure_stream_kernel<CodecF64><<<g, b, 0, st>>>((const double*)cur_buf(c), (double*)other_buf(c), c->kp); break;
+            case TVLBM_FP32: closure_stream_kernel<CodecF32><<<g, b, 0, st>>>((const float*)cur_buf(c), (float*)other_buf(c), c->kp); break;
+            default: closure_stream_kernel<CodecF32Dev><<<g, b, 0, st>>>((const float*)cur_buf(c), (float*)other_buf(c), c->kp); break;
         }
         CL_CUDA(c, cudaGetLastError(), "closure stream kernel");
         c->cur ^= 1;
-        // the network's coefficients from the streamed state, then the learned collision in place
-        CL_CUDA(c, launch_moments(c, m6), "closure moments kernel");
-        CL_CUDA(c, launch_features(c, m6, nrm, x), "closure features kernel");
-        rc = mlp_forward_async(m, x, (int)cells, y);
-        if (rc) return ctx_fail(c, rc, tvlbm_mlp_last_error(m));
+        const dim3 bm(32, 8), gm = grid_of(c->nx, c->ny, bm);
         switch (c->storage) {
-            case TVLBM_FP64: closure_collide_kernel<CodecF64><<<g, b, 0, c->stream>>>((double*)cur_buf(c), c->kp, y, bf, bd, sc); break;
-            case TVLBM_FP32: closure_collide_kernel<CodecF32><<<g, b, 0, c->stream>>>((float*)cur_buf(c), c->kp, y, bf, bd, sc); break;
-            default: closure_collide_kernel<CodecF32Dev><<<g, b, 0, c->stream>>>((float*)cur_buf(c), c->kp, y, bf, bd, sc); break;
+            case TVLBM_FP64: closure_moments_kernel<CodecF64><<<gm, bm, 0, st>>>((const double*)cur_buf(c), m6, c->kp); break;
+            case TVLBM_FP32: closure_moments_kernel<CodecF32><<<gm, bm, 0, st>>>((const float*)cur_buf(c), m6, c->kp); break;
+            default: closure_moments_kernel<CodecF32Dev><<<gm, bm, 0, st>>>((const float*)cur_buf(c), m6, c->kp); break;
+        }
+        CL_CUDA(c, cudaGetLastError(), "closure moments kernel");
+        closure_features_kernel<<<gm, bm, 0, st>>>(m6, c->nx, c->ny, nrm, (__nv_bfloat16*)x);
+        CL_CUDA(c, cudaGetLastError(), "closure features kernel");
+        const int r = mlp_forward_async(m, x, (int)ncell, y);
+        if (r) return ctx_fail(c, r, tvlbm_mlp_last_error(m));
+        switch (c->storage) {
+            case TVLBM_FP64: closure_collide_kernel<CodecF64><<<g, b, 0, st>>>((double*)cur_buf(c), c->kp, y, bf, bd, sc); break;
+            case TVLBM_FP32: closure_collide_kernel<CodecF32><<<g, b, 0, st>>>((float*)cur_buf(c), c->kp, y, bf, bd, sc); break;
+            default: closure_collide_kernel<CodecF32Dev><<<g, b, 0, st>>>((float*)cur_buf(c), c->kp, y, bf, bd, sc); break;
         }
         CL_CUDA(c, cudaGetLastError(), "closure collide kernel");
+        return TVLBM_OK;
+    };
+    // the graphs replay two steps each; they hold this network and these constants
+    float key[24];
+    for (int q = 0; q < NF; ++q) {
+        key[q] = nrm.mu[q];
+        key[NF + q] = nrm.isg[q];
+    }
+    for (int k = 0; k < NK; ++k) key[2 * NF + k] = sc.s[k];
+    if (c->cl_key_net != mlp_uid(m) || memcmp(key, c->cl_key, sizeof(key)) != 0) {
+        for (int k = 0; k < 2; ++k)
+            if (c->cl_graph[k]) {
+                cudaGraphExecDestroy(c->cl_graph[k]);
+                c->cl_graph[k] = nullptr;
+            }
+        c->cl_key_net = mlp_uid(m);
+        memcpy(c->cl_key, key, sizeof(key));
+    }
+    int left = n;
+    mlp_set_stream(m, c->stream);
+    if (c->graphs && left >= 2) {
+        if (!c->cl_graph[c->cur]) {
+            rc = one_step(c->stream);  // first launches of every kernel happen outside a capture
+            if (rc) return rc;
+            --left;
+        }
+        while (left >= 2) {
+            if (!c->cl_graph[c->cur]) {
+                const int parity = c->cur;
+                cudaGraph_t gr = nullptr;
+                CL_CUDA(c, cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+                mlp_set_stream(m, c->capture_stream);
+                int r1 = one_step(c->capture_stream);
+                if (!r1) r1 = one_step(c->capture_stream);
+                mlp_set_stream(m, c->stream);
+                const cudaError_t ce = cudaStreamEndCapture(c->capture_stream, &gr);
+                c->cur = parity;  // capture does not run the steps
+                if (r1) {
+                    if (gr) cudaGraphDestroy(gr);
+                    return r1;
+                }
+                CL_CUDA(c, ce, "end capture");
+                const cudaError_t ie = cudaGraphInstantiate(&c->cl_graph[parity], gr, 0);
+                cudaGraphDestroy(gr);
+                if (ie != cudaSuccess) {
+                    c->cl_graph[parity] = nullptr;
+                    CL_CUDA(c, ie, "graph instantiate");
+                }
+            }
+            CL_CUDA(c, cudaGraphLaunch(c->cl_graph[c->cur], c->stream), "graph launch");
+            left -= 2;  // parity unchanged
+        }
+    }
+    for (; left > 0; --left) {
+        rc = one_step(c->stream);
+        if (rc) return rc;
     }
     return TVLBM_OK;
 }

@@ -18,6 +18,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <new>
 
 #include "tvlbm.h"
@@ -527,6 +528,7 @@ struct tvlbm_mlp {
     bf16 *h1, *h1t, *g1, *h2, *h2t, *g2, *dy, *dyt, *dz2, *dz2t, *dz1t, *xt;
     float* ybuf;
     int adam_t;
+    unsigned long long uid;
     // descriptors of the last inference call (inputs at cached_x, cached_rows rows)
     const void* cached_x;
     int cached_rows;
@@ -656,6 +658,8 @@ int mlp_set_stream(tvlbm_mlp* m, cudaStream_t s) {
     return TVLBM_OK;
 }
 int mlp_status(tvlbm_mlp* m) { return read_status(m); }
+unsigned long long mlp_uid(const tvlbm_mlp* m) { return m->uid; }
+cudaStream_t mlp_stream(const tvlbm_mlp* m) { return m->stream; }
 }  // namespace tvlbm
 
 extern "C" {
@@ -669,6 +673,8 @@ int tvlbm_mlp_create(int max_rows, tvlbm_mlp** out) {
     memset(m, 0, sizeof(*m));
     cudaGetDevice(&m->device);
     m->max_rows = max_rows;
+    static std::atomic<unsigned long long> next_uid{1};
+    m->uid = next_uid.fetch_add(1);
     const size_t R = (size_t)max_rows;
     int splits = 0, cps = 0;
     split_k(max_rows / BK, &splits, &cps);

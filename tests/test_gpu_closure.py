@@ -301,6 +301,29 @@ def test_closure_step_fp32_conserves_to_storage_rounding(tv):
     sim.close()
 
 
+def test_closure_graphs_equal_direct_launches(tv):
+    """Learned steps replayed through the captured graphs (two steps each) equal direct launches
+    bit for bit, for even and odd step counts, and follow a change of the output scale."""
+    nx, ny = 64, 32
+    fields = workloads.random_smooth(nx, ny, seed=50, amp_u=0.05, amp_T=0.03)
+    p = bf16_params(cl.init_params(51, scale=1.5))
+    m = tv.Mlp(nx * ny)
+    m.set_params(cl.pack(p).astype(np.float32))
+    mu = np.array([1.0, 0.0, 0.0, 1.0, 0.0, 0.0])
+    isg = np.array([30.0, 20.0, 20.0, 30.0, 500.0, 500.0])
+    sims = []
+    for graphs in (True, False):
+        s_ = tv.Simulation(nx, ny, "D2Q16", tau=0.55, storage="fp32_dev", graphs=graphs)
+        s_.init_moments(*fields)
+        tv.step_closure(s_, m, mu, isg, np.full(12, 2e-4), 7)
+        tv.step_closure(s_, m, mu, isg, np.full(12, 1e-4), 6)
+        sims.append(s_)
+    assert np.array_equal(sims[0].raw_populations(), sims[1].raw_populations())
+    for s_ in sims:
+        s_.close()
+    m.close()
+
+
 def test_closure_rejects_unsupported_contexts(tv):
     m = tv.Mlp(1024)
     mu, isg, sc = np.zeros(6), np.ones(6), np.ones(12)
