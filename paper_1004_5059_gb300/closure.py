@@ -380,7 +380,7 @@ def rms_errors(got, want):
 
 
 def evaluate(cfg: ClosureConfig, net, norm: Normalisation, seed: int, steps: int):
-    """Fine run (the judge), plain coarse run and learned coarse run from the same start, `steps`
+    """Fine run (the reference), plain coarse run and learned coarse run from the same start, `steps`
     coarse steps after `warm`; errors of both coarse runs against the block-averaged fine run."""
     fine = _fine_sim(cfg, seed)
     fine.step(cfg.m * cfg.warm)

@@ -79,18 +79,20 @@ __device__ __forceinline__ void load_f(const typename C::T* f, const KParams& p,
         }
 }
 
-template <class C>
+// M: the arithmetic (double for the training-side entry points, float on the learned step,
+// whose features are rounded to BF16 after normalisation anyway).
+template <class C, class M = double>
 __global__ void closure_moments_kernel(const typename C::T* __restrict__ f, float* __restrict__ m6, const KParams p) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= p.nx || y >= p.ny) return;
-    double fl[Q];
-    load_f<C>(f, p, x, y, fl);
-    double rho = 0, jx = 0, jy = 0, e2 = 0, sxy = 0, sd = 0;
+    M rho = 0, jx = 0, jy = 0, e2 = 0, sxy = 0, sd = 0;
 #pragma unroll
     for (int j = 0; j < N1; ++j)
 #pragma unroll
         for (int i = 0; i < N1; ++i) {
-            const double v = fl[i + N1 * j], cx = p.xd[i], cy = p.xd[j];
+            const int l = i + N1 * j;
+            const M v = to_f<C, M>((M)C::ld(f + cell_index(p, l, x, y)), kw<M>(p, i) * kw<M>(p, j), krho0<M>(p));
+            const M cx = kx<M>(p, i), cy = kx<M>(p, j);
             rho += v;
             jx += v * cx;
             jy += v * cy;
@@ -98,8 +100,8 @@ __global__ void closure_moments_kernel(const typename C::T* __restrict__ f, floa
             sxy += v * cx * cy;
             sd += v * (cx * cx - cy * cy);
         }
-    const double ux = jx / rho, uy = jy / rho;
-    const double T = 0.5 * (e2 / rho - (ux * ux + uy * uy));
+    const M ux = jx / rho, uy = jy / rho;
+    const M T = M(0.5) * (e2 / rho - (ux * ux + uy * uy));
     const long long c = (long long)y * p.nx + x, n = (long long)p.nx * p.ny;
     m6[c] = (float)rho;
     m6[n + c] = (float)ux;
@@ -507,8 +509,8 @@ int tvlbm_step_closure(tvlbm_ctx* c, tvlbm_mlp* m, const float* mu, const float*
         const dim3 bm(32, 8), gm = grid_of(c->nx, c->ny, bm);
         switch (c->storage) {
             case TVLBM_FP64: closure_moments_kernel<CodecF64><<<gm, bm, 0, st>>>((const double*)cur_buf(c), m6, c->kp); break;
-            case TVLBM_FP32: closure_moments_kernel<CodecF32><<<gm, bm, 0, st>>>((const float*)cur_buf(c), m6, c->kp); break;
-            default: closure_moments_kernel<CodecF32Dev><<<gm, bm, 0, st>>>((const float*)cur_buf(c), m6, c->kp); break;
+            case TVLBM_FP32: closure_moments_kernel<CodecF32, float><<<gm, bm, 0, st>>>((const float*)cur_buf(c), m6, c->kp); break;
+            default: closure_moments_kernel<CodecF32Dev, float><<<gm, bm, 0, st>>>((const float*)cur_buf(c), m6, c->kp); break;
         }
         CL_CUDA(c, cudaGetLastError(), "closure moments kernel");
         closure_features_kernel<<<gm, bm, 0, st>>>(m6, c->nx, c->ny, nrm, (__nv_bfloat16*)x);

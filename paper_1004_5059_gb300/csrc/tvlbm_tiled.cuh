@@ -428,7 +428,7 @@ struct FlowCfg {
     static constexpr int STAGE_BYTES = Tile::Q * Tile::WIN_BYTES;
     // two stages where they fit (one otherwise: the producer then only overlaps the next
     // task's dependency wait with the current compute)
-    static constexpr int STAGES = 2 * STAGE_BYTES + 256 <= 227 * 1024 ? 2 : 1;
+    static constexpr int STAGES = 2 * STAGE_BYTES + 256 <= 227 * 1024 ? 2 : 1;  // (3 measured slower: fewer CTAs)
     static constexpr int CONSUMERS = Tile::THREADS;          // compute threads (whole warps)
     static constexpr int THREADS = CONSUMERS + 32;           // + the producer warp
     static constexpr uint32_t TX_BYTES = (uint32_t)(Tile::Q * Tile::BX * Tile::BY * Tile::ES);

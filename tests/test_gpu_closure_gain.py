@@ -1,7 +1,7 @@
 """What the trained closure gains over the method without it.
 
 A 256 x 256 D2Q16 run (tau = 0.8, seeded Gaussian temperature bump + random Fourier flow) is
-the judge; its 4 x 4 block average is the coarse truth.  The network is trained by the
+the reference; its 4 x 4 block average is the coarse truth.  The network is trained by the
 library's own tcgen05 kernels on four training seeds, then a held-out seed is advanced 32
 coarse steps (= 128 fine steps) by the plain coarse run (tau_c - 1/2 = (tau - 1/2) / 4) and by
 the learned coarse run from the same block-averaged start.  The learned run must be closer to
