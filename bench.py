@@ -513,7 +513,35 @@ def run_batch(args, rank, world, local_rank):
         "clocks": clk,
     }
     b.close()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = batch_cpu_baseline()
     return line if rank == 0 else None
+
+
+def batch_cpu_baseline(target_s=10.0):
+    """The oracle on a bounded sample of the batched workload: time steps of the smallest domains
+    (all of them advanced together) repeated until about target_s seconds of host work."""
+    import oracle
+    specs = sorted(workloads.batched_domains(BATCH["count"], seed=BATCH["seed"]), key=lambda s: s["n"])[:8]
+    cores = _oracle_threads()
+    sims = []
+    for s in specs:
+        o = oracle.Oracle(s["n"], s["n"], BATCH["velset"], tau=s["tau"], threads=cores)
+        o.init_moments(*batch_fields(s))
+        sims.append(o)
+    cells = sum(s["n"] ** 2 for s in specs)
+    for o in sims:
+        o.run(1)
+    done, t0 = 0, time.perf_counter()
+    while True:
+        for o in sims:
+            o.run(1)
+        done += 1
+        dt = time.perf_counter() - t0
+        if dt >= target_s:
+            break
+    return {"value": cells * done / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d time steps of the %d smallest domains (%d cells) of the same batch" % (done, len(specs), cells)}
 
 
 def run_batch_reference(args, rank):
