@@ -166,6 +166,19 @@ int tvlbm_set_graphs(tvlbm_ctx *ctx, int enable);
  * T <= 0). */
 int tvlbm_set_reference(tvlbm_ctx *ctx, double ux, double uy, double T);
 
+/* Deviation storage on a domain with walls: a reference that varies across the channel.  Fluid
+ * row y (0 <= y < ny) stores d_l = f_l / w_l - R_l(y), R_l(y) = f_eq_l(rho0, (ux[y], uy[y]), T[y]) / w_l;
+ * the ghost rows beyond a wall take the adjacent fluid row's reference.  A wall-driven flow (a
+ * Couette channel with a temperature difference) varies mostly across the channel, so a profile
+ * that follows it (e.g. linear between the wall values) keeps |d| near the non-equilibrium part
+ * and the half-precision rounding error with it.  The time step is unchanged in exact
+ * arithmetic: the gather of row y adds S_l(y), the gather of R over the source rows minus R_l(y),
+ * and the collision takes the row's reference moments.  ux, uy, T: host arrays of ny values
+ * (copied).  The current state is re-encoded (synchronises); tvlbm_set_reference returns to a
+ * single reference.  Errors: EINVAL (full-f storage, periodic domain, null array, T <= 0 or a
+ * non-finite value), ENOMEM, ECUDA. */
+int tvlbm_set_reference_rows(tvlbm_ctx *ctx, const double *ux, const double *uy, const double *T);
+
 /* Tile configurations of the tiled form (an autotuner picks among them): their number, and
  * the shape of one -- tile width and height in cells and rows each thread walks.
  * tvlbm_set_tile selects one (synchronises the stream; default 0).  Errors: EINVAL (out of

@@ -247,6 +247,41 @@ int upload_fields_and_init(tvlbm_ctx* c, const double* rho, const double* ux, co
     return TVLBM_OK;
 }
 
+void free_reference_rows(tvlbm_ctx* c) {
+    if (c->ref_rowf) cudaFree(c->ref_rowf);
+    if (c->ref_rowd) cudaFree(c->ref_rowd);
+    delete[] c->ref_rowd_host;
+    c->ref_rowf = nullptr;
+    c->ref_rowd = nullptr;
+    c->ref_rowd_host = nullptr;
+}
+
+// Pref_l of stored row r under the context's current reference.
+double current_pref(const tvlbm_ctx* c, int r, int l) {
+    return c->ref_rowd_host ? c->ref_rowd_host[(size_t)r * kRowD + l] : c->kp.Prefd[l];
+}
+
+// Re-encode the current state from the context's reference to the one whose Pref is new_pref(r, l)
+// (d += Pref_old - Pref_new on every stored element), synchronously.
+template <class F>
+int reencode_to(tvlbm_ctx* c, F new_pref) {
+    const int rows = c->L.rows;
+    float* h = new (std::nothrow) float[(size_t)rows * kMaxQ];
+    if (!h) return fail(c, TVLBM_ENOMEM, "host table");
+    for (int r = 0; r < rows; ++r)
+        for (int l = 0; l < kMaxQ; ++l)
+            h[(size_t)r * kMaxQ + l] = l < c->Q ? (float)(current_pref(c, r, l) - new_pref(r, l)) : 0.0f;
+    float* d = nullptr;
+    cudaError_t e = cudaMalloc((void**)&d, sizeof(float) * (size_t)rows * kMaxQ);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d, h, sizeof(float) * (size_t)rows * kMaxQ, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = c->kt->reencode(c->storage, fcur(c), d, c->kp, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (d) cudaFree(d);
+    delete[] h;
+    if (e != cudaSuccess) return fail(c, TVLBM_ECUDA, "reencode: %s", cudaGetErrorString(e));
+    return TVLBM_OK;
+}
+
 }  // namespace
 
 // =============================================================================================
@@ -285,6 +320,7 @@ int tvlbm_destroy(tvlbm_ctx* c) {
     if (c->fv_omega) cudaFree(c->fv_omega);
     if (c->fv_dy) cudaFree(c->fv_dy);
     if (c->fv_wall_eq) cudaFree(c->fv_wall_eq);
+    free_reference_rows(c);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     if (c->own_mem && c->mem) cudaFree(c->mem);
     delete c;
@@ -318,6 +354,7 @@ int tvlbm_set_graphs(tvlbm_ctx* c, int enable) {
     return TVLBM_OK;
 }
 
+
 int tvlbm_set_reference(tvlbm_ctx* c, double ux, double uy, double T) {
     if (!c) return TVLBM_EINVAL;
     if (c->storage == TVLBM_FP64 || c->storage == TVLBM_FP32)
@@ -327,12 +364,56 @@ int tvlbm_set_reference(tvlbm_ctx* c, double ux, double uy, double T) {
     cudaSetDevice(c->device);
     KParams np = c->kp;
     set_reference_params(np, c->rule, c->rho0, ux, uy, T);
-    RefShift sh;
-    memset(&sh, 0, sizeof(sh));
-    for (int l = 0; l < c->Q; ++l) sh.delta[l] = (float)(c->kp.Prefd[l] - np.Prefd[l]);
-    TVLBM_CUDA(c, c->kt->reencode(c->storage, fcur(c), sh, c->kp, c->stream), "reencode kernel");
-    TVLBM_CUDA(c, cudaStreamSynchronize(c->stream), "reencode synchronize");
+    const int rc = reencode_to(c, [&](int, int l) { return np.Prefd[l]; });
+    if (rc) return rc;
+    free_reference_rows(c);
     c->kp = np;
+    drop_graphs(c);
+    return TVLBM_OK;
+}
+
+int tvlbm_set_reference_rows(tvlbm_ctx* c, const double* ux, const double* uy, const double* T) {
+    if (!c) return TVLBM_EINVAL;
+    if (c->storage == TVLBM_FP64 || c->storage == TVLBM_FP32)
+        return fail(c, TVLBM_EINVAL, "the reference applies to deviation storage only");
+    if (!c->kp.walls) return fail(c, TVLBM_EINVAL, "a per-row reference needs a domain with walls");
+    if (!ux || !uy || !T) return fail(c, TVLBM_EINVAL, "null profile");
+    for (int y = 0; y < c->ny; ++y)
+        if (!(T[y] > 0.0) || !isfinite(T[y]) || !isfinite(ux[y]) || !isfinite(uy[y]))
+            return fail(c, TVLBM_EINVAL, "row %d: the reference needs T > 0 and a finite velocity", y);
+    cudaSetDevice(c->device);
+    const int rows = c->L.rows;
+    float* hf = new (std::nothrow) float[(size_t)rows * kRowF];
+    double* hd = new (std::nothrow) double[(size_t)rows * kRowD];
+    if (!hf || !hd) {
+        delete[] hf;
+        delete[] hd;
+        return fail(c, TVLBM_ENOMEM, "host tables");
+    }
+    reference_rows(c->kp, c->rule, c->rho0, c->ny, rows, ux, uy, T, hf, hd);
+    float* df = nullptr;
+    double* dd = nullptr;
+    cudaError_t e = cudaMalloc((void**)&df, sizeof(float) * (size_t)rows * kRowF);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&dd, sizeof(double) * (size_t)rows * kRowD);
+    if (e == cudaSuccess) e = cudaMemcpy(df, hf, sizeof(float) * (size_t)rows * kRowF, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dd, hd, sizeof(double) * (size_t)rows * kRowD, cudaMemcpyHostToDevice);
+    int rc = e == cudaSuccess ? TVLBM_OK : fail(c, TVLBM_ECUDA, "row tables: %s", cudaGetErrorString(e));
+    if (!rc) rc = reencode_to(c, [&](int r, int l) { return hd[(size_t)r * kRowD + l]; });
+    delete[] hf;
+    if (rc) {
+        if (df) cudaFree(df);
+        if (dd) cudaFree(dd);
+        delete[] hd;
+        return rc;
+    }
+    free_reference_rows(c);
+    c->ref_rowf = df;
+    c->ref_rowd = dd;
+    c->ref_rowd_host = hd;
+    set_reference_params(c->kp, c->rule, c->rho0, 0.0, 0.0, 1.0);
+    c->kp.has_ref = 1;
+    c->kp.rowf = df;
+    c->kp.rowd = dd;
     drop_graphs(c);
     return TVLBM_OK;
 }

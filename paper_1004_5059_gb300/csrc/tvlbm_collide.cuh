@@ -31,8 +31,10 @@
 
 namespace tvlbm {
 
+// row: the cell row's entries of a per-row reference table (KParams::rowf), or null.
 template <int N1>
-__device__ __forceinline__ void cell_collide_dev(float (&s)[N1 * N1], const KParams& p, float om) {
+__device__ __forceinline__ void cell_collide_dev(float (&s)[N1 * N1], const KParams& p, float om,
+                                                 const float* row = nullptr) {
     constexpr int N = N1 - 1, H = N1 / 2;
     constexpr bool ODD = (N1 & 1) != 0;
     // ---- moments: rho = rho0 + sum w d, rho u = sum w c d, sum w |c|^2 d --------------------
@@ -74,8 +76,10 @@ __device__ __forceinline__ void cell_collide_dev(float (&s)[N1 * N1], const KPar
     // direction that repeats from step to step, and the equilibrium velocity it feeds drifted by
     // 1.4e-5 over 1000 steps of the 1024^2 workload (1.4e-6 with this one)
     const float inv = __frcp_rn(rho);
-    const float ux = (p.jreff[0] + mx) * inv, uy = (p.jreff[1] + my) * inv;
-    const float th = 0.5f * ((p.ereff + me - 2.0f * m0) * inv - (ux * ux + uy * uy));
+    const float jrx = row ? __ldg(row + 2 * kMaxQ) : p.jreff[0], jry = row ? __ldg(row + 2 * kMaxQ + 1) : p.jreff[1];
+    const float eref = row ? __ldg(row + 2 * kMaxQ + 2) : p.ereff;
+    const float ux = (jrx + mx) * inv, uy = (jry + my) * inv;
+    const float th = 0.5f * ((eref + me - 2.0f * m0) * inv - (ux * ux + uy * uy));
 
     // ---- Hermite coefficients of the Maxwellian, per axis ----------------------------------
     float hx[N + 1], hy[N + 1];
@@ -89,8 +93,11 @@ __device__ __forceinline__ void cell_collide_dev(float (&s)[N1 * N1], const KPar
     }
 
     // ---- first-order cancellation of the table defects -------------------------------------
-    float Dm = fmaf(2.f * p.dS[0], m0, p.refD[0]), De = fmaf(2.f * m0, p.dVS[0], p.refD[3]);
-    float Dx = fmaf(rho * ux, p.dUS, p.refD[1]), Dy = fmaf(rho * uy, p.dUS, p.refD[2]);
+    // (scalar selects: a pointer into the parameter block would copy it to local memory)
+    const float rD0 = row ? __ldg(row + 2 * kMaxQ + 3) : p.refD[0], rD1 = row ? __ldg(row + 2 * kMaxQ + 4) : p.refD[1];
+    const float rD2 = row ? __ldg(row + 2 * kMaxQ + 5) : p.refD[2], rD3 = row ? __ldg(row + 2 * kMaxQ + 6) : p.refD[3];
+    float Dm = fmaf(2.f * p.dS[0], m0, rD0), De = fmaf(2.f * m0, p.dVS[0], rD3);
+    float Dx = fmaf(rho * ux, p.dUS, rD1), Dy = fmaf(rho * uy, p.dUS, rD2);
 #pragma unroll
     for (int a = 2; a <= N; a += 2) {  // dS, dV vanish for odd orders (mirror symmetry)
         const float hs = rho * (hx[a] + hy[a]);
@@ -151,7 +158,10 @@ __device__ __forceinline__ void cell_collide_dev(float (&s)[N1 * N1], const KPar
             s[i + N1 * j] = fmaf(keep, s[i + N1 * j], weq);
         }
     }
-    if (p.has_ref) {  // the reference's own deviation: d_eq -= Pref
+    if (row) {  // the row reference's own deviation: d_eq -= Pref(y)
+#pragma unroll
+        for (int l = 0; l < N1 * N1; ++l) s[l] = fmaf(-om, __ldg(row + l), s[l]);
+    } else if (p.has_ref) {  // the reference's own deviation: d_eq -= Pref
 #pragma unroll
         for (int l = 0; l < N1 * N1; ++l) s[l] = fmaf(-om, p.Preff[l], s[l]);
     }

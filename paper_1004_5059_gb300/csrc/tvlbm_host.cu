@@ -334,44 +334,94 @@ bool encode_tensor_map(CUtensorMap* m, void* base, int storage, const Layout& L,
     return r == CUDA_SUCCESS;
 }
 
-void set_reference_params(KParams& p, const Rule& r, double rho0, double ux, double uy, double T) {
-    const int n = r.n, Q = n * n;
+RefEntry reference_entry(const KParams& p, const Rule& r, double rho0, double ux, double uy, double T) {
+    const int n = r.n;
+    RefEntry e;
+    memset(&e, 0, sizeof(e));
     double feq[kMaxQ];
     host_equilibrium(r, rho0, ux, uy, T, feq);
-    p.has_ref = 0;
-    for (int l = 0; l < kMaxQ; ++l) {
-        p.Prefd[l] = 0.0;
-        p.Preff[l] = 0.0f;
-    }
+    const bool rest = ux == 0.0 && uy == 0.0 && T == 1.0;
     for (int j = 0; j < n; ++j)
         for (int i = 0; i < n; ++i) {
             const int l = i + n * j;
-            const double pr = (ux == 0.0 && uy == 0.0 && T == 1.0) ? 0.0 : feq[l] / (r.w[i] * r.w[j]) - rho0;
-            p.Prefd[l] = pr;
-            p.Preff[l] = (float)pr;
-            if (pr != 0.0) p.has_ref = 1;
+            const double pr = rest ? 0.0 : feq[l] / (r.w[i] * r.w[j]) - rho0;
+            e.Prefd[l] = pr;
+            e.Preff[l] = (float)pr;
+            if (pr != 0.0) e.nonzero = true;
         }
-    p.jrefd[0] = rho0 * ux;
-    p.jrefd[1] = rho0 * uy;
-    p.erefd = rho0 * (2.0 * (T - 1.0) + ux * ux + uy * uy);
-    p.jreff[0] = (float)p.jrefd[0];
-    p.jreff[1] = (float)p.jrefd[1];
-    p.ereff = (float)p.erefd;
+    e.jrefd[0] = rho0 * ux;
+    e.jrefd[1] = rho0 * uy;
+    e.erefd = rho0 * (2.0 * (T - 1.0) + ux * ux + uy * uy);
+    e.jreff[0] = (float)e.jrefd[0];
+    e.jreff[1] = (float)e.jrefd[1];
+    e.ereff = (float)e.erefd;
     // the reference table's moments under the FP32 moment constants, exactly, minus their ideal
     long double m = 0, mx = 0, my = 0, me = 0;
     for (int j = 0; j < n; ++j)
         for (int i = 0; i < n; ++i) {
-            const long double v = p.Preff[i + n * j];
+            const long double v = e.Preff[i + n * j];
             m += (long double)p.wf[i] * p.wf[j] * v;
             mx += (long double)p.wxf[i] * p.wf[j] * v;
             my += (long double)p.wf[i] * p.wxf[j] * v;
             me += ((long double)p.wx2f[i] * p.wf[j] + (long double)p.wf[i] * p.wx2f[j]) * v;
         }
-    p.refD[0] = (float)(-(m - 0.0L));
-    p.refD[1] = (float)(-(mx - (long double)p.jreff[0]));
-    p.refD[2] = (float)(-(my - (long double)p.jreff[1]));
-    p.refD[3] = (float)(-(me - (long double)p.ereff));
-    (void)Q;
+    e.refD[0] = (float)(-(m - 0.0L));
+    e.refD[1] = (float)(-(mx - (long double)e.jreff[0]));
+    e.refD[2] = (float)(-(my - (long double)e.jreff[1]));
+    e.refD[3] = (float)(-(me - (long double)e.ereff));
+    return e;
+}
+
+void set_reference_params(KParams& p, const Rule& r, double rho0, double ux, double uy, double T) {
+    const RefEntry e = reference_entry(p, r, rho0, ux, uy, T);
+    p.has_ref = e.nonzero ? 1 : 0;
+    memcpy(p.Prefd, e.Prefd, sizeof(p.Prefd));
+    memcpy(p.Preff, e.Preff, sizeof(p.Preff));
+    p.jrefd[0] = e.jrefd[0];
+    p.jrefd[1] = e.jrefd[1];
+    p.erefd = e.erefd;
+    p.jreff[0] = e.jreff[0];
+    p.jreff[1] = e.jreff[1];
+    p.ereff = e.ereff;
+    memcpy(p.refD, e.refD, sizeof(p.refD));
+    p.rowf = nullptr;
+    p.rowd = nullptr;
+}
+
+void reference_rows(const KParams& p, const Rule& r, double rho0, int ny, int rows, const double* ux,
+                    const double* uy, const double* T, float* rowf, double* rowd) {
+    const int n = r.n, Q = n * n;
+    memset(rowf, 0, sizeof(float) * (size_t)rows * kRowF);
+    memset(rowd, 0, sizeof(double) * (size_t)rows * kRowD);
+    for (int row = 0; row < rows; ++row) {
+        int y = row - HY;
+        y = y < 0 ? 0 : (y >= ny ? ny - 1 : y);
+        const RefEntry e = reference_entry(p, r, rho0, ux[y], uy[y], T[y]);
+        float* f = rowf + (size_t)row * kRowF;
+        double* d = rowd + (size_t)row * kRowD;
+        for (int l = 0; l < Q; ++l) {
+            f[l] = e.Preff[l];
+            d[l] = e.Prefd[l];
+        }
+        f[2 * kMaxQ + 0] = e.jreff[0];
+        f[2 * kMaxQ + 1] = e.jreff[1];
+        f[2 * kMaxQ + 2] = e.ereff;
+        for (int k = 0; k < 4; ++k) f[2 * kMaxQ + 3 + k] = e.refD[k];
+        d[kMaxQ + 0] = e.jrefd[0];
+        d[kMaxQ + 1] = e.jrefd[1];
+        d[kMaxQ + 2] = e.erefd;
+    }
+    // gather shift of the fluid rows (the sources of row y lie within FILL rows of it)
+    for (int y = 0; y < ny; ++y)
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) {
+                const int l = i + n * j;
+                const double a = p.ad[j];
+                const double r0 = rowd[(size_t)(y - p.sh[j] + HY) * kRowD + l];
+                const double r1 = rowd[(size_t)(y - p.sh[j] - 1 + HY) * kRowD + l];
+                const double self = rowd[(size_t)(y + HY) * kRowD + l];
+                rowf[(size_t)(y + HY) * kRowF + kMaxQ + l] = (float)((1.0 - a) * r0 + a * r1 - self);
+            }
 }
 
 }  // namespace host

@@ -50,9 +50,27 @@ int validate(int nx, int ny, int velset, double tau, double dt, const tvlbm_bc* 
 void fill_kparams(KParams& p, const Rule& r, int N, double dt, double tau, double rho0, int nx, int ny,
                   const Layout& L, const tvlbm_bc& bc);
 
-// Deviation-storage reference of the kernel parameters: R_l = f_eq_l(rho0, u_ref, T_ref) / w_l
-// (Pref, jref, eref, refD, has_ref); (0, 0, 1) is the default reference.
+// One deviation-storage reference R_l = f_eq_l(rho0, u_ref, T_ref) / w_l: Pref = R - rho0 in FP64
+// and float, jref, eref and refD (the float Pref table's share of the FP32 constants' defects,
+// see KParams); nonzero unless it is the default reference (0, 0, 1).
+struct RefEntry {
+    double Prefd[kMaxQ];
+    float Preff[kMaxQ];
+    double jrefd[2], erefd;
+    float jreff[2], ereff, refD[4];
+    bool nonzero;
+};
+RefEntry reference_entry(const KParams& p, const Rule& r, double rho0, double ux, double uy, double T);
+
+// Single deviation-storage reference of the kernel parameters (Pref, jref, eref, refD, has_ref;
+// clears the per-row tables); (0, 0, 1) is the default reference.
 void set_reference_params(KParams& p, const Rule& r, double rho0, double ux, double uy, double T);
+
+// Per-row reference tables in the layout of KParams::rowf / rowd over `rows` stored rows: fluid
+// row y takes (ux[y], uy[y], T[y]); a ghost row takes the nearest fluid row's.  rowf holds
+// rows * kRowF floats, rowd rows * kRowD doubles.
+void reference_rows(const KParams& p, const Rule& r, double rho0, int ny, int rows, const double* ux,
+                    const double* uy, const double* T, float* rowf, double* rowd);
 
 // TMA descriptor of one population buffer: a 3-D view [Q][rows][pitch], box bx x by x 1.
 bool encode_tensor_map(CUtensorMap* m, void* base, int storage, const Layout& L, int Q, int bx, int by);

@@ -25,6 +25,8 @@ constexpr int FILL = 4;
 constexpr int kRedBlocks = 1024;  // fixed partial count of the FP64 reduction (deterministic)
 constexpr int kTileConfigs = 4;  // tile shapes of the tiled form
 constexpr int kFlowDone = 16;    // first per-tile counter in the dataflow scratch (64-byte aligned)
+constexpr int kRowF = 2 * kMaxQ + 8;  // floats per stored row of the per-row reference table
+constexpr int kRowD = kMaxQ + 4;      // doubles per stored row of its FP64 table
 
 enum Storage { ST_FP64 = 0, ST_FP32 = 1, ST_BF16_DEV = 2, ST_FP16_DEV = 3, ST_FP32_DEV = 4 };
 enum Form { FORM_PLAIN = 0, FORM_TILED = 1, FORM_FLOW = 2 };
@@ -73,6 +75,15 @@ struct KParams {
     double Prefd[kMaxQ];
     float jreff[2], ereff, refD[4];
     double jrefd[2], erefd;
+    // Per-row reference of a domain with walls (null: the single reference above).  Stored row
+    // r = y + HY (ghost rows included) has its own Pref_l, jref, eref and refD, as above but for
+    // R_l(y) = f_eq_l(rho0, u_ref(y), T_ref(y)) / w_l, and the gather shift S_l(y): streaming
+    // moves d_l + R_l(y_source), so the gathered deviation against R_l(y) is the gather of d plus
+    // S_l(y) = (1 - a_j) R_l(y - sh_j) + a_j R_l(y - sh_j - 1) - R_l(y)  (exact: R is constant in x).
+    //   rowf[r * kRowF + l]: Pref_l; [kMaxQ + l]: S_l; [2 kMaxQ + 0..1]: jref; [+2]: eref; [+3..6]: refD
+    //   rowd[r * kRowD + l]: Pref_l; [kMaxQ + 0..1]: jref; [kMaxQ + 2]: eref
+    const float* rowf;
+    const double* rowd;
     // Device status word: bit 0 is set by a kernel whose bounded wait gave up.
     int* status;
 };
@@ -121,6 +132,13 @@ template <class R> __device__ __forceinline__ R krho0(const KParams& p) {
 }
 template <class R> __device__ __forceinline__ R kPref(const KParams& p, int l) {
     if constexpr (std::is_same<R, double>::value) return p.Prefd[l]; else return p.Preff[l];
+}
+// Pref_l of fluid row y (y may be a ghost row), per-row table or the single reference.
+template <class R> __device__ __forceinline__ R kPrefRow(const KParams& p, int l, int y) {
+    if constexpr (std::is_same<R, double>::value)
+        return p.rowd ? __ldg(p.rowd + (long long)(y + HY) * kRowD + l) : p.Prefd[l];
+    else
+        return p.rowf ? __ldg(p.rowf + (long long)(y + HY) * kRowF + l) : p.Preff[l];
 }
 template <class R> __device__ __forceinline__ R kjref(const KParams& p, int k) {
     if constexpr (std::is_same<R, double>::value) return p.jrefd[k]; else return p.jreff[k];
@@ -179,8 +197,10 @@ __device__ __forceinline__ R from_f(R f, R w, R ref) { if constexpr (C::dev) ret
 // with D = 2.  In deviation space f = w (R + d) with R the reference's f_eq / w, whose moments
 // are (rho0, rho0 u_ref, rho0 (D T_ref + u_ref^2)) by exact quadrature, so rho = rho0 + sum w d,
 // rho u = jref + sum w c d, and T - 1 = ((eref + sum w |c|^2 d - D sum w d)/rho - u^2)/D.
+// ref3: the cell row's reference moments (jref_x, jref_y, eref) of a per-row reference, or null.
 template <int N1, bool DEV, class R>
-__device__ __forceinline__ void cell_moments(const R (&s)[N1 * N1], const KParams& p, R& rho, R& ux, R& uy, R& th) {
+__device__ __forceinline__ void cell_moments(const R (&s)[N1 * N1], const KParams& p, R& rho, R& ux, R& uy, R& th,
+                                             const R* ref3 = nullptr) {
     R m0 = 0, mx = 0, my = 0, me = 0;
 #pragma unroll
     for (int j = 0; j < N1; ++j) {
@@ -203,9 +223,9 @@ __device__ __forceinline__ void cell_moments(const R (&s)[N1 * N1], const KParam
     if constexpr (DEV) {
         rho = krho0<R>(p) + m0;
         const R inv = R(1) / rho;
-        ux = (kjref<R>(p, 0) + mx) * inv;
-        uy = (kjref<R>(p, 1) + my) * inv;
-        th = R(0.5) * ((keref<R>(p) + me - R(2) * m0) * inv - (ux * ux + uy * uy));
+        ux = ((ref3 ? ref3[0] : kjref<R>(p, 0)) + mx) * inv;
+        uy = ((ref3 ? ref3[1] : kjref<R>(p, 1)) + my) * inv;
+        th = R(0.5) * (((ref3 ? ref3[2] : keref<R>(p)) + me - R(2) * m0) * inv - (ux * ux + uy * uy));
     } else {
         rho = m0;
         const R inv = R(1) / rho;
@@ -222,8 +242,10 @@ __device__ __forceinline__ void cell_moments(const R (&s)[N1 * N1], const KParam
 // With X_ia = h_a(u_x) E_ia (X_i0 = 1), P_jk = sum_{1<=b<=k} h_b(u_y) E_jb:
 //   sum_{a+b<=N} X_ia Y_jb = 1 + phi_ij,  phi_ij = sum_{a>=1} X_ia + sum_{a<N} X_ia P_j,N-a.
 // Storage-space equilibrium: full f_eq = w rho (1 + phi); deviation d_eq = (rho - rho0) + rho phi - Pref.
+// pref: the cell row's Pref table of a per-row reference, or null.
 template <int N1, bool DEV, class R>
-__device__ __forceinline__ void cell_equilibrium(const KParams& p, R rho, R ux, R uy, R th, R (&eq)[N1 * N1]) {
+__device__ __forceinline__ void cell_equilibrium(const KParams& p, R rho, R ux, R uy, R th, R (&eq)[N1 * N1],
+                                                 const R* pref = nullptr) {
     constexpr int N = N1 - 1;
     R hx[N + 1], hy[N + 1];
     hx[0] = R(1); hy[0] = R(1);
@@ -255,7 +277,7 @@ __device__ __forceinline__ void cell_equilibrium(const KParams& p, R rho, R ux, 
             R phi = SX[i] + P[j][N];  // a = 0 term: X_i0 = 1
 #pragma unroll
             for (int a = 1; a < N; ++a) phi = fma(X[i][a], P[j][N - a], phi);
-            if constexpr (DEV) eq[i + N1 * j] = fma(rho, phi, drho) - kPref<R>(p, i + N1 * j);
+            if constexpr (DEV) eq[i + N1 * j] = fma(rho, phi, drho) - (pref ? pref[i + N1 * j] : kPref<R>(p, i + N1 * j));
             else eq[i + N1 * j] = (kw<R>(p, i) * kw<R>(p, j) * rho) * (R(1) + phi);
         }
     }
@@ -344,11 +366,6 @@ struct FlowSrc {
 
 struct BatchSrc;  // tile source of the batched sweep (tvlbm_tiled.cuh)
 
-// Per-velocity change of the deviation reference: d_l += delta_l re-expresses stored
-// populations against a new reference.
-struct RefShift {
-    float delta[kMaxQ];
-};
 
 // ---- kernel table (one per N1, defined in tvlbm_kernels_q*.cu) ----------------------------
 struct KernelTable {
@@ -365,8 +382,9 @@ struct KernelTable {
     int (*tiled_available)(int storage);
     void (*tiled_box)(int storage, int cfg, int* bx, int* by);  // TMA box (elements) of a tile config
     void (*tile_shape)(int storage, int cfg, int* tx, int* ty, int* rows_per_thread);
-    // re-express every stored element of buffer f against a new deviation reference
-    cudaError_t (*reencode)(int storage, void* f, const RefShift& shift, const KParams& p, cudaStream_t s);
+    // re-express every stored element of buffer f against a new deviation reference:
+    // d_l += delta[r * kMaxQ + l] on stored row r (delta: device, [rows][kMaxQ])
+    cudaError_t (*reencode)(int storage, void* f, const float* delta, const KParams& p, cudaStream_t s);
     // n time steps of one periodic domain in a single dataflow launch
     cudaError_t (*flow_sweep)(int storage, int cfg, const FlowSrc& src, const KParams& p, cudaStream_t s);
     // one time step of every domain of a batch (persistent launch over all tiles)

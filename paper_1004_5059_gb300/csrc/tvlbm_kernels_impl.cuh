@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(256) sweep_plain_kernel(const typename C::T* _
         }
     }
     const Geom g = geom_of(p);
-    collide_cell<N1, C>(s, p, g);
+    collide_cell<N1, C>(s, p, g, y);
     store_collided<N1, C>(fout, g, x, y, s);
 }
 
@@ -61,7 +61,7 @@ __global__ void init_kernel(const double* __restrict__ fields, typename C::T* __
     const long long c = (long long)y * p.nx + x, n = (long long)p.nx * p.ny;
     const double rho = fields[c], ux = fields[n + c], uy = fields[2 * n + c], T = fields[3 * n + c];
     double eq[Q];
-    cell_equilibrium<N1, C::dev, double>(p, rho, ux, uy, T - 1.0, eq);
+    cell_equilibrium<N1, C::dev, double>(p, rho, ux, uy, T - 1.0, eq, p.rowd ? p.rowd + (long long)(y + HY) * kRowD : nullptr);
 #pragma unroll
     const Geom g = geom_of(p);
 #pragma unroll
@@ -81,7 +81,8 @@ __global__ void moments_kernel(const typename C::T* __restrict__ f, double* __re
 #pragma unroll
     for (int l = 0; l < Q; ++l) s[l] = (double)C::ld(f + sidx(p, l, x, y));
     double rho, ux, uy, th;
-    cell_moments<N1, C::dev, double>(s, p, rho, ux, uy, th);
+    cell_moments<N1, C::dev, double>(s, p, rho, ux, uy, th,
+                                      p.rowd ? p.rowd + (long long)(y + HY) * kRowD + kMaxQ : nullptr);
     const long long c = (long long)y * p.nx + x, n = (long long)p.nx * p.ny;
     out4[c] = rho;
     out4[n + c] = ux;
@@ -116,7 +117,7 @@ __global__ void __launch_bounds__(256) reduce_kernel(const typename C::T* __rest
             for (int i = 0; i < N1; ++i) {
                 const double v = (double)C::ld(f + sidx(p, i + N1 * j, x, y));
                 acc[4] += isfinite(v) ? 0.0 : 1.0;
-                const double fv = to_f<C, double>(v, p.wd[i] * p.wd[j], p.rho0d + p.Prefd[i + N1 * j]);
+                const double fv = to_f<C, double>(v, p.wd[i] * p.wd[j], p.rho0d + kPrefRow<double>(p, i + N1 * j, y));
                 r += fv;
                 rx += p.xd[i] * fv;
                 rxx += p.xd[i] * p.xd[i] * fv;
@@ -204,7 +205,7 @@ __global__ void wall_kernel(typename C::T* __restrict__ f, const KParams p) {
                     for (int pp = 0; pp < 2; ++pp) {
                         const int xs = x - p.sh[i] - pp;
                         const R wx = pp ? ax : R(1) - ax;
-                        acc += wx * wy * to_f<C, R>(C::ld(f + sidx(p, l, xs, ys)), w, rho0 + kPref<R>(p, l));
+                        acc += wx * wy * to_f<C, R>(C::ld(f + sidx(p, l, xs, ys)), w, rho0 + kPrefRow<R>(p, l, ys));
                     }
                 }
                 mout += acc;
@@ -221,10 +222,10 @@ __global__ void wall_kernel(typename C::T* __restrict__ f, const KParams p) {
         for (int i = 0; i < N1; ++i) {
             const int l = i + N1 * j;
             const R w = kw<R>(p, i) * kw<R>(p, j);
-            const typename C::T v = C::enc(from_f<C, R>(A * kfeqw<R>(p, side, l), w, rho0 + kPref<R>(p, l)));
+            const R fw = A * kfeqw<R>(p, side, l);
             for (int d = 1; d <= HY; ++d) {
                 const int yd = side == 0 ? -d : p.ny - 1 + d;
-                f[sidx(p, l, xo, yd)] = v;
+                f[sidx(p, l, xo, yd)] = C::enc(from_f<C, R>(fw, w, rho0 + kPrefRow<R>(p, l, yd)));
             }
         }
     }
@@ -249,13 +250,16 @@ __global__ void halo_kernel(T* __restrict__ f, const KParams p, int Q) {
     }
 }
 
-// d_l += delta_l on every stored element (fluid and frame) of a deviation-coded buffer.
+// d_l += delta[r][l] on every stored element (fluid and frame, stored row r) of a
+// deviation-coded buffer.
 template <class C>
-__global__ void reencode_kernel(typename C::T* __restrict__ f, long long plane, int Q, const RefShift sh) {
+__global__ void reencode_kernel(typename C::T* __restrict__ f, long long plane, int pitch, int Q,
+                                const float* __restrict__ delta) {
     const long long n = plane * Q;
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
         const int l = (int)(t / plane);
-        f[t] = C::enc(C::ld(f + t) + sh.delta[l]);
+        const int r = (int)((t - (long long)l * plane) / pitch);
+        f[t] = C::enc(C::ld(f + t) + __ldg(delta + (long long)r * kMaxQ + l));
     }
 }
 
@@ -266,7 +270,7 @@ __global__ void decode_plane_kernel(const typename C::T* __restrict__ f, int l, 
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= p.nx || y >= p.ny) return;
     const double w = p.wd[l % n1] * p.wd[l / n1];
-    out[(long long)y * p.nx + x] = to_f<C, double>((double)C::ld(f + sidx(p, l, x, y)), w, p.rho0d + p.Prefd[l]);
+    out[(long long)y * p.nx + x] = to_f<C, double>((double)C::ld(f + sidx(p, l, x, y)), w, p.rho0d + kPrefRow<double>(p, l, y));
 }
 template <class C>
 __global__ void encode_plane_kernel(typename C::T* __restrict__ f, int l, int n1, const double* __restrict__ in,
@@ -274,7 +278,8 @@ __global__ void encode_plane_kernel(typename C::T* __restrict__ f, int l, int n1
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= p.nx || y >= p.ny) return;
     const double w = p.wd[l % n1] * p.wd[l / n1];
-    f[sidx(p, l, x, y)] = C::enc((typename C::R)from_f<C, double>(in[(long long)y * p.nx + x], w, p.rho0d + p.Prefd[l]));
+    f[sidx(p, l, x, y)] =
+        C::enc((typename C::R)from_f<C, double>(in[(long long)y * p.nx + x], w, p.rho0d + kPrefRow<double>(p, l, y)));
 }
 
 // =============================================================================================
@@ -322,9 +327,9 @@ struct Launch {
         return cudaGetLastError();
     }
     template <class C>
-    static cudaError_t reencode_c(void* f, const RefShift& sh, const KParams& p, cudaStream_t s) {
+    static cudaError_t reencode_c(void* f, const float* delta, const KParams& p, cudaStream_t s) {
         if constexpr (!C::dev) return cudaErrorInvalidValue;
-        reencode_kernel<C><<<1024, 256, 0, s>>>((typename C::T*)f, p.plane, N1 * N1, sh);
+        reencode_kernel<C><<<1024, 256, 0, s>>>((typename C::T*)f, p.plane, p.pitch, N1 * N1, delta);
         return cudaGetLastError();
     }
     template <class C>
@@ -388,8 +393,8 @@ struct Launch {
         *ty = t.ty;
         *r = t.ty / t.rs;
     }
-    static cudaError_t reencode(int storage, void* f, const RefShift& sh, const KParams& p, cudaStream_t s) {
-        TVLBM_DISPATCH(reencode_c, (f, sh, p, s))
+    static cudaError_t reencode(int storage, void* f, const float* delta, const KParams& p, cudaStream_t s) {
+        TVLBM_DISPATCH(reencode_c, (f, delta, p, s))
     }
     static cudaError_t flow(int storage, int cfg, const FlowSrc& src, const KParams& p, cudaStream_t s) {
         switch (storage) {

@@ -131,10 +131,20 @@ __device__ __forceinline__ void store_images_of(T* f, const Geom& g, long long l
             if (xx != x || yy != y) stg(f + lbase + (long long)(yy + HY) * g.pitch + (xx + g.hx), v);
 }
 
-// Collision of one gathered cell in the codec's arithmetic, relaxation rate of the domain.
-template <int N1, class C>
-__device__ __forceinline__ void collide_cell(typename C::R (&s)[N1 * N1], const KParams& p, const Geom& g) {
-    if constexpr (C::dev) cell_collide_dev<N1>(s, p, g.omegaf);
+// Collision of one gathered cell (fluid row y) in the codec's arithmetic, relaxation rate of the
+// domain.  With a per-row deviation reference the gathered deviations first take the row's
+// gather shift S_l(y), then collide against the row's reference (ROWS = false: the launch never
+// has one, e.g. a periodic-only form).
+template <int N1, class C, bool ROWS = true>
+__device__ __forceinline__ void collide_cell(typename C::R (&s)[N1 * N1], const KParams& p, const Geom& g, int y) {
+    if constexpr (C::dev) {
+        const float* row = ROWS && p.rowf ? p.rowf + (long long)(y + HY) * kRowF : nullptr;
+        if (row) {
+#pragma unroll
+            for (int l = 0; l < N1 * N1; ++l) s[l] += __ldg(row + kMaxQ + l);
+        }
+        cell_collide_dev<N1>(s, p, g.omegaf, row);
+    }
     else if constexpr (std::is_same<typename C::R, double>::value) cell_collide<N1, false, double>(s, p, g.omegad);
     else cell_collide<N1, false, float>(s, p, g.omegaf);
 }
@@ -209,7 +219,7 @@ struct BatchSrc {
 };
 
 // Gather, collide and store one tile whose Q windows are in shared memory at base.
-template <int N1, class C, int CFG>
+template <int N1, class C, int CFG, bool ROWS>
 __device__ __forceinline__ void tile_compute(const unsigned char* base, int x0, int y0, const Geom& g,
                                              typename C::T* fout, const KParams& p, int tid) {
     using Cfg = TileCfg<N1, C, CFG>;
@@ -252,7 +262,7 @@ __device__ __forceinline__ void tile_compute(const unsigned char* base, int x0, 
         }
         const int y = y0 + r0 + kk;
         if (x < g.nx && y < g.ny) {
-            collide_cell<N1, C>(s, p, g);
+            collide_cell<N1, C, ROWS>(s, p, g, y);
             store_collided<N1, C>(fout, g, x, y, s);
         }
     }
@@ -319,7 +329,8 @@ __global__ void __launch_bounds__(TileCfg<N1, C, CFG>::THREADS)
         return;
     }
 
-    tile_compute<N1, C, CFG>(base, x0, y0, g, reinterpret_cast<T*>(outv), p, tid);
+    // only a single domain can have walls, and with them a per-row reference
+    tile_compute<N1, C, CFG, std::is_same<Src, SingleSrc>::value>(base, x0, y0, g, reinterpret_cast<T*>(outv), p, tid);
 }
 
 template <int N1>
@@ -576,7 +587,7 @@ __global__ void __launch_bounds__(FlowCfg<N1, C, CFG>::THREADS, FlowCfg<N1, C, C
         if (code < 0) return;  // no tasks left, or the producer gave up
         const int t = code, k = slot[F::STAGES + st];
         const int x0 = (t % src.tiles_x) * TX, y0 = (t / src.tiles_x) * TY;
-        tile_compute<N1, C, CFG>(base + st * F::STAGE_BYTES, x0, y0, g, reinterpret_cast<T*>(src.buf[(k + 1) & 1]), p,
+        tile_compute<N1, C, CFG, false>(base + st * F::STAGE_BYTES, x0, y0, g, reinterpret_cast<T*>(src.buf[(k + 1) & 1]), p,
                                  tid);
         fence_proxy_async_global();  // this thread's stores, visible to the TMA reads of later tasks
         __syncwarp();
