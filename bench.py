@@ -44,7 +44,7 @@ WORKLOADS = {
                nx=64, ny=64, velset="D2Q16", storage="fp64", plain_storage="fp64", tau=0.8, walls=None, tsteps=200),
     "c2": dict(desc="D2Q36 4096x512 thermal Couette FP16-deviation storage tau=0.9, walls T=1.0/1.1, u_top=0.1, "
                     "1000 time steps", nx=4096, ny=512, velset="D2Q36", storage="fp16_dev", plain_storage="fp16_dev",
-               tau=0.9, walls=(0.0, 1.0, 0.1, 1.1), tsteps=1000, reference="rows"),
+               tau=0.9, walls=(0.0, 1.0, 0.1, 1.1), tsteps=1000, reference="rows", refresh=100),
 }
 
 BATCH = dict(desc="256 independent periodic D2Q16 domains, sides drawn from {128,256,512,768,1024}, tau~U[0.55,1.5], "
@@ -205,6 +205,8 @@ def run_ours(args, w, rank, world, local_rank):
         elif w.get("reference") and (storage or w["storage"]).endswith("_dev"):
             s.set_reference(*w["reference"])
         s.init_moments(*fields)
+        if w.get("refresh") and (storage or w["storage"]).endswith("_dev"):
+            s.set_reference_refresh(w["refresh"])
         return s
 
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
@@ -322,7 +324,8 @@ def run_ours(args, w, rank, world, local_rank):
         "data": "synthetic (seeded fields shaped like the paper's test problems)",
         "config": {"workload": w["desc"], "nx": nx, "ny": ny, "velset": w["velset"], "storage": w["storage"],
                    "tau": w["tau"], "time_steps_per_bench_step": tsteps, "form": chosen,
-                   "deviation_reference": ("per row: u = 0, T linear between the walls (the start)"
+                   "deviation_reference": ("per row: u = 0, T linear between the walls (the start), reset to the "
+                                           "row averages every %d steps inside the timed region" % w.get("refresh", 0)
                                            if w.get("reference") == "rows" else w.get("reference")),
                    "tile": (list(tv.tvlbm_tile_shape(probe.ctx, tuning["best"])) if tuning else
                             (list(tv.tvlbm_tile_shape(probe.ctx, max(args.tile, 0))) if chosen != "plain" else None)),

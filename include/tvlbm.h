@@ -173,11 +173,22 @@ int tvlbm_set_reference(tvlbm_ctx *ctx, double ux, double uy, double T);
  * that follows it (e.g. linear between the wall values) keeps |d| near the non-equilibrium part
  * and the half-precision rounding error with it.  The time step is unchanged in exact
  * arithmetic: the gather of row y adds S_l(y), the gather of R over the source rows minus R_l(y),
- * and the collision takes the row's reference moments.  ux, uy, T: host arrays of ny values
- * (copied).  The current state is re-encoded (synchronises); tvlbm_set_reference returns to a
- * single reference.  Errors: EINVAL (full-f storage, periodic domain, null array, T <= 0 or a
+ * and the collision takes the row's reference moments (tables of a few hundred bytes per row,
+ * built on the device).  ux, uy, T: host arrays of ny values (copied).  The current state is
+ * re-encoded (synchronises); tvlbm_set_reference returns to a single reference.  Errors: EINVAL (full-f storage, periodic domain, null array, T <= 0 or a
  * non-finite value), ENOMEM, ECUDA. */
 int tvlbm_set_reference_rows(tvlbm_ctx *ctx, const double *ux, const double *uy, const double *T);
+
+/* Deviation storage on a domain with walls: keep the per-row reference following the flow.
+ * Every `every` time steps tvlbm_step resets the reference rows to the current row averages of
+ * (ux, uy, T) and re-encodes the state: a row-average pass, two small table kernels and one
+ * re-encoding pass over the state, queued on the context's stream without a host
+ * synchronisation.  With no per-row reference yet, one is taken from the current state at once.
+ * A row whose average is not a valid state (T <= 0, not finite) takes the default reference.
+ * every = 0 turns refreshing off (the reference stays as it is).  Refreshing only changes the
+ * encoding: in exact arithmetic the state is unchanged.  Errors: EINVAL (full-f storage,
+ * periodic domain, every < 0), ENOMEM, ECUDA. */
+int tvlbm_set_reference_refresh(tvlbm_ctx *ctx, int every);
 
 /* Tile configurations of the tiled form (an autotuner picks among them): their number, and
  * the shape of one -- tile width and height in cells and rows each thread walks.

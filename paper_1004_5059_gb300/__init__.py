@@ -78,6 +78,7 @@ def _load_library() -> ctypes.CDLL:
         "tvlbm_set_fv_walls": (_I, [_P, _I, _I, _DP]),
         "tvlbm_set_reference": (_I, [_P, _D, _D, _D]),
         "tvlbm_set_reference_rows": (_I, [_P, _P, _P, _P]),
+        "tvlbm_set_reference_refresh": (_I, [_P, _I]),
         "tvlbm_tile_count": (_I, [_P]),
         "tvlbm_tile_shape": (_I, [_P, _I, _IP, _IP, _IP]),
         "tvlbm_set_tile": (_I, [_P, _I]),
@@ -206,6 +207,10 @@ def tvlbm_set_reference(ctx, ux: float, uy: float, T: float):
 def tvlbm_set_reference_rows(ctx, ny: int, ux, uy, T):
     arrs = [np.ascontiguousarray(np.broadcast_to(np.asarray(a, dtype=np.float64), (ny,))) for a in (ux, uy, T)]
     _check(_lib.tvlbm_set_reference_rows(ctx, *(_dp(a) for a in arrs)), ctx)
+
+
+def tvlbm_set_reference_refresh(ctx, every: int):
+    _check(_lib.tvlbm_set_reference_refresh(ctx, int(every)), ctx)
 
 
 def tvlbm_tile_count(ctx) -> int:
@@ -357,6 +362,10 @@ class Simulation:
     def set_reference_rows(self, ux, uy, T):
         """Per-row deviation reference of a channel: ux, uy, T hold ny values (or scalars)."""
         tvlbm_set_reference_rows(self.ctx, self.ny, ux, uy, T)
+
+    def set_reference_refresh(self, every: int):
+        """Reset the per-row reference to the row averages every `every` steps (0: off)."""
+        tvlbm_set_reference_refresh(self.ctx, every)
 
     def init_moments(self, rho, ux, uy, T):
         tvlbm_init_moments(self.ctx, rho, ux, uy, T)

@@ -247,39 +247,87 @@ int upload_fields_and_init(tvlbm_ctx* c, const double* rho, const double* ux, co
     return TVLBM_OK;
 }
 
-void free_reference_rows(tvlbm_ctx* c) {
-    if (c->ref_rowf) cudaFree(c->ref_rowf);
-    if (c->ref_rowd) cudaFree(c->ref_rowd);
-    delete[] c->ref_rowd_host;
-    c->ref_rowf = nullptr;
-    c->ref_rowd = nullptr;
-    c->ref_rowd_host = nullptr;
+// ---- per-row deviation reference -----------------------------------------------------------
+// Device buffers, allocated on first use: the live tables the kernels read (KParams::rowd /
+// rowf), a second pair the next reference is built in, the re-encoding shifts and the profile.
+bool ensure_reference_buffers(tvlbm_ctx* c) {
+    if (c->ref_mem) return true;
+    const size_t rows = (size_t)c->L.rows;
+    const size_t bd = align_up(rows * kRowD * sizeof(double), 256), bf = align_up(rows * kRowF * sizeof(float), 256);
+    const size_t bdel = align_up(rows * kMaxQ * sizeof(float), 256), bp = align_up(3 * (size_t)c->ny * sizeof(double), 256);
+    unsigned char* m = nullptr;
+    if (cudaMalloc((void**)&m, 2 * bd + 2 * bf + bdel + bp) != cudaSuccess) return false;
+    c->ref_mem = m;
+    c->ref_rowd = (double*)m;
+    c->ref_new_d = (double*)(m + bd);
+    c->ref_rowf = (float*)(m + 2 * bd);
+    c->ref_new_f = (float*)(m + 2 * bd + bf);
+    c->ref_delta = (float*)(m + 2 * bd + 2 * bf);
+    c->ref_prof = (double*)(m + 2 * bd + 2 * bf + bdel);
+    return true;
 }
 
-// Pref_l of stored row r under the context's current reference.
-double current_pref(const tvlbm_ctx* c, int r, int l) {
-    return c->ref_rowd_host ? c->ref_rowd_host[(size_t)r * kRowD + l] : c->kp.Prefd[l];
+// One reference's Pref table: per stored row (rows: [rows][kRowD]) or the same for every row.
+struct RefSide {
+    const double* rows;
+    double c[kMaxQ];
+};
+RefSide ref_side_of(const KParams& p) {
+    RefSide r;
+    r.rows = p.rowd;
+    for (int l = 0; l < kMaxQ; ++l) r.c[l] = p.Prefd[l];
+    return r;
 }
 
-// Re-encode the current state from the context's reference to the one whose Pref is new_pref(r, l)
-// (d += Pref_old - Pref_new on every stored element), synchronously.
-template <class F>
-int reencode_to(tvlbm_ctx* c, F new_pref) {
-    const int rows = c->L.rows;
-    float* h = new (std::nothrow) float[(size_t)rows * kMaxQ];
-    if (!h) return fail(c, TVLBM_ENOMEM, "host table");
-    for (int r = 0; r < rows; ++r)
-        for (int l = 0; l < kMaxQ; ++l)
-            h[(size_t)r * kMaxQ + l] = l < c->Q ? (float)(current_pref(c, r, l) - new_pref(r, l)) : 0.0f;
-    float* d = nullptr;
-    cudaError_t e = cudaMalloc((void**)&d, sizeof(float) * (size_t)rows * kMaxQ);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d, h, sizeof(float) * (size_t)rows * kMaxQ, cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess) e = c->kt->reencode(c->storage, fcur(c), d, c->kp, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    if (d) cudaFree(d);
-    delete[] h;
-    if (e != cudaSuccess) return fail(c, TVLBM_ECUDA, "reencode: %s", cudaGetErrorString(e));
+// delta[r][l] = Pref_old - Pref_new: the shift that re-expresses a stored deviation.
+__global__ void ref_delta_kernel(float* __restrict__ delta, const RefSide from, const RefSide to, int rows, int Q) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= rows * kMaxQ) return;
+    const int r = t / kMaxQ, l = t - r * kMaxQ;
+    const double o = from.rows ? from.rows[(long long)r * kRowD + l] : from.c[l];
+    const double n = to.rows ? to.rows[(long long)r * kRowD + l] : to.c[l];
+    delta[t] = l < Q ? (float)(o - n) : 0.0f;
+}
+
+// Re-express the current state from reference `from` to reference `to` (stream-ordered).
+cudaError_t reencode_between(tvlbm_ctx* c, const RefSide& from, const RefSide& to) {
+    const int n = c->L.rows * kMaxQ;
+    ref_delta_kernel<<<(n + 255) / 256, 256, 0, c->stream>>>(c->ref_delta, from, to, c->L.rows, c->Q);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return c->kt->reencode(c->storage, fcur(c), c->ref_delta, c->kp, c->stream);
+}
+
+// Switch to the per-row reference of the profile in c->ref_prof (device [3][ny]): build its tables
+// in the spare pair, re-encode the state, copy the tables over the live ones (stream-ordered, no
+// host synchronisation; the kernel parameters keep the live pointers, so captured graphs stay
+// valid).  The first switch points the kernel parameters at the live tables.
+int install_reference_rows(tvlbm_ctx* c) {
+    TVLBM_CUDA(c, c->kt->ref_tables(c->ref_prof, c->ref_new_d, c->ref_new_f, c->kp, c->stream), "reference tables");
+    RefSide to;
+    to.rows = c->ref_new_d;
+    for (int l = 0; l < kMaxQ; ++l) to.c[l] = 0.0;
+    TVLBM_CUDA(c, reencode_between(c, ref_side_of(c->kp), to), "re-encoding");
+    const size_t rows = (size_t)c->L.rows;
+    TVLBM_CUDA(c, cudaMemcpyAsync(c->ref_rowd, c->ref_new_d, rows * kRowD * sizeof(double), cudaMemcpyDeviceToDevice,
+                                  c->stream), "row tables");
+    TVLBM_CUDA(c, cudaMemcpyAsync(c->ref_rowf, c->ref_new_f, rows * kRowF * sizeof(float), cudaMemcpyDeviceToDevice,
+                                  c->stream), "row tables");
+    if (c->kp.rowf != c->ref_rowf) {
+        set_reference_params(c->kp, c->rule, c->rho0, 0.0, 0.0, 1.0);
+        c->kp.has_ref = 1;
+        c->kp.rowf = c->ref_rowf;
+        c->kp.rowd = c->ref_rowd;
+        drop_graphs(c);
+    }
     return TVLBM_OK;
+}
+
+// Reset the per-row reference to the current row averages of (u_x, u_y, T) and re-encode.
+int refresh_reference_rows(tvlbm_ctx* c) {
+    if (!ensure_reference_buffers(c)) return fail(c, TVLBM_ENOMEM, "reference tables");
+    TVLBM_CUDA(c, c->kt->row_means(c->storage, fcur(c), c->ref_prof, c->kp, c->stream), "row means kernel");
+    return install_reference_rows(c);
 }
 
 }  // namespace
@@ -320,7 +368,7 @@ int tvlbm_destroy(tvlbm_ctx* c) {
     if (c->fv_omega) cudaFree(c->fv_omega);
     if (c->fv_dy) cudaFree(c->fv_dy);
     if (c->fv_wall_eq) cudaFree(c->fv_wall_eq);
-    free_reference_rows(c);
+    if (c->ref_mem) cudaFree(c->ref_mem);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     if (c->own_mem && c->mem) cudaFree(c->mem);
     delete c;
@@ -362,59 +410,62 @@ int tvlbm_set_reference(tvlbm_ctx* c, double ux, double uy, double T) {
     if (!(T > 0.0) || !isfinite(T) || !isfinite(ux) || !isfinite(uy))
         return fail(c, TVLBM_EINVAL, "reference needs T > 0 and a finite velocity");
     cudaSetDevice(c->device);
+    if (!ensure_reference_buffers(c)) return fail(c, TVLBM_ENOMEM, "re-encoding table");
     KParams np = c->kp;
     set_reference_params(np, c->rule, c->rho0, ux, uy, T);
-    const int rc = reencode_to(c, [&](int, int l) { return np.Prefd[l]; });
-    if (rc) return rc;
-    free_reference_rows(c);
+    TVLBM_CUDA(c, reencode_between(c, ref_side_of(c->kp), ref_side_of(np)), "re-encoding");
+    TVLBM_CUDA(c, cudaStreamSynchronize(c->stream), "reencode synchronize");
     c->kp = np;
+    c->ref_every = 0;
+    c->ref_count = 0;
     drop_graphs(c);
+    return TVLBM_OK;
+}
+
+static int rows_applicable(tvlbm_ctx* c) {
+    if (c->storage == TVLBM_FP64 || c->storage == TVLBM_FP32)
+        return fail(c, TVLBM_EINVAL, "the reference applies to deviation storage only");
+    if (!c->kp.walls) return fail(c, TVLBM_EINVAL, "a per-row reference needs a domain with walls");
     return TVLBM_OK;
 }
 
 int tvlbm_set_reference_rows(tvlbm_ctx* c, const double* ux, const double* uy, const double* T) {
     if (!c) return TVLBM_EINVAL;
-    if (c->storage == TVLBM_FP64 || c->storage == TVLBM_FP32)
-        return fail(c, TVLBM_EINVAL, "the reference applies to deviation storage only");
-    if (!c->kp.walls) return fail(c, TVLBM_EINVAL, "a per-row reference needs a domain with walls");
+    int rc = rows_applicable(c);
+    if (rc) return rc;
     if (!ux || !uy || !T) return fail(c, TVLBM_EINVAL, "null profile");
     for (int y = 0; y < c->ny; ++y)
         if (!(T[y] > 0.0) || !isfinite(T[y]) || !isfinite(ux[y]) || !isfinite(uy[y]))
             return fail(c, TVLBM_EINVAL, "row %d: the reference needs T > 0 and a finite velocity", y);
     cudaSetDevice(c->device);
-    const int rows = c->L.rows;
-    float* hf = new (std::nothrow) float[(size_t)rows * kRowF];
-    double* hd = new (std::nothrow) double[(size_t)rows * kRowD];
-    if (!hf || !hd) {
-        delete[] hf;
-        delete[] hd;
-        return fail(c, TVLBM_ENOMEM, "host tables");
+    if (!ensure_reference_buffers(c)) return fail(c, TVLBM_ENOMEM, "reference tables");
+    const double* src[3] = {ux, uy, T};
+    for (int k = 0; k < 3; ++k)
+        TVLBM_CUDA(c, cudaMemcpyAsync(c->ref_prof + (size_t)k * c->ny, src[k], c->ny * sizeof(double),
+                                      cudaMemcpyHostToDevice, c->stream), "profile upload");
+    rc = install_reference_rows(c);
+    if (rc) return rc;
+    TVLBM_CUDA(c, cudaStreamSynchronize(c->stream), "reference synchronize");
+    return TVLBM_OK;
+}
+
+int tvlbm_set_reference_refresh(tvlbm_ctx* c, int every) {
+    if (!c) return TVLBM_EINVAL;
+    if (every < 0) return fail(c, TVLBM_EINVAL, "negative refresh period");
+    if (every == 0) {
+        c->ref_every = 0;
+        c->ref_count = 0;
+        return TVLBM_OK;
     }
-    reference_rows(c->kp, c->rule, c->rho0, c->ny, rows, ux, uy, T, hf, hd);
-    float* df = nullptr;
-    double* dd = nullptr;
-    cudaError_t e = cudaMalloc((void**)&df, sizeof(float) * (size_t)rows * kRowF);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&dd, sizeof(double) * (size_t)rows * kRowD);
-    if (e == cudaSuccess) e = cudaMemcpy(df, hf, sizeof(float) * (size_t)rows * kRowF, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(dd, hd, sizeof(double) * (size_t)rows * kRowD, cudaMemcpyHostToDevice);
-    int rc = e == cudaSuccess ? TVLBM_OK : fail(c, TVLBM_ECUDA, "row tables: %s", cudaGetErrorString(e));
-    if (!rc) rc = reencode_to(c, [&](int r, int l) { return hd[(size_t)r * kRowD + l]; });
-    delete[] hf;
-    if (rc) {
-        if (df) cudaFree(df);
-        if (dd) cudaFree(dd);
-        delete[] hd;
-        return rc;
+    int rc = rows_applicable(c);
+    if (rc) return rc;
+    cudaSetDevice(c->device);
+    if (!c->kp.rowf) {
+        rc = refresh_reference_rows(c);
+        if (rc) return rc;
     }
-    free_reference_rows(c);
-    c->ref_rowf = df;
-    c->ref_rowd = dd;
-    c->ref_rowd_host = hd;
-    set_reference_params(c->kp, c->rule, c->rho0, 0.0, 0.0, 1.0);
-    c->kp.has_ref = 1;
-    c->kp.rowf = df;
-    c->kp.rowd = dd;
-    drop_graphs(c);
+    c->ref_every = every;
+    c->ref_count = 0;
     return TVLBM_OK;
 }
 
@@ -460,6 +511,8 @@ int tvlbm_init_moments(tvlbm_ctx* c, const double* rho, const double* ux, const 
     return upload_fields_and_init(c, rho, ux, uy, T);
 }
 
+static int run_steps(tvlbm_ctx* c, int n);
+
 int tvlbm_step(tvlbm_ctx* c, int n) {
     if (!c) return TVLBM_EINVAL;
     if (n < 0) return fail(c, TVLBM_EINVAL, "negative step count");
@@ -469,6 +522,25 @@ int tvlbm_step(tvlbm_ctx* c, int n) {
         TVLBM_CUDA(c, launch_flow(c, n, c->stream), "dataflow launch");
         return TVLBM_OK;
     }
+    if (c->ref_every > 0) {  // per-row reference following the flow: refresh between chunks
+        while (n > 0) {
+            const int chunk = n < c->ref_every - c->ref_count ? n : c->ref_every - c->ref_count;
+            const int rc = run_steps(c, chunk);
+            if (rc) return rc;
+            n -= chunk;
+            c->ref_count += chunk;
+            if (c->ref_count >= c->ref_every) {
+                const int rr = refresh_reference_rows(c);
+                if (rr) return rr;
+                c->ref_count = 0;
+            }
+        }
+        return TVLBM_OK;
+    }
+    return run_steps(c, n);
+}
+
+static int run_steps(tvlbm_ctx* c, int n) {
     int left = n;
     if (c->graphs) {
         while (left >= kGraphSteps) {

@@ -31,7 +31,8 @@
 
 namespace tvlbm {
 
-// row: the cell row's entries of a per-row reference table (KParams::rowf), or null.
+// row: the cell row's entries of a per-row reference table (KParams::rowf), or null; s then holds
+// the plain gather of the stored deviations (the row's shift enters through its table).
 template <int N1>
 __device__ __forceinline__ void cell_collide_dev(float (&s)[N1 * N1], const KParams& p, float om,
                                                  const float* row = nullptr) {
@@ -71,15 +72,24 @@ __device__ __forceinline__ void cell_collide_dev(float (&s)[N1 * N1], const KPar
         mx = fmaf(p.wf[H], rx[H], mx);
         me = fmaf(p.wf[H], rxx[H], me);
     }
+    // the row's entries (16-byte aligned): moments of its gather shift, jref, eref and refD
+    // (scalar selects: a pointer into the parameter block would copy it to local memory)
+    const float4 rsm = row ? __ldg(reinterpret_cast<const float4*>(row + kRowSM)) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 rje = row ? __ldg(reinterpret_cast<const float4*>(row + kRowJ))
+                           : make_float4(p.jreff[0], p.jreff[1], p.ereff, p.refD[0]);
+    const float4 rrd = row ? __ldg(reinterpret_cast<const float4*>(row + kRowJ + 4))
+                           : make_float4(p.refD[1], p.refD[2], p.refD[3], 0.f);
+    m0 += rsm.x;
+    mx += rsm.y;
+    my += rsm.z;
+    me += rsm.w;
     const float rho = p.rho0f + m0;
     // correctly rounded reciprocal: the approximate hardware one is off by up to an ulp in a
     // direction that repeats from step to step, and the equilibrium velocity it feeds drifted by
     // 1.4e-5 over 1000 steps of the 1024^2 workload (1.4e-6 with this one)
     const float inv = __frcp_rn(rho);
-    const float jrx = row ? __ldg(row + 2 * kMaxQ) : p.jreff[0], jry = row ? __ldg(row + 2 * kMaxQ + 1) : p.jreff[1];
-    const float eref = row ? __ldg(row + 2 * kMaxQ + 2) : p.ereff;
-    const float ux = (jrx + mx) * inv, uy = (jry + my) * inv;
-    const float th = 0.5f * ((eref + me - 2.0f * m0) * inv - (ux * ux + uy * uy));
+    const float ux = (rje.x + mx) * inv, uy = (rje.y + my) * inv;
+    const float th = 0.5f * ((rje.z + me - 2.0f * m0) * inv - (ux * ux + uy * uy));
 
     // ---- Hermite coefficients of the Maxwellian, per axis ----------------------------------
     float hx[N + 1], hy[N + 1];
@@ -93,9 +103,7 @@ __device__ __forceinline__ void cell_collide_dev(float (&s)[N1 * N1], const KPar
     }
 
     // ---- first-order cancellation of the table defects -------------------------------------
-    // (scalar selects: a pointer into the parameter block would copy it to local memory)
-    const float rD0 = row ? __ldg(row + 2 * kMaxQ + 3) : p.refD[0], rD1 = row ? __ldg(row + 2 * kMaxQ + 4) : p.refD[1];
-    const float rD2 = row ? __ldg(row + 2 * kMaxQ + 5) : p.refD[2], rD3 = row ? __ldg(row + 2 * kMaxQ + 6) : p.refD[3];
+    const float rD0 = rje.w, rD1 = rrd.x, rD2 = rrd.y, rD3 = rrd.z;
     float Dm = fmaf(2.f * p.dS[0], m0, rD0), De = fmaf(2.f * m0, p.dVS[0], rD3);
     float Dx = fmaf(rho * ux, p.dUS, rD1), Dy = fmaf(rho * uy, p.dUS, rD2);
 #pragma unroll
@@ -158,9 +166,15 @@ __device__ __forceinline__ void cell_collide_dev(float (&s)[N1 * N1], const KPar
             s[i + N1 * j] = fmaf(keep, s[i + N1 * j], weq);
         }
     }
-    if (row) {  // the row reference's own deviation: d_eq -= Pref(y)
+    if (row) {  // the row's gather shift kept by the relaxation and its reference's deviation
 #pragma unroll
-        for (int l = 0; l < N1 * N1; ++l) s[l] = fmaf(-om, __ldg(row + l), s[l]);
+        for (int l4 = 0; l4 < (N1 * N1 + 3) / 4; ++l4) {
+            const float4 c = __ldg(reinterpret_cast<const float4*>(row) + l4);
+            const float cv[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (4 * l4 + k < N1 * N1) s[4 * l4 + k] += cv[k];
+        }
     } else if (p.has_ref) {  // the reference's own deviation: d_eq -= Pref
 #pragma unroll
         for (int l = 0; l < N1 * N1; ++l) s[l] = fmaf(-om, p.Preff[l], s[l]);

@@ -33,9 +33,14 @@ struct tvlbm_ctx {
     double* fv_dy;                    // finite-volume channel: node spacings in y [ny - 1] (device; null: 1)
     double* fv_wall_eq;               // finite-volume channel: wall equilibria [2][nx][2] (device)
     int fv_exact, fv_nr_iters;        // finite-volume channel: Newton-Raphson imposition, iterations
-    float* ref_rowf;                  // per-row deviation reference: device tables (null: single reference)
-    double* ref_rowd;
-    double* ref_rowd_host;            // host copy of the FP64 table (re-encoding against the next reference)
+    unsigned char* ref_mem;           // per-row deviation reference: one device allocation holding
+    double* ref_rowd;                 //   the live tables (KParams::rowd / rowf),
+    float* ref_rowf;
+    double* ref_new_d;                //   the pair the next reference is built in,
+    float* ref_new_f;
+    float* ref_delta;                 //   the re-encoding shifts [rows][kMaxQ]
+    double* ref_prof;                 //   and the profile [3][ny] (ux, uy, T)
+    int ref_every, ref_count;         // refresh period in steps (0: off), steps since the last refresh
     cudaGraphExec_t cl_graph[2];      // learned coarse steps: two steps per graph, by start parity
     unsigned long long cl_key_net;    // the network and constants the graphs were captured with
     float cl_key[24];

@@ -141,12 +141,14 @@ void host_equilibrium(const Rule& r, double rho, double ux, double uy, double T,
         hx[k + 1] = ux * hx[k] + k * (T - 1.0) * hx[k - 1];
         hy[k + 1] = uy * hy[k] + k * (T - 1.0) * hy[k - 1];
     }
+    double E[kMaxN1][kMaxN1];  // He_a(x_i) / a!
+    for (int i = 0; i < n; ++i)
+        for (int a = 0; a <= N; ++a) E[i][a] = hermite_over_fact(a, r.x[i]);
     for (int j = 0; j < n; ++j)
         for (int i = 0; i < n; ++i) {
             double s = 0.0;
             for (int a = 0; a <= N; ++a)
-                for (int b = 0; a + b <= N; ++b)
-                    s += hx[a] * hermite_over_fact(a, r.x[i]) * hy[b] * hermite_over_fact(b, r.x[j]);
+                for (int b = 0; a + b <= N; ++b) s += hx[a] * E[i][a] * hy[b] * E[j][b];
             feq[i + n * j] = rho * r.w[i] * r.w[j] * s;
         }
 }
@@ -386,42 +388,6 @@ void set_reference_params(KParams& p, const Rule& r, double rho0, double ux, dou
     memcpy(p.refD, e.refD, sizeof(p.refD));
     p.rowf = nullptr;
     p.rowd = nullptr;
-}
-
-void reference_rows(const KParams& p, const Rule& r, double rho0, int ny, int rows, const double* ux,
-                    const double* uy, const double* T, float* rowf, double* rowd) {
-    const int n = r.n, Q = n * n;
-    memset(rowf, 0, sizeof(float) * (size_t)rows * kRowF);
-    memset(rowd, 0, sizeof(double) * (size_t)rows * kRowD);
-    for (int row = 0; row < rows; ++row) {
-        int y = row - HY;
-        y = y < 0 ? 0 : (y >= ny ? ny - 1 : y);
-        const RefEntry e = reference_entry(p, r, rho0, ux[y], uy[y], T[y]);
-        float* f = rowf + (size_t)row * kRowF;
-        double* d = rowd + (size_t)row * kRowD;
-        for (int l = 0; l < Q; ++l) {
-            f[l] = e.Preff[l];
-            d[l] = e.Prefd[l];
-        }
-        f[2 * kMaxQ + 0] = e.jreff[0];
-        f[2 * kMaxQ + 1] = e.jreff[1];
-        f[2 * kMaxQ + 2] = e.ereff;
-        for (int k = 0; k < 4; ++k) f[2 * kMaxQ + 3 + k] = e.refD[k];
-        d[kMaxQ + 0] = e.jrefd[0];
-        d[kMaxQ + 1] = e.jrefd[1];
-        d[kMaxQ + 2] = e.erefd;
-    }
-    // gather shift of the fluid rows (the sources of row y lie within FILL rows of it)
-    for (int y = 0; y < ny; ++y)
-        for (int j = 0; j < n; ++j)
-            for (int i = 0; i < n; ++i) {
-                const int l = i + n * j;
-                const double a = p.ad[j];
-                const double r0 = rowd[(size_t)(y - p.sh[j] + HY) * kRowD + l];
-                const double r1 = rowd[(size_t)(y - p.sh[j] - 1 + HY) * kRowD + l];
-                const double self = rowd[(size_t)(y + HY) * kRowD + l];
-                rowf[(size_t)(y + HY) * kRowF + kMaxQ + l] = (float)((1.0 - a) * r0 + a * r1 - self);
-            }
 }
 
 }  // namespace host

@@ -66,12 +66,6 @@ RefEntry reference_entry(const KParams& p, const Rule& r, double rho0, double ux
 // clears the per-row tables); (0, 0, 1) is the default reference.
 void set_reference_params(KParams& p, const Rule& r, double rho0, double ux, double uy, double T);
 
-// Per-row reference tables in the layout of KParams::rowf / rowd over `rows` stored rows: fluid
-// row y takes (ux[y], uy[y], T[y]); a ghost row takes the nearest fluid row's.  rowf holds
-// rows * kRowF floats, rowd rows * kRowD doubles.
-void reference_rows(const KParams& p, const Rule& r, double rho0, int ny, int rows, const double* ux,
-                    const double* uy, const double* T, float* rowf, double* rowd);
-
 // TMA descriptor of one population buffer: a 3-D view [Q][rows][pitch], box bx x by x 1.
 bool encode_tensor_map(CUtensorMap* m, void* base, int storage, const Layout& L, int Q, int bx, int by);
 // The driver's cuTensorMapEncodeTiled (null if the driver does not provide it).

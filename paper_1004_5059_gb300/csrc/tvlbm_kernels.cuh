@@ -25,8 +25,12 @@ constexpr int FILL = 4;
 constexpr int kRedBlocks = 1024;  // fixed partial count of the FP64 reduction (deterministic)
 constexpr int kTileConfigs = 4;  // tile shapes of the tiled form
 constexpr int kFlowDone = 16;    // first per-tile counter in the dataflow scratch (64-byte aligned)
-constexpr int kRowF = 2 * kMaxQ + 8;  // floats per stored row of the per-row reference table
-constexpr int kRowD = kMaxQ + 4;      // doubles per stored row of its FP64 table
+// Per-row deviation reference tables (KParams::rowf / rowd): entries per stored row and the
+// offsets of the float table's fields.
+constexpr int kRowD = kMaxQ + 4;   // doubles per row: Pref_l, jref (2), eref
+constexpr int kRowF = kMaxQ + 12;  // floats per row: C_l, S moments (4), jref (2), eref, refD (4)
+constexpr int kRowSM = kMaxQ, kRowJ = kMaxQ + 4, kRowE = kMaxQ + 6, kRowRD = kMaxQ + 7;
+static_assert(kMaxQ % 4 == 0 && kRowF % 4 == 0, "row entries are read as float4");
 
 enum Storage { ST_FP64 = 0, ST_FP32 = 1, ST_BF16_DEV = 2, ST_FP16_DEV = 3, ST_FP32_DEV = 4 };
 enum Form { FORM_PLAIN = 0, FORM_TILED = 1, FORM_FLOW = 2 };
@@ -76,12 +80,15 @@ struct KParams {
     float jreff[2], ereff, refD[4];
     double jrefd[2], erefd;
     // Per-row reference of a domain with walls (null: the single reference above).  Stored row
-    // r = y + HY (ghost rows included) has its own Pref_l, jref, eref and refD, as above but for
-    // R_l(y) = f_eq_l(rho0, u_ref(y), T_ref(y)) / w_l, and the gather shift S_l(y): streaming
-    // moves d_l + R_l(y_source), so the gathered deviation against R_l(y) is the gather of d plus
-    // S_l(y) = (1 - a_j) R_l(y - sh_j) + a_j R_l(y - sh_j - 1) - R_l(y)  (exact: R is constant in x).
-    //   rowf[r * kRowF + l]: Pref_l; [kMaxQ + l]: S_l; [2 kMaxQ + 0..1]: jref; [+2]: eref; [+3..6]: refD
+    // r = y + HY (ghost rows included) has its own reference R_l(y) = f_eq_l(rho0, u_ref(y),
+    // T_ref(y)) / w_l.  Streaming moves d_l + R_l(y_source), so the gathered deviation against
+    // R_l(y) is the gather of d plus the shift S_l(y) = (1 - a_j) R_l(y - sh_j) + a_j R_l(y - sh_j - 1)
+    // - R_l(y) (exact: R is constant in x).  The FP32 collision takes the moments of S and, after
+    // relaxing, adds C_l(y) = (1 - omega) S_l(y) - omega Pref_l(y) (the shift kept by the BGK
+    // update and the row reference's own equilibrium deviation).
     //   rowd[r * kRowD + l]: Pref_l; [kMaxQ + 0..1]: jref; [kMaxQ + 2]: eref
+    //   rowf[r * kRowF + l]: C_l; [kRowSM + 0..3]: FP32-constant moments (m0, mx, my, me) of S;
+    //   [kRowJ + 0..1]: jref; [kRowE]: eref; [kRowRD + 0..3]: refD of the row's float Pref
     const float* rowf;
     const double* rowd;
     // Device status word: bit 0 is set by a kernel whose bounded wait gave up.
@@ -138,7 +145,7 @@ template <class R> __device__ __forceinline__ R kPrefRow(const KParams& p, int l
     if constexpr (std::is_same<R, double>::value)
         return p.rowd ? __ldg(p.rowd + (long long)(y + HY) * kRowD + l) : p.Prefd[l];
     else
-        return p.rowf ? __ldg(p.rowf + (long long)(y + HY) * kRowF + l) : p.Preff[l];
+        return p.rowd ? (R)__ldg(p.rowd + (long long)(y + HY) * kRowD + l) : p.Preff[l];
 }
 template <class R> __device__ __forceinline__ R kjref(const KParams& p, int k) {
     if constexpr (std::is_same<R, double>::value) return p.jrefd[k]; else return p.jreff[k];
@@ -389,6 +396,10 @@ struct KernelTable {
     cudaError_t (*flow_sweep)(int storage, int cfg, const FlowSrc& src, const KParams& p, cudaStream_t s);
     // one time step of every domain of a batch (persistent launch over all tiles)
     cudaError_t (*batch_sweep)(int storage, int cfg, const BatchSrc& src, const KParams& p, cudaStream_t s);
+    // row averages of (ux, uy, T) of buffer f into prof [3][ny] (device)
+    cudaError_t (*row_means)(int storage, const void* f, double* prof, const KParams& p, cudaStream_t s);
+    // per-row reference tables (KParams::rowd / rowf layout, p.rows rows) of the profile prof [3][ny]
+    cudaError_t (*ref_tables)(const double* prof, double* rowd, float* rowf, const KParams& p, cudaStream_t s);
 };
 
 const KernelTable* kernel_table_q3();

@@ -165,69 +165,76 @@ static __global__ void __launch_bounds__(256) reduce_final_kernel(const double* 
 }
 
 // =============================================================================================
-// Diffuse-reflection walls through ghost rows (Eq. IMPOSITION).  One thread per (column, wall).
+// Diffuse-reflection walls through ghost rows (Eq. IMPOSITION).
 // M_out(x): what the gather would move into the rows beyond the wall for the outgoing
 // velocities (c.n > 0, n the wall's outward normal), counting only fluid sources.  Every
 // incoming ghost row of column x then holds A(x) f_eq_l(1, u_w, T_w) with
 // A = M_out / sum_in |c_y dt| f_eq_l, so a uniform ghost column re-emits exactly M_out.
 // Columns of the x-frame are filled too (periodic images).
+// A block covers 32 output columns of one wall with one thread per (column, outgoing velocity):
+// each sums its velocity's share of M_out (unrolled, so its few loads are in flight together),
+// the column's shares are added in a fixed order in shared memory, and the same threads then
+// write the incoming velocities' ghost rows (by mirror symmetry there are as many).
 // =============================================================================================
+template <int N1>
+__host__ __device__ constexpr int wall_lanes() { return (N1 / 2) * N1; }  // outgoing (= incoming) velocities per wall
+
 template <int N1, class C>
-__global__ void wall_kernel(typename C::T* __restrict__ f, const KParams p) {
+__global__ void __launch_bounds__(32 * wall_lanes<N1>()) wall_kernel(typename C::T* __restrict__ f, const KParams p) {
     using R = typename C::R;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int ncol = p.nx + 2 * FILL;
-    if (t >= 2 * ncol) return;
-    const int side = t / ncol;          // 0: wall at y = -1/2, 1: wall at y = ny - 1/2
-    const int xo = t - side * ncol - FILL;  // output column, in [-FILL, nx + FILL)
+    constexpr int H = N1 / 2, NL = wall_lanes<N1>();
+    __shared__ R part[NL][32];
+    __shared__ R amp[32];
+    const int tx = threadIdx.x, k = threadIdx.y;
+    const int side = blockIdx.y;                 // 0: wall at y = -1/2, 1: wall at y = ny - 1/2
+    const int xo = blockIdx.x * 32 + tx - FILL;  // output column, in [-FILL, nx + FILL)
+    const bool col = xo < p.nx + FILL;
     const int x = ((xo % p.nx) + p.nx) % p.nx;
+    const int i = k % N1, jj = k / N1;
     const R rho0 = krho0<R>(p);
-    R mout = 0;
+    {
+        // nodes ascend, so the H lowest y-nodes move towards the wall at y = -1/2
+        const int j = side == 0 ? jj : N1 - 1 - jj;
+        const int l = i + N1 * j;
+        const R ay = ka<R>(p, j), ax = ka<R>(p, i), w = kw<R>(p, i) * kw<R>(p, j);
+        R acc = 0;
+        if (col) {
 #pragma unroll
-    for (int j = 0; j < N1; ++j) {
-        const R cyj = kx<R>(p, j);
-        const bool outgoing = side == 0 ? cyj < R(0) : cyj > R(0);
-        if (!outgoing) continue;
-        const R ay = ka<R>(p, j);
-#pragma unroll
-        for (int i = 0; i < N1; ++i) {
-            const R ax = ka<R>(p, i), w = kw<R>(p, i) * kw<R>(p, j);
-            const int l = i + N1 * j;
             for (int d = 1; d <= HY; ++d) {
                 const int yd = side == 0 ? -d : p.ny - 1 + d;
-                R acc = 0;
 #pragma unroll
                 for (int q = 0; q < 2; ++q) {
                     const int ys = yd - p.sh[j] - q;
                     if (ys < 0 || ys >= p.ny) continue;  // beyond the wall: no mass
                     const R wy = q ? ay : R(1) - ay;
+                    const R ref = rho0 + kPrefRow<R>(p, l, ys);
 #pragma unroll
                     for (int pp = 0; pp < 2; ++pp) {
                         const int xs = x - p.sh[i] - pp;
                         const R wx = pp ? ax : R(1) - ax;
-                        acc += wx * wy * to_f<C, R>(C::ld(f + sidx(p, l, xs, ys)), w, rho0 + kPrefRow<R>(p, l, ys));
+                        acc += wx * wy * to_f<C, R>(C::ld(f + sidx(p, l, xs, ys)), w, ref);
                     }
                 }
-                mout += acc;
             }
         }
+        part[k][tx] = acc;
     }
-    const R A = mout * kinvden<R>(p, side);
+    __syncthreads();
+    if (k == 0) {
+        R m = 0;
+        for (int kk = 0; kk < NL; ++kk) m += part[kk][tx];
+        amp[tx] = m * kinvden<R>(p, side);
+    }
+    __syncthreads();
+    if (!col) return;
+    const int j = side == 0 ? N1 - 1 - jj : jj;  // the incoming velocity of this lane
+    const int l = i + N1 * j;
+    const R w = kw<R>(p, i) * kw<R>(p, j);
+    const R fw = amp[tx] * kfeqw<R>(p, side, l);
 #pragma unroll
-    for (int j = 0; j < N1; ++j) {
-        const R cyj = kx<R>(p, j);
-        const bool incoming = side == 0 ? cyj > R(0) : cyj < R(0);
-        if (!incoming) continue;
-#pragma unroll
-        for (int i = 0; i < N1; ++i) {
-            const int l = i + N1 * j;
-            const R w = kw<R>(p, i) * kw<R>(p, j);
-            const R fw = A * kfeqw<R>(p, side, l);
-            for (int d = 1; d <= HY; ++d) {
-                const int yd = side == 0 ? -d : p.ny - 1 + d;
-                f[sidx(p, l, xo, yd)] = C::enc(from_f<C, R>(fw, w, rho0 + kPrefRow<R>(p, l, yd)));
-            }
-        }
+    for (int d = 1; d <= HY; ++d) {
+        const int yd = side == 0 ? -d : p.ny - 1 + d;
+        f[sidx(p, l, xo, yd)] = C::enc(from_f<C, R>(fw, w, rho0 + kPrefRow<R>(p, l, yd)));
     }
 }
 
@@ -251,15 +258,15 @@ __global__ void halo_kernel(T* __restrict__ f, const KParams p, int Q) {
 }
 
 // d_l += delta[r][l] on every stored element (fluid and frame, stored row r) of a
-// deviation-coded buffer.
+// deviation-coded buffer: grid (pitch / 256, <= 65535 row blocks striding over the rows, Q).
 template <class C>
-__global__ void reencode_kernel(typename C::T* __restrict__ f, long long plane, int pitch, int Q,
-                                const float* __restrict__ delta) {
-    const long long n = plane * Q;
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-        const int l = (int)(t / plane);
-        const int r = (int)((t - (long long)l * plane) / pitch);
-        f[t] = C::enc(C::ld(f + t) + __ldg(delta + (long long)r * kMaxQ + l));
+__global__ void __launch_bounds__(256) reencode_kernel(typename C::T* __restrict__ f, long long plane, int pitch,
+                                                       int rows, const float* __restrict__ delta) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, l = blockIdx.z;
+    if (x >= pitch) return;
+    for (int r = blockIdx.y; r < rows; r += gridDim.y) {
+        typename C::T* q = f + (long long)l * plane + (long long)r * pitch + x;
+        *q = C::enc(C::ld(q) + __ldg(delta + (long long)r * kMaxQ + l));
     }
 }
 
@@ -280,6 +287,130 @@ __global__ void encode_plane_kernel(typename C::T* __restrict__ f, int l, int n1
     const double w = p.wd[l % n1] * p.wd[l / n1];
     f[sidx(p, l, x, y)] =
         C::enc((typename C::R)from_f<C, double>(in[(long long)y * p.nx + x], w, p.rho0d + kPrefRow<double>(p, l, y)));
+}
+
+// =============================================================================================
+// Per-row deviation reference of a channel.
+// =============================================================================================
+// Row averages of (u_x, u_y, T) of the stored state, prof = [ux | uy | T][ny]: one block of 256
+// threads per fluid row, cell moments in the storage's arithmetic (any profile is an exact
+// encoding, so the reference needs no more), sums in FP64 in a fixed order.
+template <int N1, class C>
+__global__ void __launch_bounds__(256) row_means_kernel(const typename C::T* __restrict__ f, double* __restrict__ prof,
+                                                        const KParams p) {
+    constexpr int Q = N1 * N1;
+    using R = typename C::R;
+    __shared__ double sh[3][256];
+    const int y = blockIdx.x, t = threadIdx.x;
+    R ref3v[3];
+    const R* ref3 = nullptr;
+    if (p.rowd) {
+        for (int k = 0; k < 3; ++k) ref3v[k] = (R)__ldg(p.rowd + (long long)(y + HY) * kRowD + kMaxQ + k);
+        ref3 = ref3v;
+    }
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int x = t; x < p.nx; x += blockDim.x) {
+        R v[Q];
+#pragma unroll
+        for (int l = 0; l < Q; ++l) v[l] = C::ld(f + sidx(p, l, x, y));
+        R rho, ux, uy, th;
+        cell_moments<N1, C::dev, R>(v, p, rho, ux, uy, th, ref3);
+        acc[0] += (double)ux;
+        acc[1] += (double)uy;
+        acc[2] += 1.0 + (double)th;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) sh[k][t] = acc[k];
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (t < h)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) sh[k][t] += sh[k][t + h];
+        __syncthreads();
+    }
+    if (t < 3) prof[(long long)t * p.ny + y] = sh[t][0] / p.nx;
+}
+
+// Reference entries of every stored row r (fluid row y = r - HY clamped into the fluid; a row
+// whose profile is not a valid state takes the default reference): Pref_l = f_eq_l(rho0, u, T) /
+// w_l - rho0, jref, eref in FP64; jref, eref and refD (the float Pref's share of the FP32 constants'
+// defects, as for the single reference) in the float table.  One thread per row.
+template <int N1>
+__global__ void ref_rows_kernel(const double* __restrict__ prof, double* __restrict__ rowd, float* __restrict__ rowf,
+                                const KParams p) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= p.rows) return;
+    const int y = min(max(r - HY, 0), p.ny - 1);
+    double ux = prof[y], uy = prof[p.ny + y], T = prof[2 * p.ny + y];
+    if (!(T > 0.0) || !isfinite(T) || !isfinite(ux) || !isfinite(uy)) {
+        ux = 0.0;
+        uy = 0.0;
+        T = 1.0;
+    }
+    double eq[N1 * N1];
+    cell_equilibrium<N1, false, double>(p, p.rho0d, ux, uy, T - 1.0, eq);
+    double* d = rowd + (long long)r * kRowD;
+    float* fr = rowf + (long long)r * kRowF;
+    double m = 0.0, mx = 0.0, my = 0.0, me = 0.0;
+    for (int j = 0; j < N1; ++j)
+        for (int i = 0; i < N1; ++i) {
+            const int l = i + N1 * j;
+            const double pr = eq[l] / (p.wd[i] * p.wd[j]) - p.rho0d;
+            d[l] = pr;
+            const double v = (double)(float)pr;
+            m += (double)p.wf[i] * p.wf[j] * v;
+            mx += (double)p.wxf[i] * p.wf[j] * v;
+            my += (double)p.wf[i] * p.wxf[j] * v;
+            me += ((double)p.wx2f[i] * p.wf[j] + (double)p.wf[i] * p.wx2f[j]) * v;
+        }
+    d[kMaxQ] = p.rho0d * ux;
+    d[kMaxQ + 1] = p.rho0d * uy;
+    d[kMaxQ + 2] = p.rho0d * (2.0 * (T - 1.0) + ux * ux + uy * uy);
+    fr[kRowJ] = (float)d[kMaxQ];
+    fr[kRowJ + 1] = (float)d[kMaxQ + 1];
+    fr[kRowE] = (float)d[kMaxQ + 2];
+    fr[kRowRD] = (float)(-m);
+    fr[kRowRD + 1] = (float)(-(mx - (double)fr[kRowJ]));
+    fr[kRowRD + 2] = (float)(-(my - (double)fr[kRowJ + 1]));
+    fr[kRowRD + 3] = (float)(-(me - (double)fr[kRowE]));
+}
+
+// Gather shift of every fluid row from the FP64 Pref table (the sources of row y lie within FILL
+// rows of it): C_l = (1 - omega) S_l - omega Pref_l and the FP32-constant moments of float(S).
+// Ghost rows collide nowhere and get zeros.  One thread per stored row.
+template <int N1>
+__global__ void ref_shift_kernel(const double* __restrict__ rowd, float* __restrict__ rowf, const KParams p) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= p.rows) return;
+    const int y = r - HY;
+    float* fr = rowf + (long long)r * kRowF;
+    if (y < 0 || y >= p.ny) {
+        for (int l = 0; l < kMaxQ; ++l) fr[l] = 0.0f;
+        for (int k = 0; k < 4; ++k) fr[kRowSM + k] = 0.0f;
+        return;
+    }
+    const double om = (double)p.omegaf;
+    double m = 0.0, mx = 0.0, my = 0.0, me = 0.0;
+    for (int j = 0; j < N1; ++j)
+        for (int i = 0; i < N1; ++i) {
+            const int l = i + N1 * j;
+            const double a = p.ad[j];
+            const double r0 = rowd[(long long)(y - p.sh[j] + HY) * kRowD + l];
+            const double r1 = rowd[(long long)(y - p.sh[j] - 1 + HY) * kRowD + l];
+            const double self = rowd[(long long)r * kRowD + l];
+            const double S = (1.0 - a) * r0 + a * r1 - self;
+            fr[l] = (float)((1.0 - om) * S - om * self);
+            const double v = (double)(float)S;
+            m += (double)p.wf[i] * p.wf[j] * v;
+            mx += (double)p.wxf[i] * p.wf[j] * v;
+            my += (double)p.wf[i] * p.wxf[j] * v;
+            me += ((double)p.wx2f[i] * p.wf[j] + (double)p.wf[i] * p.wx2f[j]) * v;
+        }
+    for (int l = N1 * N1; l < kMaxQ; ++l) fr[l] = 0.0f;
+    fr[kRowSM] = (float)m;
+    fr[kRowSM + 1] = (float)mx;
+    fr[kRowSM + 2] = (float)my;
+    fr[kRowSM + 3] = (float)me;
 }
 
 // =============================================================================================
@@ -317,8 +448,8 @@ struct Launch {
     }
     template <class C>
     static cudaError_t wall_c(void* f, const KParams& p, cudaStream_t s) {
-        const int n = 2 * (p.nx + 2 * FILL);
-        wall_kernel<N1, C><<<(n + 127) / 128, 128, 0, s>>>((typename C::T*)f, p);
+        const dim3 grid((p.nx + 2 * FILL + 31) / 32, 2), block(32, wall_lanes<N1>());
+        wall_kernel<N1, C><<<grid, block, 0, s>>>((typename C::T*)f, p);
         return cudaGetLastError();
     }
     template <class C>
@@ -329,7 +460,8 @@ struct Launch {
     template <class C>
     static cudaError_t reencode_c(void* f, const float* delta, const KParams& p, cudaStream_t s) {
         if constexpr (!C::dev) return cudaErrorInvalidValue;
-        reencode_kernel<C><<<1024, 256, 0, s>>>((typename C::T*)f, p.plane, p.pitch, N1 * N1, delta);
+        const dim3 grid((p.pitch + 255) / 256, p.rows < 65535 ? p.rows : 65535, N1 * N1);
+        reencode_kernel<C><<<grid, 256, 0, s>>>((typename C::T*)f, p.plane, p.pitch, p.rows, delta);
         return cudaGetLastError();
     }
     template <class C>
@@ -396,6 +528,20 @@ struct Launch {
     static cudaError_t reencode(int storage, void* f, const float* delta, const KParams& p, cudaStream_t s) {
         TVLBM_DISPATCH(reencode_c, (f, delta, p, s))
     }
+    template <class C>
+    static cudaError_t row_means_c(const void* f, double* prof, const KParams& p, cudaStream_t s) {
+        row_means_kernel<N1, C><<<p.ny, 256, 0, s>>>((const typename C::T*)f, prof, p);
+        return cudaGetLastError();
+    }
+    static cudaError_t row_means(int storage, const void* f, double* prof, const KParams& p, cudaStream_t s) {
+        TVLBM_DISPATCH(row_means_c, (f, prof, p, s))
+    }
+    static cudaError_t ref_tables(const double* prof, double* rowd, float* rowf, const KParams& p, cudaStream_t s) {
+        const int blocks = (p.rows + 127) / 128;
+        ref_rows_kernel<N1><<<blocks, 128, 0, s>>>(prof, rowd, rowf, p);
+        ref_shift_kernel<N1><<<blocks, 128, 0, s>>>(rowd, rowf, p);
+        return cudaGetLastError();
+    }
     static cudaError_t flow(int storage, int cfg, const FlowSrc& src, const KParams& p, cudaStream_t s) {
         switch (storage) {
             case ST_FP64: return flow_sweep<N1, CodecF64>(cfg, src, p, s);
@@ -420,7 +566,7 @@ struct Launch {
 
     static const KernelTable* table() {
         static const KernelTable t = {&sweep, &init, &moments, &reduce, &wall, &halo, &decode, &encode, &tiled_available,
-                                      &box, &shape, &reencode, &flow, &batch};
+                                      &box, &shape, &reencode, &flow, &batch, &row_means, &ref_tables};
         return &t;
     }
 };

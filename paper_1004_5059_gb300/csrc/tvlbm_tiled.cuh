@@ -132,17 +132,12 @@ __device__ __forceinline__ void store_images_of(T* f, const Geom& g, long long l
 }
 
 // Collision of one gathered cell (fluid row y) in the codec's arithmetic, relaxation rate of the
-// domain.  With a per-row deviation reference the gathered deviations first take the row's
-// gather shift S_l(y), then collide against the row's reference (ROWS = false: the launch never
-// has one, e.g. a periodic-only form).
+// domain; with a per-row deviation reference, against the row's reference (ROWS = false: the
+// launch never has one, e.g. a periodic-only form).
 template <int N1, class C, bool ROWS = true>
 __device__ __forceinline__ void collide_cell(typename C::R (&s)[N1 * N1], const KParams& p, const Geom& g, int y) {
     if constexpr (C::dev) {
         const float* row = ROWS && p.rowf ? p.rowf + (long long)(y + HY) * kRowF : nullptr;
-        if (row) {
-#pragma unroll
-            for (int l = 0; l < N1 * N1; ++l) s[l] += __ldg(row + kMaxQ + l);
-        }
         cell_collide_dev<N1>(s, p, g.omegaf, row);
     }
     else if constexpr (std::is_same<typename C::R, double>::value) cell_collide<N1, false, double>(s, p, g.omegad);
@@ -274,7 +269,9 @@ __device__ __forceinline__ void tile_compute(const unsigned char* base, int x0, 
 // barrier.  Each thread walks R rows of one column (x-lerp of the previous row carried in
 // registers), collides and stores straight to global memory.  Every wait is bounded; a timeout
 // sets the status word and the CTA returns after a bounded drain of its own loads.
-template <int N1, class C, int CFG, class Src>
+// ROWS: the launch has a per-row deviation reference (a separate instantiation, so the common
+// launch without one compiles exactly like the dataflow kernel's tile computation).
+template <int N1, class C, int CFG, class Src, bool ROWS>
 __global__ void __launch_bounds__(TileCfg<N1, C, CFG>::THREADS)
     sweep_tiled_kernel(const __grid_constant__ Src src, const KParams p) {
     using Cfg = TileCfg<N1, C, CFG>;
@@ -329,8 +326,7 @@ __global__ void __launch_bounds__(TileCfg<N1, C, CFG>::THREADS)
         return;
     }
 
-    // only a single domain can have walls, and with them a per-row reference
-    tile_compute<N1, C, CFG, std::is_same<Src, SingleSrc>::value>(base, x0, y0, g, reinterpret_cast<T*>(outv), p, tid);
+    tile_compute<N1, C, CFG, ROWS>(base, x0, y0, g, reinterpret_cast<T*>(outv), p, tid);
 }
 
 template <int N1>
@@ -346,7 +342,7 @@ inline void tiled_box(int cfg, int* bx, int* by) {
     *by = t.ty + 1;
 }
 
-template <int N1, class C, int CFG, class Src>
+template <int N1, class C, int CFG, class Src, bool ROWS>
 inline cudaError_t tiled_prepare() {
     using Cfg = TileCfg<N1, C, CFG>;
     static bool attr_set[64] = {};  // per device
@@ -354,7 +350,7 @@ inline cudaError_t tiled_prepare() {
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!attr_set[dev]) {
-        const cudaError_t e = cudaFuncSetAttribute(sweep_tiled_kernel<N1, C, CFG, Src>,
+        const cudaError_t e = cudaFuncSetAttribute(sweep_tiled_kernel<N1, C, CFG, Src, ROWS>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
         if (e != cudaSuccess) return e;
         attr_set[dev] = true;
@@ -362,18 +358,27 @@ inline cudaError_t tiled_prepare() {
     return cudaSuccess;
 }
 
-template <int N1, class C, int CFG>
-inline cudaError_t tiled_launch(const SweepMaps* maps, typename C::T* fout, const KParams& p, cudaStream_t s) {
+template <int N1, class C, int CFG, bool ROWS>
+inline cudaError_t tiled_launch_rows(const SweepMaps* maps, typename C::T* fout, const KParams& p, cudaStream_t s) {
     using Cfg = TileCfg<N1, C, CFG>;
-    const cudaError_t e = tiled_prepare<N1, C, CFG, SingleSrc>();
+    const cudaError_t e = tiled_prepare<N1, C, CFG, SingleSrc, ROWS>();
     if (e != cudaSuccess) return e;
     SingleSrc src;
     src.map_in = *(const CUtensorMap*)maps->in;
     src.fout = fout;
     src.tiles_x = (p.nx + Cfg::TX - 1) / Cfg::TX;
     src.ntiles = src.tiles_x * ((p.ny + Cfg::TY - 1) / Cfg::TY);
-    return launch_pdl(sweep_tiled_kernel<N1, C, CFG, SingleSrc>, dim3(src.ntiles), dim3(Cfg::THREADS), Cfg::SMEM, s,
-                      src, p);
+    return launch_pdl(sweep_tiled_kernel<N1, C, CFG, SingleSrc, ROWS>, dim3(src.ntiles), dim3(Cfg::THREADS), Cfg::SMEM,
+                      s, src, p);
+}
+
+// Only deviation codecs have a per-row reference.
+template <int N1, class C, int CFG>
+inline cudaError_t tiled_launch(const SweepMaps* maps, typename C::T* fout, const KParams& p, cudaStream_t s) {
+    if constexpr (C::dev) {
+        if (p.rowf) return tiled_launch_rows<N1, C, CFG, true>(maps, fout, p, s);
+    }
+    return tiled_launch_rows<N1, C, CFG, false>(maps, fout, p, s);
 }
 
 template <int N1, class C>
@@ -390,9 +395,9 @@ inline cudaError_t tiled_sweep(int cfg, const SweepMaps* maps, typename C::T* fo
 template <int N1, class C, int CFG>
 inline cudaError_t batch_launch(const BatchSrc& src, const KParams& p, cudaStream_t s) {
     using Cfg = TileCfg<N1, C, CFG>;
-    const cudaError_t e = tiled_prepare<N1, C, CFG, BatchSrc>();
+    const cudaError_t e = tiled_prepare<N1, C, CFG, BatchSrc, false>();
     if (e != cudaSuccess) return e;
-    return launch_pdl(sweep_tiled_kernel<N1, C, CFG, BatchSrc>, dim3(src.ntiles), dim3(Cfg::THREADS), Cfg::SMEM, s,
+    return launch_pdl(sweep_tiled_kernel<N1, C, CFG, BatchSrc, false>, dim3(src.ntiles), dim3(Cfg::THREADS), Cfg::SMEM, s,
                       src, p);
 }
 
