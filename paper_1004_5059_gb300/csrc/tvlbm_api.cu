@@ -85,12 +85,13 @@ bool flow_tiles(const tvlbm_ctx* c, int cfg, int* tiles_x, int* tiles_y) {
     return true;
 }
 
-// n time steps in dataflow launches (tasks per launch kept below 2^30).
+// n time steps in dataflow launches (tasks per launch below 2^30, steps per launch at most 2^24,
+// so the per-tile counters, warps per task x steps, stay far inside an int).
 cudaError_t launch_flow(tvlbm_ctx* c, int n, cudaStream_t s) {
     int tiles_x = 0, tiles_y = 0;
     if (!flow_tiles(c, c->tile_cfg, &tiles_x, &tiles_y)) return cudaErrorInvalidValue;
     const int ntiles = tiles_x * tiles_y;
-    const int chunk_max = (1 << 30) / ntiles;
+    const int chunk_max = (1 << 30) / ntiles < (1 << 24) ? (1 << 30) / ntiles : (1 << 24);
     int* ctr = (int*)dptr(c, c->L.off_flow);
     while (n > 0) {
         const int chunk = n < chunk_max ? n : chunk_max;
@@ -284,8 +285,8 @@ __global__ void ref_delta_kernel(float* __restrict__ delta, const RefSide from, 
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= rows * kMaxQ) return;
     const int r = t / kMaxQ, l = t - r * kMaxQ;
-    const double o = from.rows ? from.rows[(long long)r * kRowD + l] : from.c[l];
-    const double n = to.rows ? to.rows[(long long)r * kRowD + l] : to.c[l];
+    const double o = from.rows ? ld_row(from.rows + (long long)r * kRowD + l) : from.c[l];
+    const double n = to.rows ? ld_row(to.rows + (long long)r * kRowD + l) : to.c[l];
     delta[t] = l < Q ? (float)(o - n) : 0.0f;
 }
 

@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(256) closure_collide_kernel(typename C::T* __r
     R s[Q];
 #pragma unroll
     for (int l = 0; l < Q; ++l) s[l] = C::ld(f + cell_index(p, l, x, y));
-    if constexpr (C::dev) cell_collide_dev<N1>(s, p, 1.0f);
+    if constexpr (C::dev) cell_collide_dev<N1, false>(s, p, 1.0f, nullptr);
     else cell_collide<N1, false, R>(s, p, R(1));
     // the correction in the storage's arithmetic: a rounded basis table leaves a conserved-moment
     // residue of the order of its rounding, so FP64 storage uses the FP64 table

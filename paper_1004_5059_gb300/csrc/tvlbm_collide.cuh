@@ -31,11 +31,11 @@
 
 namespace tvlbm {
 
-// row: the cell row's entries of a per-row reference table (KParams::rowf), or null; s then holds
-// the plain gather of the stored deviations (the row's shift enters through its table).
-template <int N1>
-__device__ __forceinline__ void cell_collide_dev(float (&s)[N1 * N1], const KParams& p, float om,
-                                                 const float* row = nullptr) {
+// ROW: row points at the cell row's entries of a per-row reference table (KParams::rowf); s then
+// holds the plain gather of the stored deviations (the row's shift enters through its table).
+// Without ROW, row is unused.
+template <int N1, bool ROW>
+__device__ __forceinline__ void cell_collide_dev(float (&s)[N1 * N1], const KParams& p, float om, const float* row) {
     constexpr int N = N1 - 1, H = N1 / 2;
     constexpr bool ODD = (N1 & 1) != 0;
     // ---- moments: rho = rho0 + sum w d, rho u = sum w c d, sum w |c|^2 d --------------------
@@ -74,11 +74,16 @@ __device__ __forceinline__ void cell_collide_dev(float (&s)[N1 * N1], const KPar
     }
     // the row's entries (16-byte aligned): moments of its gather shift, jref, eref and refD
     // (scalar selects: a pointer into the parameter block would copy it to local memory)
-    const float4 rsm = row ? __ldg(reinterpret_cast<const float4*>(row + kRowSM)) : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 rje = row ? __ldg(reinterpret_cast<const float4*>(row + kRowJ))
-                           : make_float4(p.jreff[0], p.jreff[1], p.ereff, p.refD[0]);
-    const float4 rrd = row ? __ldg(reinterpret_cast<const float4*>(row + kRowJ + 4))
-                           : make_float4(p.refD[1], p.refD[2], p.refD[3], 0.f);
+    float4 rsm, rje, rrd;
+    if constexpr (ROW) {
+        rsm = ld_row4(row + kRowSM);
+        rje = ld_row4(row + kRowJ);
+        rrd = ld_row4(row + kRowJ + 4);
+    } else {
+        rsm = make_float4(0.f, 0.f, 0.f, 0.f);
+        rje = make_float4(p.jreff[0], p.jreff[1], p.ereff, p.refD[0]);
+        rrd = make_float4(p.refD[1], p.refD[2], p.refD[3], 0.f);
+    }
     m0 += rsm.x;
     mx += rsm.y;
     my += rsm.z;
@@ -166,10 +171,10 @@ __device__ __forceinline__ void cell_collide_dev(float (&s)[N1 * N1], const KPar
             s[i + N1 * j] = fmaf(keep, s[i + N1 * j], weq);
         }
     }
-    if (row) {  // the row's gather shift kept by the relaxation and its reference's deviation
+    if constexpr (ROW) {  // the row's gather shift kept by the relaxation and its reference's deviation
 #pragma unroll
         for (int l4 = 0; l4 < (N1 * N1 + 3) / 4; ++l4) {
-            const float4 c = __ldg(reinterpret_cast<const float4*>(row) + l4);
+            const float4 c = ld_row4(row + 4 * l4);
             const float cv[4] = {c.x, c.y, c.z, c.w};
 #pragma unroll
             for (int k = 0; k < 4; ++k)

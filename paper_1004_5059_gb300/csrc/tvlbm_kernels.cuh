@@ -140,12 +140,29 @@ template <class R> __device__ __forceinline__ R krho0(const KParams& p) {
 template <class R> __device__ __forceinline__ R kPref(const KParams& p, int l) {
     if constexpr (std::is_same<R, double>::value) return p.Prefd[l]; else return p.Preff[l];
 }
+// Loads from a per-row reference table that is only read when it exists: the load sits in its
+// branch as volatile inline PTX, so it is never issued ahead of the test (a table pointer may be
+// null on the same code path).
+__device__ __forceinline__ double ld_row(const double* q) {
+    double v;
+    asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(q));
+    return v;
+}
+__device__ __forceinline__ float ld_row(const float* q) {
+    float v;
+    asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(q));
+    return v;
+}
+__device__ __forceinline__ float4 ld_row4(const float* q) {  // q 16-byte aligned
+    float4 v;
+    asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(q));
+    return v;
+}
+
 // Pref_l of fluid row y (y may be a ghost row), per-row table or the single reference.
 template <class R> __device__ __forceinline__ R kPrefRow(const KParams& p, int l, int y) {
-    if constexpr (std::is_same<R, double>::value)
-        return p.rowd ? __ldg(p.rowd + (long long)(y + HY) * kRowD + l) : p.Prefd[l];
-    else
-        return p.rowd ? (R)__ldg(p.rowd + (long long)(y + HY) * kRowD + l) : p.Preff[l];
+    if (p.rowd) return (R)ld_row(p.rowd + (long long)(y + HY) * kRowD + l);
+    if constexpr (std::is_same<R, double>::value) return p.Prefd[l]; else return p.Preff[l];
 }
 template <class R> __device__ __forceinline__ R kjref(const KParams& p, int k) {
     if constexpr (std::is_same<R, double>::value) return p.jrefd[k]; else return p.jreff[k];
@@ -366,7 +383,7 @@ struct FlowSrc {
     CUtensorMap map[2];  // input descriptors: [0] the buffer holding the state at launch, [1] the other
     void* buf[2];        // the same two buffers
     int tiles_x, tiles_y, ntiles, nsteps;
-    int* done;       // [ntiles] steps completed in this launch (zeroed before it)
+    int* done;       // [ntiles] compute-warp completions in this launch (zeroed before it)
     int* next_task;  // task counter (zeroed before the launch)
     int* abort;      // raised by a CTA whose bounded wait gave up (zeroed before the launch)
 };

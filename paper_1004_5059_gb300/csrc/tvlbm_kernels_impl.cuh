@@ -15,7 +15,8 @@ namespace tvlbm {
 // (the area of the shifted source square inside the destination square).  Periodic images
 // and wall ghost rows live in the stored frame, so no index wraps here.
 // =============================================================================================
-template <int N1, class C>
+// ROWS: the launch has a per-row deviation reference (chosen at launch, as for the tiled form).
+template <int N1, class C, bool ROWS>
 __global__ void __launch_bounds__(256) sweep_plain_kernel(const typename C::T* __restrict__ fin,
                                                           typename C::T* __restrict__ fout, const KParams p) {
     using R = typename C::R;
@@ -44,7 +45,7 @@ __global__ void __launch_bounds__(256) sweep_plain_kernel(const typename C::T* _
         }
     }
     const Geom g = geom_of(p);
-    collide_cell<N1, C>(s, p, g, y);
+    collide_cell<N1, C, ROWS>(s, p, g, y);
     store_collided<N1, C>(fout, g, x, y, s);
 }
 
@@ -61,7 +62,14 @@ __global__ void init_kernel(const double* __restrict__ fields, typename C::T* __
     const long long c = (long long)y * p.nx + x, n = (long long)p.nx * p.ny;
     const double rho = fields[c], ux = fields[n + c], uy = fields[2 * n + c], T = fields[3 * n + c];
     double eq[Q];
-    cell_equilibrium<N1, C::dev, double>(p, rho, ux, uy, T - 1.0, eq, p.rowd ? p.rowd + (long long)(y + HY) * kRowD : nullptr);
+    if (p.rowd) {
+        double pref[Q];
+#pragma unroll
+        for (int l = 0; l < Q; ++l) pref[l] = ld_row(p.rowd + (long long)(y + HY) * kRowD + l);
+        cell_equilibrium<N1, C::dev, double>(p, rho, ux, uy, T - 1.0, eq, pref);
+    } else {
+        cell_equilibrium<N1, C::dev, double>(p, rho, ux, uy, T - 1.0, eq);
+    }
 #pragma unroll
     const Geom g = geom_of(p);
 #pragma unroll
@@ -81,8 +89,14 @@ __global__ void moments_kernel(const typename C::T* __restrict__ f, double* __re
 #pragma unroll
     for (int l = 0; l < Q; ++l) s[l] = (double)C::ld(f + sidx(p, l, x, y));
     double rho, ux, uy, th;
-    cell_moments<N1, C::dev, double>(s, p, rho, ux, uy, th,
-                                      p.rowd ? p.rowd + (long long)(y + HY) * kRowD + kMaxQ : nullptr);
+    if (p.rowd) {
+        double ref3[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) ref3[k] = ld_row(p.rowd + (long long)(y + HY) * kRowD + kMaxQ + k);
+        cell_moments<N1, C::dev, double>(s, p, rho, ux, uy, th, ref3);
+    } else {
+        cell_moments<N1, C::dev, double>(s, p, rho, ux, uy, th);
+    }
     const long long c = (long long)y * p.nx + x, n = (long long)p.nx * p.ny;
     out4[c] = rho;
     out4[n + c] = ux;
@@ -302,19 +316,18 @@ __global__ void __launch_bounds__(256) row_means_kernel(const typename C::T* __r
     using R = typename C::R;
     __shared__ double sh[3][256];
     const int y = blockIdx.x, t = threadIdx.x;
-    R ref3v[3];
-    const R* ref3 = nullptr;
-    if (p.rowd) {
-        for (int k = 0; k < 3; ++k) ref3v[k] = (R)__ldg(p.rowd + (long long)(y + HY) * kRowD + kMaxQ + k);
-        ref3 = ref3v;
-    }
+    const bool rows = p.rowd != nullptr;
+    R ref3[3] = {R(0), R(0), R(0)};
+    if (rows)
+        for (int k = 0; k < 3; ++k) ref3[k] = (R)ld_row(p.rowd + (long long)(y + HY) * kRowD + kMaxQ + k);
     double acc[3] = {0.0, 0.0, 0.0};
     for (int x = t; x < p.nx; x += blockDim.x) {
         R v[Q];
 #pragma unroll
         for (int l = 0; l < Q; ++l) v[l] = C::ld(f + sidx(p, l, x, y));
         R rho, ux, uy, th;
-        cell_moments<N1, C::dev, R>(v, p, rho, ux, uy, th, ref3);
+        if (rows) cell_moments<N1, C::dev, R>(v, p, rho, ux, uy, th, ref3);
+        else cell_moments<N1, C::dev, R>(v, p, rho, ux, uy, th);
         acc[0] += (double)ux;
         acc[1] += (double)uy;
         acc[2] += 1.0 + (double)th;
@@ -426,7 +439,10 @@ struct Launch {
         using T = typename C::T;
         if (form == FORM_TILED) return tiled_sweep<N1, C>(cfg, maps, (T*)fout, p, s);
         const dim3 b(32, 8);
-        return launch_pdl(sweep_plain_kernel<N1, C>, grid2d(p, b), b, 0, s, (const T*)fin, (T*)fout, p);
+        if constexpr (C::dev) {
+            if (p.rowf) return launch_pdl(sweep_plain_kernel<N1, C, true>, grid2d(p, b), b, 0, s, (const T*)fin, (T*)fout, p);
+        }
+        return launch_pdl(sweep_plain_kernel<N1, C, false>, grid2d(p, b), b, 0, s, (const T*)fin, (T*)fout, p);
     }
     template <class C>
     static cudaError_t init_c(const double* fields, void* f, const KParams& p, cudaStream_t s) {

@@ -119,46 +119,50 @@ __device__ __forceinline__ typename C::R lds(const unsigned char* p) {
 
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s: a TMA load never takes that long
 
-// Periodic frame images of the value already stored at fluid cell (x, y) of plane lbase.
-template <class T>
-__device__ __forceinline__ void store_images_of(T* f, const Geom& g, long long lbase, int x, int y) {
-    const T v = f[lbase + (long long)(y + HY) * g.pitch + (x + g.hx)];
-    const int x0 = x - g.nx * ((x + FILL) / g.nx);
-    const int y0 = g.walls ? y : y - g.ny * ((y + FILL) / g.ny);
-    const int y1 = g.walls ? y + 1 : g.ny + FILL;
-    for (int yy = y0; yy < y1; yy += g.ny)
-        for (int xx = x0; xx < g.nx + FILL; xx += g.nx)
-            if (xx != x || yy != y) stg(f + lbase + (long long)(yy + HY) * g.pitch + (xx + g.hx), v);
-}
-
 // Collision of one gathered cell (fluid row y) in the codec's arithmetic, relaxation rate of the
 // domain; with a per-row deviation reference, against the row's reference (ROWS = false: the
 // launch never has one, e.g. a periodic-only form).
-template <int N1, class C, bool ROWS = true>
+// A ROWS launch always has the table (the launch checks it).
+template <int N1, class C, bool ROWS>
 __device__ __forceinline__ void collide_cell(typename C::R (&s)[N1 * N1], const KParams& p, const Geom& g, int y) {
     if constexpr (C::dev) {
-        const float* row = ROWS && p.rowf ? p.rowf + (long long)(y + HY) * kRowF : nullptr;
-        cell_collide_dev<N1>(s, p, g.omegaf, row);
+        if constexpr (ROWS) cell_collide_dev<N1, true>(s, p, g.omegaf, p.rowf + (long long)(y + HY) * kRowF);
+        else cell_collide_dev<N1, false>(s, p, g.omegaf, nullptr);
     }
     else if constexpr (std::is_same<typename C::R, double>::value) cell_collide<N1, false, double>(s, p, g.omegad);
     else cell_collide<N1, false, float>(s, p, g.omegaf);
 }
 
-// Store one collided cell: plain stores, then (cells within FILL of a periodic edge) the images.
+// Store one collided cell.  A cell within FILL of a periodic edge is stored at every position it
+// has in the read frame (itself and its periodic images), straight from the registers; the image
+// positions are worked out once per cell.
 template <int N1, class C>
 __device__ __forceinline__ void store_collided(typename C::T* f, const Geom& g, int x, int y,
                                                const typename C::R (&s)[N1 * N1]) {
-    typename C::T* q = f + ((long long)(y + HY) * g.pitch + (x + g.hx));
-#pragma unroll
-    for (int l = 0; l < N1 * N1; ++l) {
-        stg(q, C::enc(s[l]));
-        q += g.plane;
-    }
     const bool edge = x < FILL || x >= g.nx - FILL || (!g.walls && (y < FILL || y >= g.ny - FILL));
-    if (edge) {
-#pragma unroll 1
-        for (int l = 0; l < N1 * N1; ++l) store_images_of(f, g, (long long)l * g.plane, x, y);
+    if (!edge) {
+        typename C::T* q = f + ((long long)(y + HY) * g.pitch + (x + g.hx));
+#pragma unroll
+        for (int l = 0; l < N1 * N1; ++l) {
+            stg(q, C::enc(s[l]));
+            q += g.plane;
+        }
+        return;
     }
+    const int x0 = x - g.nx * ((x + FILL) / g.nx);
+    const int y0 = g.walls ? y : y - g.ny * ((y + FILL) / g.ny);
+    const int y1 = g.walls ? y + 1 : g.ny + FILL;
+#pragma unroll 1
+    for (int yy = y0; yy < y1; yy += g.ny)
+#pragma unroll 1
+        for (int xx = x0; xx < g.nx + FILL; xx += g.nx) {
+            typename C::T* q = f + ((long long)(yy + HY) * g.pitch + (xx + g.hx));
+#pragma unroll
+            for (int l = 0; l < N1 * N1; ++l) {
+                stg(q, C::enc(s[l]));
+                q += g.plane;
+            }
+        }
 }
 
 // ---- tile sources: where tile t lives --------------------------------------------------------
@@ -415,9 +419,11 @@ inline cudaError_t batch_sweep(int cfg, const BatchSrc& src, const KParams& p, c
 // ---- multi-step dataflow sweep ----------------------------------------------------------------
 // One persistent launch advances n time steps of a periodic domain.  Tasks (step k, tile t) are
 // handed out in step-major order from a global counter; a task starts once the 3 x 3 periodic
-// neighbourhood of its tile has finished step k - 1 (per-tile counters written with release
-// semantics after the tile's stores), which covers both the windows it reads and the region its
-// own stores overwrite (that region was the neighbours' step k - 1 input).  A task only waits on
+// neighbourhood of its tile has finished step k - 1 (per-tile counters that every compute warp
+// of the task raises with release semantics after its own stores, so a tile has finished step
+// k - 1 when its counter reaches k times the warps per task), which covers both the windows it
+// reads and the region its own stores overwrite (that region was the neighbours' step k - 1
+// input).  The compute warps of a CTA never wait for one another.  A task only waits on
 // tasks handed out before it, which are held by running CTAs, so the launch always progresses
 // (whether or not all CTAs are resident at once).
 // Every wait is bounded: a CTA that gives up raises the abort word and the status bit, and the
@@ -429,8 +435,8 @@ __device__ __forceinline__ int ld_relaxed_gpu(const int* p) {
     asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void st_release_gpu(int* p, int v) {
-    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void red_release_gpu_add(int* p, int v) {
+    asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 __device__ __forceinline__ void fence_acquire_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 // Generic-proxy global writes (made visible by the acquire) become visible to TMA reads.
@@ -465,21 +471,6 @@ struct FlowCfg {
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
-// Barrier `id` over the first `n` threads of the block that also returns whether `pred` held in
-// every one of them.
-__device__ __forceinline__ bool bar_and(int id, int n, bool pred) {
-    int out;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\t"
-        "setp.ne.s32 p, %1, 0;\n\t"
-        "barrier.cta.red.and.pred q, %2, %3, p;\n\t"
-        "selp.s32 %0, 1, 0, q;\n\t}"
-        : "=r"(out)
-        : "r"(pred ? 1 : 0), "r"(id), "r"(n)
-        : "memory");
-    return out != 0;
-}
-__device__ __forceinline__ void bar_sync(int id, int n) { asm volatile("barrier.cta.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
 
 // Producer (lane 0 of the last warp): take a task, wait for its neighbourhood, wait for a free
 // stage, publish the task in the stage's slot and start its Q window loads.  A negative slot
@@ -541,7 +532,7 @@ __global__ void __launch_bounds__(FlowCfg<N1, C, CFG>::THREADS, FlowCfg<N1, C, C
                 for (;;) {
                     int ready = 0;
 #pragma unroll
-                    for (int d = 0; d < 9; ++d) ready += ld_relaxed_gpu(nb[d]) >= k ? 1 : 0;
+                    for (int d = 0; d < 9; ++d) ready += ld_relaxed_gpu(nb[d]) >= k * NCW ? 1 : 0;
                     if (ready == 9) break;
                     if (*(volatile int*)src.abort || global_ns() - t0 > kWaitLimitNs) {
                         code = -2;
@@ -576,13 +567,13 @@ __global__ void __launch_bounds__(FlowCfg<N1, C, CFG>::THREADS, FlowCfg<N1, C, C
         }
     }
 
-    // ---- compute threads ----
+    // ---- compute threads: each warp on its own through the stages ----
     for (int n = 0;; ++n) {
         const int st = n % F::STAGES;
         const uint32_t par = (n / F::STAGES) & 1;
-        const bool ok = mbar_wait_bounded(&full[st], par, kConsumerLimitNs);
-        if (!bar_and(1, F::CONSUMERS, ok)) {
-            if (tid == 0) {
+        const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&full[st], par, kConsumerLimitNs));
+        if (!ok) {
+            if ((tid & 31) == 0) {
                 atomicExch(src.abort, 1);
                 if (p.status) atomicOr(p.status, 1);
             }
@@ -595,10 +586,11 @@ __global__ void __launch_bounds__(FlowCfg<N1, C, CFG>::THREADS, FlowCfg<N1, C, C
         tile_compute<N1, C, CFG, false>(base + st * F::STAGE_BYTES, x0, y0, g, reinterpret_cast<T*>(src.buf[(k + 1) & 1]), p,
                                  tid);
         fence_proxy_async_global();  // this thread's stores, visible to the TMA reads of later tasks
-        __syncwarp();
-        if ((tid & 31) == 0) mbar_arrive(&empty[st]);  // this warp is done with the stage
-        bar_sync(1, F::CONSUMERS);
-        if (tid == 0) st_release_gpu(src.done + t, k + 1);
+        __syncwarp();                // orders the lanes' stores before lane 0's release
+        if ((tid & 31) == 0) {
+            mbar_arrive(&empty[st]);  // this warp is done with the stage
+            red_release_gpu_add(src.done + t, 1);
+        }
     }
 }
 
