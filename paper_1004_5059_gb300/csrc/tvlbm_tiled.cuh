@@ -58,6 +58,11 @@ struct TileCfg {
     static constexpr int WIN_BYTES = (BX * BY * ES + 127) / 128 * 128;
     static constexpr int SMEM = Q * WIN_BYTES + 8 * Q + 128;  // windows, Q barriers, alignment slack
     static_assert(SMEM <= 227 * 1024, "tile windows exceed shared memory");
+    // resident CTAs per SM to compile for: D2Q36 in 32-bit arithmetic is held to about 168
+    // registers a thread (3 CTAs of 128 threads; left alone the compiler takes 253 and 2 fit),
+    // the others are unconstrained
+    static constexpr int MINB_D2Q36 = 65536 / (THREADS * 168);
+    static constexpr int MINB = (N1 >= 6 && sizeof(typename C::R) == 4 && MINB_D2Q36 > 1) ? MINB_D2Q36 : 1;
 };
 
 // ---- PTX wrappers -----------------------------------------------------------------------------
@@ -276,7 +281,7 @@ __device__ __forceinline__ void tile_compute(const unsigned char* base, int x0, 
 // ROWS: the launch has a per-row deviation reference (a separate instantiation, so the common
 // launch without one compiles exactly like the dataflow kernel's tile computation).
 template <int N1, class C, int CFG, class Src, bool ROWS>
-__global__ void __launch_bounds__(TileCfg<N1, C, CFG>::THREADS)
+__global__ void __launch_bounds__(TileCfg<N1, C, CFG>::THREADS, TileCfg<N1, C, CFG>::MINB)
     sweep_tiled_kernel(const __grid_constant__ Src src, const KParams p) {
     using Cfg = TileCfg<N1, C, CFG>;
     using R = typename C::R;
