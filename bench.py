@@ -163,9 +163,9 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
-def kernel_traffic(workload, form):
+def kernel_traffic(workload, form, tile=None):
     """DRAM bytes per sweep launch from the committed ncu summary, if it was taken on the
-    current kernel sources (else None)."""
+    current kernel sources with the same form and tile shape (else None)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
@@ -178,6 +178,8 @@ def kernel_traffic(workload, form):
         h.update(open(os.path.join(csrc, fn), "rb").read())
     e = d.get("%s/%s" % (workload, form))
     if not e or e.get("csrc_sha256") != h.hexdigest():
+        return None
+    if tile is not None and e.get("tile") is not None and list(e["tile"]) != list(tile):
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -316,6 +318,8 @@ def run_ours(args, w, rank, world, local_rank):
     achieved = bytes_per_cell * cells / avg_launch_s / 1e9
     if plain is not None:
         plain["roofline_frac"] = plain["bytes_per_cell"] * cells / plain_launch_s / 1e9 / peak
+    line_tile = (list(tv.tvlbm_tile_shape(probe.ctx, tuning["best"])) if tuning else
+                 (list(tv.tvlbm_tile_shape(probe.ctx, max(args.tile, 0))) if chosen != "plain" else None))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -327,15 +331,14 @@ def run_ours(args, w, rank, world, local_rank):
                    "deviation_reference": ("per row: u = 0, T linear between the walls (the start), reset to the "
                                            "row averages every %d steps inside the timed region" % w.get("refresh", 0)
                                            if w.get("reference") == "rows" else w.get("reference")),
-                   "tile": (list(tv.tvlbm_tile_shape(probe.ctx, tuning["best"])) if tuning else
-                            (list(tv.tvlbm_tile_shape(probe.ctx, max(args.tile, 0))) if chosen != "plain" else None)),
+                   "tile": line_tile,
                    "autotune_us_per_time_step": trials or None,
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "L2 flushed (512 MiB write) between timed steps; state %.0f MB" % (
                        bytes_per_cell * cells / 1e6)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": peak_kind, "bytes_per_cell": bytes_per_cell,
-                     "traffic": kernel_traffic(args.workload, chosen)},
+                     "traffic": kernel_traffic(args.workload, chosen, line_tile)},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * 8 * cells,
                 "d2h_bytes_per_step": 4 * 8 * cells},
         "gpu_launches": args.steps * (1 if chosen == "flow" else tsteps * launches_per_tstep),
