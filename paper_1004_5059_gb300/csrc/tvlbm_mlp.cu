@@ -312,7 +312,12 @@ __device__ __forceinline__ void store_h_sw128(unsigned char* h, int r, int c0, c
     }
 }
 
-__global__ void __launch_bounds__(128) mlp_fused_forward_kernel(const __grid_constant__ CUtensorMap mx,
+// Two warpgroups: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its rows) and takes columns
+// 64 (w / 4) .. + 63 of each hidden layer's epilogue, so every row's 128 GELUs are split over two
+// threads; the output layer's 16 columns go to the first warpgroup.
+constexpr int kFusedThreads = 256;
+
+__global__ void __launch_bounds__(kFusedThreads) mlp_fused_forward_kernel(const __grid_constant__ CUtensorMap mx,
                                                                 const __grid_constant__ CUtensorMap mw1,
                                                                 const __grid_constant__ CUtensorMap mw2,
                                                                 const __grid_constant__ CUtensorMap mw3,
@@ -342,8 +347,9 @@ __global__ void __launch_bounds__(128) mlp_fused_forward_kernel(const __grid_con
     unsigned char* w2 = base + FusedCfg::W2_OFF;
     unsigned char* w3 = base + FusedCfg::W3_OFF;
     unsigned char* hs = base + FusedCfg::H_OFF;
-    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
-    const int r = warp * 32 + lane;  // this thread's row of the tile (= its TMEM lane)
+    const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    const int r = (warp & 3) * 32 + lane;  // this thread's row of the tile (= its TMEM lane)
+    const int cbeg = (warp >> 2) * (NH / 2), cend = cbeg + NH / 2;  // its half of a hidden layer's columns
 
     bool ok = true;
     if (tid == 0) {
@@ -369,7 +375,7 @@ __global__ void __launch_bounds__(128) mlp_fused_forward_kernel(const __grid_con
     tc_fence_after();
     if (ok) {
 #pragma unroll 1
-        for (int c0 = 0; c0 < NH; c0 += 16) {
+        for (int c0 = cbeg; c0 < cend; c0 += 16) {
             float v[16];
             __syncwarp();
             tmem_ld16(taddr + (uint32_t)c0, v);
@@ -399,7 +405,7 @@ __global__ void __launch_bounds__(128) mlp_fused_forward_kernel(const __grid_con
     tc_fence_after();
     if (ok) {
 #pragma unroll 1
-        for (int c0 = 0; c0 < NH; c0 += 16) {
+        for (int c0 = cbeg; c0 < cend; c0 += 16) {
             float v[16];
             __syncwarp();
             tmem_ld16(taddr + (uint32_t)(NH + c0), v);
@@ -426,7 +432,7 @@ __global__ void __launch_bounds__(128) mlp_fused_forward_kernel(const __grid_con
     }
     ok = __syncthreads_and(ok && bar_wait(&mma_bar, 0)) != 0;
     tc_fence_after();
-    if (ok) {
+    if (ok && warp < 4) {
         float v[16];
         __syncwarp();
         tmem_ld16(taddr, v);
@@ -646,7 +652,8 @@ int mlp_forward_async(tvlbm_mlp* m, const void* x, int rows, float* y) {
                  "fused forward attribute");
         attr_set[dev] = true;
     }
-    mlp_fused_forward_kernel<<<tiles, 128, FusedCfg::SMEM, m->stream>>>(mx, mw1, mw2, mw3, m->theta, y, m->status);
+    mlp_fused_forward_kernel<<<tiles, kFusedThreads, FusedCfg::SMEM, m->stream>>>(mx, mw1, mw2, mw3, m->theta, y,
+                                                                                 m->status);
     MLP_CUDA(m, cudaGetLastError(), "fused forward");
     return TVLBM_OK;
 }
