@@ -312,10 +312,13 @@ __device__ __forceinline__ void store_h_sw128(unsigned char* h, int r, int c0, c
     }
 }
 
-// Two warpgroups: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its rows) and takes columns
-// 64 (w / 4) .. + 63 of each hidden layer's epilogue, so every row's 128 GELUs are split over two
-// threads; the output layer's 16 columns go to the first warpgroup.
-constexpr int kFusedThreads = 256;
+// kFusedGroups warpgroups: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its rows) and takes the
+// (w / 4)-th of kFusedGroups column ranges of each hidden layer's epilogue, so every row's 128
+// GELUs are split over kFusedGroups threads; the output layer's 16 columns go to the first
+// warpgroup.
+constexpr int kFusedGroups = 4;
+constexpr int kFusedThreads = 128 * kFusedGroups;
+static_assert(NH % (16 * kFusedGroups) == 0, "column ranges of whole 16-column loads");
 
 __global__ void __launch_bounds__(kFusedThreads) mlp_fused_forward_kernel(const __grid_constant__ CUtensorMap mx,
                                                                 const __grid_constant__ CUtensorMap mw1,
@@ -349,7 +352,7 @@ __global__ void __launch_bounds__(kFusedThreads) mlp_fused_forward_kernel(const 
     unsigned char* hs = base + FusedCfg::H_OFF;
     const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16);
     const int r = (warp & 3) * 32 + lane;  // this thread's row of the tile (= its TMEM lane)
-    const int cbeg = (warp >> 2) * (NH / 2), cend = cbeg + NH / 2;  // its half of a hidden layer's columns
+    const int cbeg = (warp >> 2) * (NH / kFusedGroups), cend = cbeg + NH / kFusedGroups;  // its column range
 
     bool ok = true;
     if (tid == 0) {
