@@ -341,7 +341,10 @@ def run_ours(args, w, rank, world, local_rank):
                      "traffic": kernel_traffic(args.workload, chosen, line_tile)},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * 8 * cells,
                 "d2h_bytes_per_step": 4 * 8 * cells},
-        "gpu_launches": args.steps * (1 if chosen == "flow" else tsteps * launches_per_tstep),
+        # sweeps (+ wall kernel per step) and, with a refreshed per-row reference, the five kernels
+        # of each refresh (row averages, two table kernels, shifts, re-encoding)
+        "gpu_launches": args.steps * ((1 if chosen == "flow" else tsteps * launches_per_tstep) +
+                                      (5 * (tsteps // w["refresh"]) if w.get("refresh") else 0)),
         "clocks": clk,
     }
     if plain is not None:
