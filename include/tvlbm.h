@@ -229,9 +229,9 @@ int tvlbm_conserved_sums(tvlbm_ctx *ctx, double out[5]);
  * is an interface variant of tvlbm_conserved_sums, the same FP64 two-pass reduction.
  *   populations  device pointer, packed [Q][ny][nx] in the storage format (the layout
  *                tvlbm_get_populations returns), caller-owned
- *   velset, storage, nx, ny, rho0   describe that array (deviation storage: d = f/w - rho0, the
- *                default reference; an array saved under tvlbm_set_reference or a per-row
- *                reference is not in that form)
+ *   velset, storage, nx, ny, rho0   describe that array (rho0: the reference density of
+ *                deviation storage, read as d = f/w - rho0, the default reference; an array
+ *                saved under tvlbm_set_reference or a per-row reference is not in that form)
  *   out5         device pointer to 5 doubles, caller-owned: M, P_x, P_y, E, #non-finite
  *   stream       cudaStream_t the two kernels are queued on (asynchronous; NULL = default)
  * The per-block partial sums live in a fixed device array of 1024 x 5 doubles (40 KiB) that
