@@ -172,16 +172,31 @@ def kernel_traffic(workload, form, tile=None):
         d = json.load(open(path))
     except (OSError, ValueError):
         return None
+    e = d.get("%s/%s" % (workload, form))
+    if not e:
+        return None
+    # the sources the kernel is built from, as recorded with the counters
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1004_5059_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        h.update(open(os.path.join(csrc, fn), "rb").read())
-    e = d.get("%s/%s" % (workload, form))
-    if not e or e.get("csrc_sha256") != h.hexdigest():
+    try:
+        for fn in e["csrc_files"]:
+            h.update(open(os.path.join(csrc, fn), "rb").read())
+    except (OSError, KeyError, TypeError):
+        return None
+    if e.get("csrc_sha256") != h.hexdigest():
         return None
     if tile is not None and e.get("tile") is not None and list(e["tile"]) != list(tile):
         return None
     return e.get("dram_bytes_per_launch")
+
+
+def traffic_per_time_step(workload, form, tile=None):
+    """kernel_traffic divided by the time steps one launch advances (a dataflow launch runs many)."""
+    b = kernel_traffic(workload, form, tile)
+    if b is None:
+        return None
+    d = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    return b / d["%s/%s" % (workload, form)].get("time_steps_per_launch", 1)
 
 
 def run_ours(args, w, rank, world, local_rank):
@@ -338,7 +353,9 @@ def run_ours(args, w, rank, world, local_rank):
                        bytes_per_cell * cells / 1e6)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": peak_kind, "bytes_per_cell": bytes_per_cell,
-                     "traffic": kernel_traffic(args.workload, chosen, line_tile)},
+                     "traffic": kernel_traffic(args.workload, chosen, line_tile),
+                     "traffic_per_time_step": traffic_per_time_step(args.workload, chosen, line_tile),
+                     "algorithmic_bytes_per_time_step": bytes_per_cell * cells},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * 8 * cells,
                 "d2h_bytes_per_step": 4 * 8 * cells},
         # sweeps (+ wall kernel per step) and, with a refreshed per-row reference, the five kernels
