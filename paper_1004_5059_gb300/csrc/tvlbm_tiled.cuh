@@ -59,10 +59,12 @@ struct TileCfg {
     static constexpr int SMEM = Q * WIN_BYTES + 8 * Q + 128;  // windows, Q barriers, alignment slack
     static_assert(SMEM <= 227 * 1024, "tile windows exceed shared memory");
     // resident CTAs per SM to compile for: D2Q36 in 32-bit arithmetic is held to about 168
-    // registers a thread (3 CTAs of 128 threads; left alone the compiler takes 253 and 2 fit),
-    // the others are unconstrained
+    // registers a thread (3 CTAs of 128 threads; left alone the compiler takes 253 and 2 fit).
+    // The others compile without a minimum (MINB = 0): even a minimum of 1 lets the compiler
+    // take more registers than the occupancy pays for (the batched D2Q16 kernel: 128 instead
+    // of 80).
     static constexpr int MINB_D2Q36 = 65536 / (THREADS * 168);
-    static constexpr int MINB = (N1 >= 6 && sizeof(typename C::R) == 4 && MINB_D2Q36 > 1) ? MINB_D2Q36 : 1;
+    static constexpr int MINB = (N1 >= 6 && sizeof(typename C::R) == 4 && MINB_D2Q36 > 1) ? MINB_D2Q36 : 0;
 };
 
 // ---- PTX wrappers -----------------------------------------------------------------------------
@@ -281,8 +283,7 @@ __device__ __forceinline__ void tile_compute(const unsigned char* base, int x0, 
 // ROWS: the launch has a per-row deviation reference (a separate instantiation, so the common
 // launch without one compiles exactly like the dataflow kernel's tile computation).
 template <int N1, class C, int CFG, class Src, bool ROWS>
-__global__ void __launch_bounds__(TileCfg<N1, C, CFG>::THREADS, TileCfg<N1, C, CFG>::MINB)
-    sweep_tiled_kernel(const __grid_constant__ Src src, const KParams p) {
+__device__ __forceinline__ void sweep_tiled_body(const Src& src, const KParams& p) {
     using Cfg = TileCfg<N1, C, CFG>;
     using R = typename C::R;
     using T = typename C::T;
@@ -338,6 +339,26 @@ __global__ void __launch_bounds__(TileCfg<N1, C, CFG>::THREADS, TileCfg<N1, C, C
     tile_compute<N1, C, CFG, ROWS>(base, x0, y0, g, reinterpret_cast<T*>(outv), p, tid);
 }
 
+// The kernel, with a minimum of resident CTAs where TileCfg asks for one.
+template <int N1, class C, int CFG, class Src, bool ROWS>
+__global__ void __launch_bounds__(TileCfg<N1, C, CFG>::THREADS)
+    sweep_tiled_kernel(const __grid_constant__ Src src, const KParams p) {
+    sweep_tiled_body<N1, C, CFG, Src, ROWS>(src, p);
+}
+template <int N1, class C, int CFG, class Src, bool ROWS>
+__global__ void __launch_bounds__(TileCfg<N1, C, CFG>::THREADS, (TileCfg<N1, C, CFG>::MINB > 0 ? TileCfg<N1, C, CFG>::MINB : 1))
+    sweep_tiled_kernel_minb(const __grid_constant__ Src src, const KParams p) {
+    sweep_tiled_body<N1, C, CFG, Src, ROWS>(src, p);
+}
+// (single domains only: the batched kernel's tile lookup needs the registers the minimum takes)
+template <int N1, class C, int CFG, class Src, bool ROWS>
+constexpr auto tiled_kernel() {
+    if constexpr (TileCfg<N1, C, CFG>::MINB > 0 && std::is_same<Src, SingleSrc>::value)
+        return sweep_tiled_kernel_minb<N1, C, CFG, Src, ROWS>;
+    else
+        return sweep_tiled_kernel<N1, C, CFG, Src, ROWS>;
+}
+
 template <int N1>
 inline int tiled_supported(int storage) {
     (void)storage;
@@ -359,7 +380,7 @@ inline cudaError_t tiled_prepare() {
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!attr_set[dev]) {
-        const cudaError_t e = cudaFuncSetAttribute(sweep_tiled_kernel<N1, C, CFG, Src, ROWS>,
+        const cudaError_t e = cudaFuncSetAttribute(tiled_kernel<N1, C, CFG, Src, ROWS>(),
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
         if (e != cudaSuccess) return e;
         attr_set[dev] = true;
@@ -377,7 +398,7 @@ inline cudaError_t tiled_launch_rows(const SweepMaps* maps, typename C::T* fout,
     src.fout = fout;
     src.tiles_x = (p.nx + Cfg::TX - 1) / Cfg::TX;
     src.ntiles = src.tiles_x * ((p.ny + Cfg::TY - 1) / Cfg::TY);
-    return launch_pdl(sweep_tiled_kernel<N1, C, CFG, SingleSrc, ROWS>, dim3(src.ntiles), dim3(Cfg::THREADS), Cfg::SMEM,
+    return launch_pdl(tiled_kernel<N1, C, CFG, SingleSrc, ROWS>(), dim3(src.ntiles), dim3(Cfg::THREADS), Cfg::SMEM,
                       s, src, p);
 }
 
@@ -406,7 +427,7 @@ inline cudaError_t batch_launch(const BatchSrc& src, const KParams& p, cudaStrea
     using Cfg = TileCfg<N1, C, CFG>;
     const cudaError_t e = tiled_prepare<N1, C, CFG, BatchSrc, false>();
     if (e != cudaSuccess) return e;
-    return launch_pdl(sweep_tiled_kernel<N1, C, CFG, BatchSrc, false>, dim3(src.ntiles), dim3(Cfg::THREADS), Cfg::SMEM, s,
+    return launch_pdl(tiled_kernel<N1, C, CFG, BatchSrc, false>(), dim3(src.ntiles), dim3(Cfg::THREADS), Cfg::SMEM, s,
                       src, p);
 }
 
