@@ -79,19 +79,18 @@ __device__ __forceinline__ void load_f(const typename C::T* f, const KParams& p,
         }
 }
 
-// M: the arithmetic (double for the training-side entry points, float on the learned step,
-// whose features are rounded to BF16 after normalisation anyway).
-template <class C, class M = double>
-__global__ void closure_moments_kernel(const typename C::T* __restrict__ f, float* __restrict__ m6, const KParams p) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= p.nx || y >= p.ny) return;
+// The six moments of one cell from its stored values v[l] (storage space), in arithmetic M:
+// m6[q][c] for q = rho, u_x, u_y, T, Pi_xy, Pi_xx - Pi_yy (non-equilibrium parts of the last two).
+template <class C, class M>
+__device__ __forceinline__ void cell_m6(const typename C::R (&sv)[Q], const KParams& p, float* __restrict__ m6, int x,
+                                        int y) {
     M rho = 0, jx = 0, jy = 0, e2 = 0, sxy = 0, sd = 0;
 #pragma unroll
     for (int j = 0; j < N1; ++j)
 #pragma unroll
         for (int i = 0; i < N1; ++i) {
             const int l = i + N1 * j;
-            const M v = to_f<C, M>((M)C::ld(f + cell_index(p, l, x, y)), kw<M>(p, i) * kw<M>(p, j), krho0<M>(p));
+            const M v = to_f<C, M>((M)sv[l], kw<M>(p, i) * kw<M>(p, j), krho0<M>(p));
             const M cx = kx<M>(p, i), cy = kx<M>(p, j);
             rho += v;
             jx += v * cx;
@@ -109,6 +108,18 @@ __global__ void closure_moments_kernel(const typename C::T* __restrict__ f, floa
     m6[3 * n + c] = (float)T;
     m6[4 * n + c] = (float)(sxy - rho * ux * uy);
     m6[5 * n + c] = (float)(sd - rho * (ux * ux - uy * uy));
+}
+
+// M: the arithmetic (double for the training-side entry points, float on the learned step,
+// whose features are rounded to BF16 after normalisation anyway).
+template <class C, class M = double>
+__global__ void closure_moments_kernel(const typename C::T* __restrict__ f, float* __restrict__ m6, const KParams p) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= p.nx || y >= p.ny) return;
+    typename C::R sv[Q];
+#pragma unroll
+    for (int l = 0; l < Q; ++l) sv[l] = C::ld(f + cell_index(p, l, x, y));
+    cell_m6<C, M>(sv, p, m6, x, y);
 }
 
 // Row y*nx + x of x_out: the normalised features of the 3 x 3 periodic neighbourhood.
@@ -219,10 +230,12 @@ __global__ void downsample_kernel(const typename CF::T* __restrict__ ff, const K
 }
 
 // Streaming alone (the learned step's first half): pull-gather as the plain sweep, stored with
-// the frame images, no collision.
-template <class C>
+// the frame images, no collision; and the streamed cell's moments into m6 in arithmetic M, from
+// the values just stored (so equal to closure_moments_kernel's on the stored state).
+template <class C, class M>
 __global__ void __launch_bounds__(256) closure_stream_kernel(const typename C::T* __restrict__ fin,
-                                                             typename C::T* __restrict__ fout, const KParams p) {
+                                                             typename C::T* __restrict__ fout, const KParams p,
+                                                             float* __restrict__ m6) {
     using R = typename C::R;
     using T = typename C::T;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -246,6 +259,7 @@ __global__ void __launch_bounds__(256) closure_stream_kernel(const typename C::T
         }
     }
     store_collided<N1, C>(fout, geom_of(p), x, y, s);
+    cell_m6<C, M>(s, p, m6, x, y);
 }
 
 // The learned collision (second half), in place on the streamed state: every cell becomes
@@ -499,20 +513,21 @@ int tvlbm_step_closure(tvlbm_ctx* c, tvlbm_mlp* m, const float* mu, const float*
         void* x = mlp_xbuf(m);
         float* y = mlp_ybuf(m);
         const dim3 b(32, 8), g = grid_of(c->nx, c->ny, b);
+        // streaming, with the streamed state's moments (FP64 storage: FP64 moments)
         switch (c->storage) {
-            case TVLBM_FP64: closure_stream_kernel<CodecF64><<<g, b, 0, st>>>((const double*)cur_buf(c), (double*)other_buf(c), c->kp); break;
-            case TVLBM_FP32: closure_stream_kernel<CodecF32><<<g, b, 0, st>>>((const float*)cur_buf(c), (float*)other_buf(c), c->kp); break;
-            default: closure_stream_kernel<CodecF32Dev><<<g, b, 0, st>>>((const float*)cur_buf(c), (float*)other_buf(c), c->kp); break;
+            case TVLBM_FP64:
+                closure_stream_kernel<CodecF64, double><<<g, b, 0, st>>>((const double*)cur_buf(c), (double*)other_buf(c), c->kp, m6);
+                break;
+            case TVLBM_FP32:
+                closure_stream_kernel<CodecF32, float><<<g, b, 0, st>>>((const float*)cur_buf(c), (float*)other_buf(c), c->kp, m6);
+                break;
+            default:
+                closure_stream_kernel<CodecF32Dev, float><<<g, b, 0, st>>>((const float*)cur_buf(c), (float*)other_buf(c), c->kp, m6);
+                break;
         }
         CL_CUDA(c, cudaGetLastError(), "closure stream kernel");
         c->cur ^= 1;
         const dim3 bm(32, 8), gm = grid_of(c->nx, c->ny, bm);
-        switch (c->storage) {
-            case TVLBM_FP64: closure_moments_kernel<CodecF64><<<gm, bm, 0, st>>>((const double*)cur_buf(c), m6, c->kp); break;
-            case TVLBM_FP32: closure_moments_kernel<CodecF32, float><<<gm, bm, 0, st>>>((const float*)cur_buf(c), m6, c->kp); break;
-            default: closure_moments_kernel<CodecF32Dev, float><<<gm, bm, 0, st>>>((const float*)cur_buf(c), m6, c->kp); break;
-        }
-        CL_CUDA(c, cudaGetLastError(), "closure moments kernel");
         closure_features_kernel<<<gm, bm, 0, st>>>(m6, c->nx, c->ny, nrm, (__nv_bfloat16*)x);
         CL_CUDA(c, cudaGetLastError(), "closure features kernel");
         const int r = mlp_forward_async(m, x, (int)ncell, y);
