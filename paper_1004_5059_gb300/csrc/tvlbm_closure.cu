@@ -510,7 +510,6 @@ int tvlbm_step_closure(tvlbm_ctx* c, tvlbm_mlp* m, const float* mu, const float*
     // one learned step on stream s: stream, features of the streamed state, network, collision
     auto one_step = [&](cudaStream_t st) -> int {
         float* m6 = (float*)(c->mem + c->L.off_mom);
-        void* x = mlp_xbuf(m);
         float* y = mlp_ybuf(m);
         const dim3 b(32, 8), g = grid_of(c->nx, c->ny, b);
         // streaming, with the streamed state's moments (FP64 storage: FP64 moments)
@@ -527,10 +526,16 @@ int tvlbm_step_closure(tvlbm_ctx* c, tvlbm_mlp* m, const float* mu, const float*
         }
         CL_CUDA(c, cudaGetLastError(), "closure stream kernel");
         c->cur ^= 1;
-        const dim3 bm(32, 8), gm = grid_of(c->nx, c->ny, bm);
-        closure_features_kernel<<<gm, bm, 0, st>>>(m6, c->nx, c->ny, nrm, (__nv_bfloat16*)x);
-        CL_CUDA(c, cudaGetLastError(), "closure features kernel");
-        const int r = mlp_forward_async(m, x, (int)ncell, y);
+        // the network, building its inputs (the 3 x 3 normalised moments) in its own tiles
+        MlpFeatures feat;
+        feat.m6 = m6;
+        feat.nx = c->nx;
+        feat.ny = c->ny;
+        for (int q = 0; q < NF; ++q) {
+            feat.mu[q] = nrm.mu[q];
+            feat.isg[q] = nrm.isg[q];
+        }
+        const int r = mlp_forward_features_async(m, feat, (int)ncell, y);
         if (r) return ctx_fail(c, r, tvlbm_mlp_last_error(m));
         switch (c->storage) {
             case TVLBM_FP64: closure_collide_kernel<CodecF64><<<g, b, 0, st>>>((double*)cur_buf(c), c->kp, y, bf, bd, sc); break;

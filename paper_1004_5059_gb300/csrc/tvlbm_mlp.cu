@@ -319,13 +319,39 @@ __device__ __forceinline__ void store_h_sw128(unsigned char* h, int r, int c0, c
 constexpr int kFusedGroups = 4;
 constexpr int kFusedThreads = 128 * kFusedGroups;
 static_assert(NH % (16 * kFusedGroups) == 0, "column ranges of whole 16-column loads");
+static_assert(NINP == 16 * kFusedGroups, "FEAT: one 16-column input chunk per warpgroup");
 
+// Features 16 G .. 16 G + 15 of cell `cell` (see MlpFeatures); neighbours wrap periodically.
+template <int G>
+__device__ __forceinline__ void feature_chunk(const MlpFeatures& f, int cell, float (&v)[16]) {
+    const int cy = cell / f.nx, cx = cell - cy * f.nx;
+    const long long n = (long long)f.nx * f.ny;
+    const int xm = cx == 0 ? f.nx - 1 : cx - 1, xp = cx == f.nx - 1 ? 0 : cx + 1;
+    const int ym = cy == 0 ? f.ny - 1 : cy - 1, yp = cy == f.ny - 1 ? 0 : cy + 1;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        constexpr int base = 16 * G;
+        const int fi = base + e;  // compile time once unrolled
+        if (fi >= NIN) {
+            v[e] = 0.0f;
+            continue;
+        }
+        const int k = fi / 6, q = fi % 6;
+        const int xx = k % 3 == 0 ? xm : (k % 3 == 1 ? cx : xp), yy = k / 3 == 0 ? ym : (k / 3 == 1 ? cy : yp);
+        v[e] = (__ldg(f.m6 + q * n + (long long)yy * f.nx + xx) - f.mu[q]) * f.isg[q];
+    }
+}
+
+// FEAT: the input tile is built by the CTA's threads from the closure's moments (MlpFeatures)
+// instead of loaded by TMA; thread (row r, warpgroup g) makes features 16 g .. 16 g + 15 of row
+// r with the closure features kernel's arithmetic, so the inputs are the same BF16 values.
+template <bool FEAT>
 __global__ void __launch_bounds__(kFusedThreads) mlp_fused_forward_kernel(const __grid_constant__ CUtensorMap mx,
                                                                 const __grid_constant__ CUtensorMap mw1,
                                                                 const __grid_constant__ CUtensorMap mw2,
                                                                 const __grid_constant__ CUtensorMap mw3,
                                                                 const float* __restrict__ theta, float* __restrict__ y,
-                                                                int* status) {
+                                                                int* status, const MlpFeatures feat) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((1024u - (saddr(smem_raw) & 1023u)) & 1023u);
     __shared__ uint64_t load_bar, mma_bar;
@@ -356,13 +382,30 @@ __global__ void __launch_bounds__(kFusedThreads) mlp_fused_forward_kernel(const 
 
     bool ok = true;
     if (tid == 0) {
-        bar_expect_tx(&load_bar, FusedCfg::TX);
-        tma_load_2d(xs, &mx, &load_bar, 0, m0);
+        bar_expect_tx(&load_bar, FEAT ? FusedCfg::TX - (uint32_t)(BM * NINP * 2) : FusedCfg::TX);
+        if (!FEAT) tma_load_2d(xs, &mx, &load_bar, 0, m0);
         tma_load_2d(w1, &mw1, &load_bar, 0, 0);
         tma_load_2d(w2, &mw2, &load_bar, 0, 0);
         tma_load_2d(w2 + 16384, &mw2, &load_bar, BK, 0);
         tma_load_2d(w3, &mw3, &load_bar, 0, 0);
         tma_load_2d(w3 + 2048, &mw3, &load_bar, BK, 0);
+    }
+    if constexpr (FEAT) {
+        // this thread's 16 input columns 16 g .. 16 g + 15 of row r, each builder with its feature
+        // indices known at compile time
+        const int g = warp >> 2;
+        float v[16];
+        switch (g) {
+            case 0: feature_chunk<0>(feat, m0 + r, v); break;
+            case 1: feature_chunk<1>(feat, m0 + r, v); break;
+            case 2: feature_chunk<2>(feat, m0 + r, v); break;
+            default: feature_chunk<3>(feat, m0 + r, v); break;
+        }
+        store_h_sw128(xs, r, 16 * g, v);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> MMA reads
+        __syncthreads();
+    }
+    if (tid == 0) {
         ok = bar_wait(&load_bar, 0);
         if (ok) {
             tc_fence_after();
@@ -650,14 +693,43 @@ int mlp_forward_async(tvlbm_mlp* m, const void* x, int rows, float* y) {
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-        MLP_CUDA(m, cudaFuncSetAttribute(mlp_fused_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        MLP_CUDA(m, cudaFuncSetAttribute(mlp_fused_forward_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          FusedCfg::SMEM),
                  "fused forward attribute");
         attr_set[dev] = true;
     }
-    mlp_fused_forward_kernel<<<tiles, kFusedThreads, FusedCfg::SMEM, m->stream>>>(mx, mw1, mw2, mw3, m->theta, y,
-                                                                                 m->status);
+    MlpFeatures none;
+    memset(&none, 0, sizeof(none));
+    mlp_fused_forward_kernel<false><<<tiles, kFusedThreads, FusedCfg::SMEM, m->stream>>>(mx, mw1, mw2, mw3, m->theta, y,
+                                                                                        m->status, none);
     MLP_CUDA(m, cudaGetLastError(), "fused forward");
+    return TVLBM_OK;
+}
+
+int mlp_forward_features_async(tvlbm_mlp* m, const MlpFeatures& feat, int rows, float* y) {
+    int rc = check_rows(m, rows);
+    if (rc) return rc;
+    if (!feat.m6 || feat.nx < 1 || feat.ny < 1 || (long long)feat.nx * feat.ny != rows)
+        return mfail(m, TVLBM_EINVAL, "feature source does not match the rows");
+    // the weight descriptors (the input one is passed along unused)
+    CUtensorMap mx, mw1, mw2, mw3;
+    memset(&mx, 0, sizeof(mx));
+    if (!bf16_map(&mw1, m->w1p, NINP, NH, NINP, NH) || !bf16_map(&mw2, m->w2, NH, NH, NH, NH) ||
+        !bf16_map(&mw3, m->w3p, NH, NOUTP, NH, NOUTP))
+        return mfail(m, TVLBM_EINVAL, "TMA descriptor rejected");
+    const int tiles = rows / BM;
+    static bool attr_set[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+        MLP_CUDA(m, cudaFuncSetAttribute(mlp_fused_forward_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         FusedCfg::SMEM),
+                 "fused forward attribute");
+        attr_set[dev] = true;
+    }
+    mlp_fused_forward_kernel<true><<<tiles, kFusedThreads, FusedCfg::SMEM, m->stream>>>(mx, mw1, mw2, mw3, m->theta, y,
+                                                                                       m->status, feat);
+    MLP_CUDA(m, cudaGetLastError(), "fused forward with features");
     return TVLBM_OK;
 }
 int mlp_max_rows(const tvlbm_mlp* m) { return m->max_rows; }
