@@ -40,8 +40,15 @@ struct WallParams {
     double* eq;  // [2][nx][2] wall equilibria (u_eq, T_eq), warm start of the next imposition
 };
 
+// Resident CTAs per SM the collision-term kernel is compiled for (as fv_update_minb: each set and
+// precision held near its own register need).
 template <int N1, class C>
-__global__ void __launch_bounds__(256) fv_omega_kernel(const typename C::T* __restrict__ f,
+constexpr int fv_omega_minb() {
+    return sizeof(typename C::R) == 4 ? (N1 <= 4 ? 4 : 2) : (N1 == 3 ? 3 : (N1 == 4 ? 2 : 1));
+}
+
+template <int N1, class C>
+__global__ void __launch_bounds__(256, fv_omega_minb<N1, C>()) fv_omega_kernel(const typename C::T* __restrict__ f,
                                                        typename C::T* __restrict__ om, const KParams p,
                                                        const FvParams fp) {
     using R = typename C::R;
@@ -117,8 +124,16 @@ __global__ void __launch_bounds__(256) fv_omega_kernel(const typename C::T* __re
     store_collided<N1, C>(om, geom_of(p), x, y, w);
 }
 
+// Resident CTAs per SM the update is compiled for: its time is load latency, so occupancy pays
+// (D2Q16 FP32: 4 CTAs of 256 threads at 64 registers, 7.9 against 7.3 G cell updates per second
+// at 106 registers and 2 CTAs); each set and precision is held near its own register need.
 template <int N1, class C>
-__global__ void __launch_bounds__(256) fv_update_kernel(const typename C::T* __restrict__ f,
+constexpr int fv_update_minb() {
+    return sizeof(typename C::R) == 4 ? (N1 <= 4 ? 4 : 3) : (N1 <= 3 ? 4 : (N1 == 4 ? 2 : 1));
+}
+
+template <int N1, class C>
+__global__ void __launch_bounds__(256, fv_update_minb<N1, C>()) fv_update_kernel(const typename C::T* __restrict__ f,
                                                         const typename C::T* __restrict__ om,
                                                         typename C::T* __restrict__ fout, const KParams p,
                                                         const FvParams fp) {
