@@ -73,3 +73,40 @@ def test_batch_conservation_per_domain(tv):
         s1 = b.conserved_sums(d)
         assert np.all(np.abs(s1[:4] - s0[d][:4]) < 2e-8 * s0[d][0]), (d, s1 - s0[d])
     b.close()
+
+
+@pytest.mark.slow
+def test_batch_full_size_bench_workload(tv):
+    """The batched workload as the bench runs it: 256 periodic D2Q16 domains (sides from
+    {128 .. 1024}, tau ~ U[0.55, 1.5], seeded Gaussian bump + random flow at each domain's Mach
+    number), FP32 deviation storage, the 64 x 16 tile the bench's autotuner picks, one bench step
+    of 20 time steps.  The smallest, a middle and the largest domain equal the same domain run
+    alone bit for bit (single-domain runs are checked against the oracle elsewhere), and every
+    domain conserves mass, momentum and energy to FP32 rounding."""
+    specs = workloads.batched_domains(256, seed=3)
+    n = [s["n"] for s in specs]
+    b = tv.Batch(n, n, [s["tau"] for s in specs], "D2Q16", storage="fp32_dev")
+    cfg = [k for k in range(b.tile_count()) if tuple(b.tile_shape(k)) == (64, 16, 4)][0]
+    b.set_tile(cfg)
+
+    def fields(s):
+        return workloads.gaussian_bump_random_flow(s["n"], s["n"], seed=s["seed"], amp_u=s["mach"], sigma=s["n"] / 16.0)
+
+    for d, s in enumerate(specs):
+        b.init_moments(d, *fields(s))
+    s0 = [b.conserved_sums(d) for d in range(len(specs))]
+    b.step(20)
+    for d in range(len(specs)):
+        s1 = b.conserved_sums(d)
+        assert s1[4] == 0, d
+        assert np.all(np.abs(s1[:4] - s0[d][:4]) < 1e-7 * s0[d][0]), (d, s1 - s0[d])
+    order = sorted(range(len(specs)), key=lambda d: specs[d]["n"])
+    for d in (order[0], order[len(order) // 2], order[-1]):
+        s = specs[d]
+        sim = tv.Simulation(s["n"], s["n"], "D2Q16", tau=s["tau"], storage="fp32_dev", form="tiled")
+        sim.set_tile(cfg)
+        sim.init_moments(*fields(s))
+        sim.step(20)
+        assert np.array_equal(b.populations_f64(d), sim.populations_f64()), d
+        sim.close()
+    b.close()
