@@ -737,7 +737,6 @@ int mlp_forward_features_async(tvlbm_mlp* m, const MlpFeatures& feat, int rows, 
 }
 int mlp_max_rows(const tvlbm_mlp* m) { return m->max_rows; }
 float* mlp_ybuf(tvlbm_mlp* m) { return m->ybuf; }
-void* mlp_xbuf(tvlbm_mlp* m) { return m->xt; }
 int mlp_set_stream(tvlbm_mlp* m, cudaStream_t s) {
     m->stream = s;
     return TVLBM_OK;

@@ -22,7 +22,6 @@ struct MlpFeatures {
 int mlp_forward_features_async(tvlbm_mlp* m, const MlpFeatures& feat, int rows, float* y);
 int mlp_max_rows(const tvlbm_mlp* m);
 float* mlp_ybuf(tvlbm_mlp* m);  // the network's own [max_rows][16] output buffer
-void* mlp_xbuf(tvlbm_mlp* m);   // max_rows x 64 BF16 of scratch (training reuses it)
 int mlp_set_stream(tvlbm_mlp* m, cudaStream_t s);
 int mlp_status(tvlbm_mlp* m);  // synchronises; ETIMEOUT if a device wait gave up
 unsigned long long mlp_uid(const tvlbm_mlp* m);  // unique over the process's networks
