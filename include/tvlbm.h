@@ -163,7 +163,8 @@ int tvlbm_set_graphs(tvlbm_ctx *ctx, int enable);
  * f_eq(rho0, (ux, uy), T), i.e. store d_l = f_l / w_l - f_eq_l / w_l (default: at rest, T = 1).
  * A reference near the flow's mean state shrinks |d| and with it the half-precision rounding
  * error.  The current state is re-encoded (synchronises).  Errors: EINVAL (full-f storage,
- * T <= 0). */
+ * T <= 0).  Allocates the context's re-encoding buffer on first use (see
+ * tvlbm_set_reference_rows). */
 int tvlbm_set_reference(tvlbm_ctx *ctx, double ux, double uy, double T);
 
 /* Deviation storage on a domain with walls: a reference that varies across the channel.  Fluid
@@ -175,7 +176,10 @@ int tvlbm_set_reference(tvlbm_ctx *ctx, double ux, double uy, double T);
  * arithmetic: the gather of row y adds S_l(y), the gather of R over the source rows minus R_l(y),
  * and the collision takes the row's reference moments (tables of a few hundred bytes per row,
  * built on the device).  ux, uy, T: host arrays of ny values (copied).  The current state is
- * re-encoded (synchronises); tvlbm_set_reference returns to a single reference.  Errors: EINVAL (full-f storage, periodic domain, null array, T <= 0 or a
+ * re-encoded (synchronises); tvlbm_set_reference returns to a single reference.  The first call
+ * allocates the context's reference tables and re-encoding buffer with cudaMalloc (about
+ * 2 (40 doubles + 48 floats) + 36 floats per stored row and 3 ny doubles; kept until
+ * tvlbm_destroy), also for a context created in caller-provided memory.  Errors: EINVAL (full-f storage, periodic domain, null array, T <= 0 or a
  * non-finite value), ENOMEM, ECUDA. */
 int tvlbm_set_reference_rows(tvlbm_ctx *ctx, const double *ux, const double *uy, const double *T);
 
