@@ -356,14 +356,11 @@ __global__ void __launch_bounds__(kFusedThreads) mlp_fused_forward_kernel(const 
     unsigned char* base = smem_raw + ((1024u - (saddr(smem_raw) & 1023u)) & 1023u);
     __shared__ uint64_t load_bar, mma_bar;
     __shared__ uint32_t tmem_slot;
-    __shared__ float bias[NH + NH + NOUTP];  // b1, b2, b3 (padded), read by every epilogue chunk
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.x * BM;
-    const float* b1 = bias;
-    const float* b2 = bias + NH;
-    const float* b3 = bias + 2 * NH;
-    for (int i = tid; i < NH + NH + NOUTP; i += kFusedThreads)
-        bias[i] = i < NH ? theta[OFF_B1 + i] : (i < 2 * NH ? theta[OFF_B2 + i - NH] : (i - 2 * NH < NOUT ? theta[OFF_B3 + i - 2 * NH] : 0.0f));
+    const float* b1 = theta + OFF_B1;
+    const float* b2 = theta + OFF_B2;
+    const float* b3 = theta + OFF_B3;
     if (tid == 0) {
         bar_init(&load_bar, 1);
         bar_init(&mma_bar, 1);
