@@ -511,7 +511,7 @@ int tvlbm_step_closure(tvlbm_ctx* c, tvlbm_mlp* m, const float* mu, const float*
     auto one_step = [&](cudaStream_t st) -> int {
         float* m6 = (float*)(c->mem + c->L.off_mom);
         float* y = mlp_ybuf(m);
-        const dim3 b(32, 8), g = grid_of(c->nx, c->ny, b);
+        const dim3 b(32, 4), g = grid_of(c->nx, c->ny, b);  // 128 threads: an even spread of the blocks over the SMs
         // streaming, with the streamed state's moments (FP64 storage: FP64 moments)
         switch (c->storage) {
             case TVLBM_FP64:
