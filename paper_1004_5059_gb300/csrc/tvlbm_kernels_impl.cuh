@@ -272,15 +272,24 @@ __global__ void halo_kernel(T* __restrict__ f, const KParams p, int Q) {
 }
 
 // d_l += delta[r][l] on every stored element (fluid and frame, stored row r) of a
-// deviation-coded buffer: grid (pitch / 256, <= 65535 row blocks striding over the rows, Q).
+// deviation-coded buffer: one 16-byte vector of a row per thread (the pitch and the plane are
+// multiples of 32 elements, so vectors are aligned and never cross a row); grid (pitch / (256 V),
+// <= 65535 row blocks striding over the rows, Q).
 template <class C>
 __global__ void __launch_bounds__(256) reencode_kernel(typename C::T* __restrict__ f, long long plane, int pitch,
                                                        int rows, const float* __restrict__ delta) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, l = blockIdx.z;
-    if (x >= pitch) return;
+    using T = typename C::T;
+    constexpr int V = 16 / (int)sizeof(T);
+    const int xv = blockIdx.x * blockDim.x + threadIdx.x, l = blockIdx.z;
+    if (xv * V >= pitch) return;
     for (int r = blockIdx.y; r < rows; r += gridDim.y) {
-        typename C::T* q = f + (long long)l * plane + (long long)r * pitch + x;
-        *q = C::enc(C::ld(q) + __ldg(delta + (long long)r * kMaxQ + l));
+        T* q = f + (long long)l * plane + (long long)r * pitch + (long long)xv * V;
+        const float d = __ldg(delta + (long long)r * kMaxQ + l);
+        uint4 u = *reinterpret_cast<const uint4*>(q);
+        T* e = reinterpret_cast<T*>(&u);
+#pragma unroll
+        for (int k = 0; k < V; ++k) e[k] = C::enc(lds<C>(reinterpret_cast<const unsigned char*>(e + k)) + d);
+        *reinterpret_cast<uint4*>(q) = u;
     }
 }
 
@@ -476,7 +485,8 @@ struct Launch {
     template <class C>
     static cudaError_t reencode_c(void* f, const float* delta, const KParams& p, cudaStream_t s) {
         if constexpr (!C::dev) return cudaErrorInvalidValue;
-        const dim3 grid((p.pitch + 255) / 256, p.rows < 65535 ? p.rows : 65535, N1 * N1);
+        constexpr int V = 16 / (int)sizeof(typename C::T);
+        const dim3 grid((p.pitch / V + 255) / 256, p.rows < 65535 ? p.rows : 65535, N1 * N1);
         reencode_kernel<C><<<grid, 256, 0, s>>>((typename C::T*)f, p.plane, p.pitch, p.rows, delta);
         return cudaGetLastError();
     }
