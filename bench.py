@@ -834,7 +834,8 @@ def run_closure(args, rank, world, local_rank):
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "peak_kind": peak_kind, "flops_per_launch": flops, "traffic": None},
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 4 * 8 * cells, "d2h_bytes_per_step": 4 * 8 * cells},
-        "gpu_launches": args.steps * nsteps * 6,
+        # per learned step: streaming with moments, the network (inputs built in it), the collision
+        "gpu_launches": args.steps * nsteps * 3,
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
