@@ -163,10 +163,22 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
+def csrc_hash(files):
+    """sha256 of the named kernel source files (in order), or None if one is missing."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1004_5059_gb300", "csrc")
+    try:
+        for fn in files:
+            h.update(open(os.path.join(csrc, fn), "rb").read())
+    except (OSError, TypeError):
+        return None
+    return h.hexdigest()
+
+
 def kernel_traffic(workload, form, tile=None):
     """DRAM bytes per sweep launch from the committed ncu summary, if it was taken on the
     current kernel sources with the same form and tile shape (else None)."""
-    import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         d = json.load(open(path))
@@ -176,14 +188,7 @@ def kernel_traffic(workload, form, tile=None):
     if not e:
         return None
     # the sources the kernel is built from, as recorded with the counters
-    h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_1004_5059_gb300", "csrc")
-    try:
-        for fn in e["csrc_files"]:
-            h.update(open(os.path.join(csrc, fn), "rb").read())
-    except (OSError, KeyError, TypeError):
-        return None
-    if e.get("csrc_sha256") != h.hexdigest():
+    if e.get("csrc_sha256") != csrc_hash(e.get("csrc_files")):
         return None
     if tile is not None and e.get("tile") is not None and list(e["tile"]) != list(tile):
         return None

@@ -55,7 +55,9 @@ extern "C" {
 
 /* ---- population storage ----------------------------------------------------------------- */
 #define TVLBM_FP64 0     /* f_l as double; FP64 arithmetic                                   */
-#define TVLBM_FP32 1     /* f_l as float;  FP32 arithmetic                                   */
+#define TVLBM_FP32 1     /* f_l as float;  FP32 arithmetic on f_l - w_l (the unit-density rest
+                            population, exact to FP64, split off: only the store rounds
+                            relative to f)                                                    */
 #define TVLBM_BF16_DEV 2 /* d_l = (f_l - w_l rho0)/w_l as bfloat16 (round to nearest even);
                             FP32 arithmetic                                                   */
 #define TVLBM_FP16_DEV 3 /* d_l as IEEE binary16 (round to nearest even); FP32 arithmetic     */
@@ -184,15 +186,29 @@ int tvlbm_set_reference(tvlbm_ctx *ctx, double ux, double uy, double T);
 int tvlbm_set_reference_rows(tvlbm_ctx *ctx, const double *ux, const double *uy, const double *T);
 
 /* Deviation storage on a domain with walls: keep the per-row reference following the flow.
- * Every `every` time steps tvlbm_step resets the reference rows to the current row averages of
- * (ux, uy, T) and re-encodes the state: a row-average pass, two small table kernels and one
- * re-encoding pass over the state, queued on the context's stream without a host
+ * Every `every` time steps tvlbm_step resets the reference rows to the current rows (the
+ * equilibria of the row averages of (ux, uy, T), or the row averages of the populations, see
+ * tvlbm_set_reference_kind) and re-encodes the state: a row-average pass, two small table kernels
+ * and one re-encoding pass over the state, queued on the context's stream without a host
  * synchronisation.  With no per-row reference yet, one is taken from the current state at once.
  * A row whose average is not a valid state (T <= 0, not finite) takes the default reference.
  * every = 0 turns refreshing off (the reference stays as it is).  Refreshing only changes the
  * encoding: in exact arithmetic the state is unchanged.  Errors: EINVAL (full-f storage,
  * periodic domain, every < 0), ENOMEM, ECUDA. */
 int tvlbm_set_reference_refresh(tvlbm_ctx *ctx, int every);
+
+/* What a refresh of the per-row reference (tvlbm_set_reference_refresh) installs:
+ *   TVLBM_REF_EQUILIBRIUM (default)  R_l(y) = f_eq_l(rho0, row average of (ux, uy), row average of T) / w_l;
+ *   TVLBM_REF_MEAN                   R_l(y) = the row average of f_l / w_l itself, the full population
+ *                                    (non-equilibrium part and the row's density included).
+ * With the mean kind, a flow that varies only across the channel (a Couette flow between the
+ * walls) is stored as its departures from its own row averages, which stay small between
+ * refreshes: the half-precision rounding error shrinks with them (BF16 deviation storage needs
+ * it to stay within 1e-3 on such a channel).  Either kind is an exact re-encoding; it takes effect
+ * at the next refresh.  Errors: EINVAL (unknown kind, full-f storage, periodic domain). */
+#define TVLBM_REF_EQUILIBRIUM 0
+#define TVLBM_REF_MEAN 1
+int tvlbm_set_reference_kind(tvlbm_ctx *ctx, int kind);
 
 /* Tile configurations of the tiled form (an autotuner picks among them): their number, and
  * the shape of one -- tile width and height in cells and rows each thread walks.

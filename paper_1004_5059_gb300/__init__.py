@@ -79,6 +79,7 @@ def _load_library() -> ctypes.CDLL:
         "tvlbm_set_reference": (_I, [_P, _D, _D, _D]),
         "tvlbm_set_reference_rows": (_I, [_P, _P, _P, _P]),
         "tvlbm_set_reference_refresh": (_I, [_P, _I]),
+        "tvlbm_set_reference_kind": (_I, [_P, _I]),
         "tvlbm_tile_count": (_I, [_P]),
         "tvlbm_tile_shape": (_I, [_P, _I, _IP, _IP, _IP]),
         "tvlbm_set_tile": (_I, [_P, _I]),
@@ -211,6 +212,13 @@ def tvlbm_set_reference_rows(ctx, ny: int, ux, uy, T):
 
 def tvlbm_set_reference_refresh(ctx, every: int):
     _check(_lib.tvlbm_set_reference_refresh(ctx, int(every)), ctx)
+
+
+REFERENCE_KINDS = {"equilibrium": 0, "mean": 1}
+
+
+def tvlbm_set_reference_kind(ctx, kind: int):
+    _check(_lib.tvlbm_set_reference_kind(ctx, int(kind)), ctx)
 
 
 def tvlbm_tile_count(ctx) -> int:
@@ -363,8 +371,12 @@ class Simulation:
         """Per-row deviation reference of a channel: ux, uy, T hold ny values (or scalars)."""
         tvlbm_set_reference_rows(self.ctx, self.ny, ux, uy, T)
 
-    def set_reference_refresh(self, every: int):
-        """Reset the per-row reference to the row averages every `every` steps (0: off)."""
+    def set_reference_refresh(self, every: int, kind=None):
+        """Reset the per-row reference to the rows every `every` steps (0: off); kind
+        "equilibrium" (the rows' average equilibria) or "mean" (the rows' average populations),
+        None keeps the current kind."""
+        if kind is not None:
+            tvlbm_set_reference_kind(self.ctx, REFERENCE_KINDS[kind] if isinstance(kind, str) else int(kind))
         tvlbm_set_reference_refresh(self.ctx, every)
 
     def init_moments(self, rho, ux, uy, T):

@@ -255,7 +255,8 @@ bool ensure_reference_buffers(tvlbm_ctx* c) {
     if (c->ref_mem) return true;
     const size_t rows = (size_t)c->L.rows;
     const size_t bd = align_up(rows * kRowD * sizeof(double), 256), bf = align_up(rows * kRowF * sizeof(float), 256);
-    const size_t bdel = align_up(rows * kMaxQ * sizeof(float), 256), bp = align_up(3 * (size_t)c->ny * sizeof(double), 256);
+    const size_t bdel = align_up(rows * kMaxQ * sizeof(float), 256);
+    const size_t bp = align_up((size_t)kMaxQ * c->ny * sizeof(double), 256);  // [3][ny] or [Q][ny] profile
     unsigned char* m = nullptr;
     if (cudaMalloc((void**)&m, 2 * bd + 2 * bf + bdel + bp) != cudaSuccess) return false;
     c->ref_mem = m;
@@ -299,12 +300,17 @@ cudaError_t reencode_between(tvlbm_ctx* c, const RefSide& from, const RefSide& t
     return c->kt->reencode(c->storage, fcur(c), c->ref_delta, c->kp, c->stream);
 }
 
-// Switch to the per-row reference of the profile in c->ref_prof (device [3][ny]): build its tables
-// in the spare pair, re-encode the state, copy the tables over the live ones (stream-ordered, no
-// host synchronisation; the kernel parameters keep the live pointers, so captured graphs stay
-// valid).  The first switch points the kernel parameters at the live tables.
-int install_reference_rows(tvlbm_ctx* c) {
-    TVLBM_CUDA(c, c->kt->ref_tables(c->ref_prof, c->ref_new_d, c->ref_new_f, c->kp, c->stream), "reference tables");
+// Switch to the per-row reference of the profile in c->ref_prof (device; mean = false: [3][ny] of
+// (ux, uy, T), the rows' equilibria; mean = true: [Q][ny] of Pref itself): build its tables in the
+// spare pair, re-encode the state, copy the tables over the live ones (stream-ordered, no host
+// synchronisation; the kernel parameters keep the live pointers, so captured graphs stay valid).
+// The first switch points the kernel parameters at the live tables.
+int install_reference_rows(tvlbm_ctx* c, bool mean) {
+    if (mean)
+        TVLBM_CUDA(c, c->kt->ref_tables_mean(c->ref_prof, c->ref_new_d, c->ref_new_f, c->kp, c->stream),
+                   "reference tables");
+    else
+        TVLBM_CUDA(c, c->kt->ref_tables(c->ref_prof, c->ref_new_d, c->ref_new_f, c->kp, c->stream), "reference tables");
     RefSide to;
     to.rows = c->ref_new_d;
     for (int l = 0; l < kMaxQ; ++l) to.c[l] = 0.0;
@@ -324,11 +330,17 @@ int install_reference_rows(tvlbm_ctx* c) {
     return TVLBM_OK;
 }
 
-// Reset the per-row reference to the current row averages of (u_x, u_y, T) and re-encode.
+// Reset the per-row reference to the current rows (kind TVLBM_REF_EQUILIBRIUM: the equilibria of
+// the row averages of (u_x, u_y, T); TVLBM_REF_MEAN: the row averages of the populations) and
+// re-encode.
 int refresh_reference_rows(tvlbm_ctx* c) {
     if (!ensure_reference_buffers(c)) return fail(c, TVLBM_ENOMEM, "reference tables");
-    TVLBM_CUDA(c, c->kt->row_means(c->storage, fcur(c), c->ref_prof, c->kp, c->stream), "row means kernel");
-    return install_reference_rows(c);
+    const bool mean = c->ref_kind == TVLBM_REF_MEAN;
+    if (mean)
+        TVLBM_CUDA(c, c->kt->row_pop_means(c->storage, fcur(c), c->ref_prof, c->kp, c->stream), "row means kernel");
+    else
+        TVLBM_CUDA(c, c->kt->row_means(c->storage, fcur(c), c->ref_prof, c->kp, c->stream), "row means kernel");
+    return install_reference_rows(c, mean);
 }
 
 }  // namespace
@@ -444,7 +456,7 @@ int tvlbm_set_reference_rows(tvlbm_ctx* c, const double* ux, const double* uy, c
     for (int k = 0; k < 3; ++k)
         TVLBM_CUDA(c, cudaMemcpyAsync(c->ref_prof + (size_t)k * c->ny, src[k], c->ny * sizeof(double),
                                       cudaMemcpyHostToDevice, c->stream), "profile upload");
-    rc = install_reference_rows(c);
+    rc = install_reference_rows(c, false);
     if (rc) return rc;
     TVLBM_CUDA(c, cudaStreamSynchronize(c->stream), "reference synchronize");
     return TVLBM_OK;
@@ -467,6 +479,15 @@ int tvlbm_set_reference_refresh(tvlbm_ctx* c, int every) {
     }
     c->ref_every = every;
     c->ref_count = 0;
+    return TVLBM_OK;
+}
+
+int tvlbm_set_reference_kind(tvlbm_ctx* c, int kind) {
+    if (!c) return TVLBM_EINVAL;
+    if (kind != TVLBM_REF_EQUILIBRIUM && kind != TVLBM_REF_MEAN) return fail(c, TVLBM_EINVAL, "unknown reference kind %d", kind);
+    const int rc = rows_applicable(c);
+    if (rc) return rc;
+    c->ref_kind = kind;
     return TVLBM_OK;
 }
 

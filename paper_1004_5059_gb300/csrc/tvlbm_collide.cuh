@@ -186,4 +186,141 @@ __device__ __forceinline__ void cell_collide_dev(float (&s)[N1 * N1], const KPar
     }
 }
 
+// Collision for full FP32 populations.  s holds the gathered s_l = f_l - Whi_l, the population
+// less the float Whi_l of its rest value w_l (exact while f_l stays within a factor 2 of it), and
+// leaves holding f*_l.  The collision takes the state for f'_l = f_l + (w_l - Whi_l): a constant
+// offset per velocity, which streaming carries over unchanged (it is uniform in space), so the
+// stored f differs from the evolved f' by that fixed offset of ~3e-8 w only and no constant has
+// to be subtracted from a freshly rounded sum (which would round the same way in every cell).
+// With f_eq(f')_l = w_l (1 + e_l), e_l = (rho - 1) + rho phi_l - c_l, the BGK update of f' is
+//     f*_l = Whi_l + [(1 - omega) s_l + w_l omega e_l],
+// the deviation collision of cell_collide_dev (rho0 = 1) scaled by the weights: every rounding
+// but the final addition of Whi_l is relative to the small bracket, and w_l omega e_l takes the
+// exact weight as Whi_l + Wlo_l (no weight-rounding pattern that follows the flow).  With
+// omega = 0 the bracket is s_l exactly, so collisionless streaming stays a bit-exact copy.
+// Moments of f' are plain sums: rho - 1 = sum s, rho u = sum c s, D rho (T - 1) + rho u^2 =
+// sum |c|^2 s - D sum s (its rest part taken at the exact moments 1, 0, D, as the deviation
+// collision takes rho0 w).  The FP32 node tables' defects are cancelled to first order as in
+// cell_collide_dev (dSx, dUx, dVSx: the defects of the exact weights with the float xf, x2f and
+// E tables; the rest part's energy defect under the float x2f enters through dVSx[0], as the
+// (rho - rho0) part's does there).
+template <int N1>
+__device__ __forceinline__ void cell_collide_split(float (&s)[N1 * N1], const KParams& p, float om) {
+    constexpr int N = N1 - 1, H = N1 / 2;
+    constexpr bool ODD = (N1 & 1) != 0;
+    float rr[N1], rx[N1], rxx[N1];
+#pragma unroll
+    for (int j = 0; j < N1; ++j) {
+        float r = 0.f, x1 = 0.f, x2 = 0.f;
+#pragma unroll
+        for (int i = 0; i < H; ++i) {
+            const int m = N1 - 1 - i;
+            const float a = s[i + N1 * j] + s[m + N1 * j];
+            const float b = s[i + N1 * j] - s[m + N1 * j];
+            r += a;
+            x1 = fmaf(p.xf[i], b, x1);
+            x2 = fmaf(p.x2f[i], a, x2);
+        }
+        if (ODD) r += s[H + N1 * j];
+        rr[j] = r;
+        rx[j] = x1;
+        rxx[j] = x2;
+    }
+    float m0 = 0.f, mx = 0.f, my = 0.f, me = 0.f;
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+        const int m = N1 - 1 - j;
+        const float a = rr[j] + rr[m];
+        m0 += a;
+        my = fmaf(p.xf[j], rr[j] - rr[m], my);
+        mx += rx[j] + rx[m];
+        me = fmaf(p.x2f[j], a, me + (rxx[j] + rxx[m]));
+    }
+    if (ODD) {
+        m0 += rr[H];
+        mx += rx[H];
+        me += rxx[H];
+    }
+    const float rho = 1.f + m0;
+    const float inv = __frcp_rn(rho);
+    const float ux = mx * inv, uy = my * inv;
+    const float th = 0.5f * ((me - 2.0f * m0) * inv - (ux * ux + uy * uy));
+
+    float hx[N + 1], hy[N + 1];
+    hx[0] = hy[0] = 1.f;
+    hx[1] = ux;
+    hy[1] = uy;
+#pragma unroll
+    for (int n = 1; n < N; ++n) {
+        hx[n + 1] = fmaf(ux, hx[n], (float)n * th * hx[n - 1]);
+        hy[n + 1] = fmaf(uy, hy[n], (float)n * th * hy[n - 1]);
+    }
+
+    // first-order cancellation of the float node tables' defects
+    float Dm = 2.f * p.dSx[0] * m0, De = 2.f * m0 * p.dVSx[0];
+    float Dx = rho * ux * p.dUSx, Dy = rho * uy * p.dUSx;
+#pragma unroll
+    for (int a = 2; a <= N; a += 2) {
+        const float hs = rho * (hx[a] + hy[a]);
+        Dm = fmaf(p.dSx[a], hs, Dm);
+        De = fmaf(p.dVSx[a], hs, De);
+    }
+#pragma unroll
+    for (int a = 3; a <= N; a += 2) {
+        Dx = fmaf(rho * p.dUx[a], hx[a], Dx);
+        Dy = fmaf(rho * p.dUx[a], hy[a], Dy);
+    }
+#pragma unroll
+    for (int b = 2; b <= N - 1; b += 2) {
+        Dx = fmaf(rho * ux * p.dSx[b], hy[b], Dx);
+        Dy = fmaf(rho * uy * p.dSx[b], hx[b], Dy);
+    }
+#pragma unroll
+    for (int b = 2; b <= N - 2; b += 2) De = fmaf(rho * p.dSx[b], fmaf(hx[2], hy[b], hy[2] * hx[b]), De);
+    const float G = 0.5f * De - Dm;
+    const float orho = om * rho;
+
+    // per-node tables as in cell_collide_dev: omega e_ij = A_i + B_j + sum_a X'_ia P_j,N-a
+    float A[N1], B[N1], Xp[N1][N > 1 ? N : 1], P[N1][N + 1];
+#pragma unroll
+    for (int i = 0; i < (ODD ? H + 1 : H); ++i) {
+        const int m = N1 - 1 - i;
+        float se = 0.f, so = 0.f, pe = 0.f, po = 0.f;
+#pragma unroll
+        for (int a = 1; a <= N; ++a) {
+            const float xa = hx[a] * p.Ef[i][a];
+            const float ya = hy[a] * p.Ef[i][a];
+            if (a & 1) { so += xa; po += ya; } else { se += xa; pe += ya; }
+            P[i][a] = pe + po;
+            P[m][a] = pe - po;
+            if (a < N) {
+                Xp[i][a] = orho * xa;
+                Xp[m][a] = (a & 1) ? -Xp[i][a] : Xp[i][a];
+            }
+        }
+        const float cx2 = 0.5f * G * p.x2f[i];
+        const float ci = fmaf(Dx, p.xf[i], cx2), cim = fmaf(-Dx, p.xf[i], cx2);
+        const float cj = fmaf(Dy, p.xf[i], cx2), cjm = fmaf(-Dy, p.xf[i], cx2);
+        A[i] = fmaf(orho, se + so, -om * ci);
+        A[m] = fmaf(orho, se - so, -om * cim);
+        B[i] = fmaf(orho, P[i][N], -om * cj);
+        B[m] = fmaf(orho, P[m][N], -om * cjm);
+    }
+    const float wdr = om * (m0 - (Dm - G));
+    const float keep = 1.f - om;
+#pragma unroll
+    for (int j = 0; j < N1; ++j) {
+        const float bj = B[j] + wdr;
+#pragma unroll
+        for (int i = 0; i < N1; ++i) {
+            const int l = i + N1 * j;
+            float weq = A[i] + bj;
+#pragma unroll
+            for (int a = 1; a < N; ++a) weq = fmaf(Xp[i][a], P[j][N - a], weq);
+            const float t = fmaf(keep, s[l], fmaf(p.Whi[l], weq, p.Wlo[l] * weq));
+            s[l] = p.Whi[l] + t;
+        }
+    }
+}
+
 }  // namespace tvlbm

@@ -39,8 +39,9 @@ struct tvlbm_ctx {
     double* ref_new_d;                //   the pair the next reference is built in,
     float* ref_new_f;
     float* ref_delta;                 //   the re-encoding shifts [rows][kMaxQ]
-    double* ref_prof;                 //   and the profile [3][ny] (ux, uy, T)
+    double* ref_prof;                 //   and the profile ([3][ny] (ux, uy, T), or [Q][ny] Pref)
     int ref_every, ref_count;         // refresh period in steps (0: off), steps since the last refresh
+    int ref_kind;                     // what a refresh installs: TVLBM_REF_EQUILIBRIUM or TVLBM_REF_MEAN
     cudaGraphExec_t cl_graph[2];      // learned coarse steps: two steps per graph, by start parity
     unsigned long long cl_key_net;    // the network and constants the graphs were captured with
     float cl_key[24];

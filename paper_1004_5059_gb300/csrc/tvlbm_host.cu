@@ -283,8 +283,41 @@ void fill_kparams(KParams& p, const Rule& r, int N, double dt, double tau, doubl
     p.dUS = (float)((long double)p.dU[1] + p.dS[0]);
     for (int a = 0; a < kMaxN1; ++a)
         p.dVS[a] = (float)((long double)p.dV[a] + p.dS[a] + (a == 2 ? (long double)p.dS[0] : 0.0L));
+    // Full-f FP32 codec: exact weights as float pairs, and the defects of the float node tables
+    // (xf, x2f, E) under the exact weights (long double sums of the FP64 weights times floats).
+    for (int l = 0; l < kMaxQ; ++l) p.Whi[l] = p.Wlo[l] = 0.0f;
+    for (int j = 0; j < r.n; ++j)
+        for (int i = 0; i < r.n; ++i) {
+            const double w = r.w[i] * r.w[j];
+            const int l = i + r.n * j;
+            p.Whi[l] = (float)w;
+            p.Wlo[l] = (float)(w - (double)p.Whi[l]);
+        }
+    for (int a = 0; a < kMaxN1; ++a) p.dSx[a] = p.dUx[a] = p.dVSx[a] = 0.0f;
+    for (int a = 0; a <= N; ++a) {
+        long double S = 0, U = 0, V = 0;
+        for (int i = 0; i < r.n; ++i) {
+            const long double w = r.w[i];
+            S += w * p.Ef[i][a];
+            U += w * p.xf[i] * p.Ef[i][a];
+            V += w * p.x2f[i] * p.Ef[i][a];
+        }
+        const long double dSx = S - (a == 0 ? 1.0L : 0.0L);
+        p.dSx[a] = (float)dSx;
+        p.dUx[a] = (float)(U - (a == 1 ? 1.0L : 0.0L));
+        p.dVSx[a] = (float)(V - (a == 0 ? 1.0L : 0.0L) - (a == 2 ? 1.0L : 0.0L) + dSx);
+    }
+    for (int a = 0; a <= N; ++a)
+        if (a == 2) p.dVSx[a] = (float)((long double)p.dVSx[a] + p.dSx[0]);
+    p.dUSx = (float)((long double)p.dUx[1] + p.dSx[0]);
     p.omegad = dt / tau;
     p.omegaf = (float)p.omegad;
+    if (p.omegad == 0.0) {
+        // collisionless (tau = inf): f* is the gathered f itself, so the full-f FP32 codec splits
+        // nothing off and an integer shift stays a bit-exact copy even where a population is
+        // beyond a factor 2 of its rest value (where f - Whi rounds)
+        for (int l = 0; l < kMaxQ; ++l) p.Whi[l] = p.Wlo[l] = 0.0f;
+    }
     p.rho0d = rho0;
     p.rho0f = (float)rho0;
     p.nx = nx;

@@ -27,7 +27,7 @@ constexpr int kTileConfigs = 4;  // tile shapes of the tiled form
 constexpr int kFlowDone = 16;    // first per-tile counter in the dataflow scratch (64-byte aligned)
 // Per-row deviation reference tables (KParams::rowf / rowd): entries per stored row and the
 // offsets of the float table's fields.
-constexpr int kRowD = kMaxQ + 4;   // doubles per row: Pref_l, jref (2), eref
+constexpr int kRowD = kMaxQ + 4;   // doubles per row: Pref_l, jref (2), eref, rref
 constexpr int kRowF = kMaxQ + 12;  // floats per row: C_l, S moments (4), jref (2), eref, refD (4)
 constexpr int kRowSM = kMaxQ, kRowJ = kMaxQ + 4, kRowE = kMaxQ + 6, kRowRD = kMaxQ + 7;
 static_assert(kMaxQ % 4 == 0 && kRowF % 4 == 0, "row entries are read as float4");
@@ -55,6 +55,14 @@ struct KParams {
     // combinations of those defects the FP32 collision uses directly: dUS = dU[1] + dS[0],
     // dVS[a] = dV[a] + dS[a] (+ dS[0] for a = 2, the h_2 term of the energy defect)
     float dUS, dVS[kMaxN1];
+    // Full-f FP32 codec (cell_collide_split): the FP64 weight w_l = w_i w_j of velocity
+    // l = i + n j as a float pair Whi_l + Wlo_l (Whi = float(w_l), Wlo = float(w_l - Whi)), and
+    // the defects of the FP32 node tables under the exact weights, whose moment sums are
+    // unweighted (constants xf, x2f): dSx[a] = sum_i w_i E_ia - [a=0], dUx[a] = sum_i w_i xf_i E_ia
+    // - [a=1], dVSx[a] = sum_i w_i x2f_i E_ia - [a=0] - [a=2] + dSx[a] (+ dSx[0] for a = 2),
+    // dUSx = dUx[1] + dSx[0].
+    float Whi[kMaxQ], Wlo[kMaxQ];
+    float dSx[kMaxN1], dUx[kMaxN1], dUSx, dVSx[kMaxN1];
     int sh[kMaxN1];
     float omegaf, rho0f;
     double omegad, rho0d;
@@ -86,9 +94,12 @@ struct KParams {
     // - R_l(y) (exact: R is constant in x).  The FP32 collision takes the moments of S and, after
     // relaxing, adds C_l(y) = (1 - omega) S_l(y) - omega Pref_l(y) (the shift kept by the BGK
     // update and the row reference's own equilibrium deviation).
-    //   rowd[r * kRowD + l]: Pref_l; [kMaxQ + 0..1]: jref; [kMaxQ + 2]: eref
+    //   rowd[r * kRowD + l]: Pref_l; [kMaxQ + 0..1]: jref; [kMaxQ + 2]: eref; [kMaxQ + 3]: rref, the
+    //   reference's mass beyond rho0 (0 for an equilibrium of density rho0; a reference taken from
+    //   the rows' mean populations has the rows' own density)
     //   rowf[r * kRowF + l]: C_l; [kRowSM + 0..3]: FP32-constant moments (m0, mx, my, me) of S;
     //   [kRowJ + 0..1]: jref; [kRowE]: eref; [kRowRD + 0..3]: refD of the row's float Pref
+    //   (the S mass entry includes rref)
     const float* rowf;
     const double* rowd;
     // Device status word: bit 0 is set by a kernel whose bounded wait gave up.
@@ -182,31 +193,41 @@ template <class R> __device__ __forceinline__ R kinvden(const KParams& p, int si
 // reference, see KParams).  Sweep arithmetic runs
 // in "storage space" (the stored quantity), so the gather and the BGK update are linear in
 // what is loaded and stored; moments and equilibrium know which space they are in.
+// split: a full FP32 codec whose sweep gathers and collides f_l - Whi_l (exact for a population
+// within a factor 2 of its rest value), so that no rounding but the store's is relative to f
+// itself (cell_collide_split).
 struct CodecF64 {
-    using T = double; using R = double; static constexpr bool dev = false;
+    using T = double; using R = double; static constexpr bool dev = false, split = false;
     __device__ static R ld(const T* p) { return __ldg(p); }
     __device__ static T enc(R v) { return v; }
 };
 struct CodecF32 {
-    using T = float; using R = float; static constexpr bool dev = false;
+    using T = float; using R = float; static constexpr bool dev = false, split = true;
     __device__ static R ld(const T* p) { return __ldg(p); }
     __device__ static T enc(R v) { return v; }
 };
 struct CodecF32Dev {
-    using T = float; using R = float; static constexpr bool dev = true;
+    using T = float; using R = float; static constexpr bool dev = true, split = false;
     __device__ static R ld(const T* p) { return __ldg(p); }
     __device__ static T enc(R v) { return v; }
 };
 struct CodecBF16Dev {
-    using T = __nv_bfloat16; using R = float; static constexpr bool dev = true;
+    using T = __nv_bfloat16; using R = float; static constexpr bool dev = true, split = false;
     __device__ static R ld(const T* p) { return __bfloat162float(__ldg(p)); }
     __device__ static T enc(R v) { return __float2bfloat16_rn(v); }
 };
 struct CodecF16Dev {
-    using T = __half; using R = float; static constexpr bool dev = true;
+    using T = __half; using R = float; static constexpr bool dev = true, split = false;
     __device__ static R ld(const T* p) { return __half2float(__ldg(p)); }
     __device__ static T enc(R v) { return __float2half_rn(v); }
 };
+
+// f_l - Whi_l, the population less the float of its rest value (split codecs; exact by
+// Sterbenz's lemma for v within a factor 2 of Whi_l).
+template <class C>
+__device__ __forceinline__ typename C::R split_rest(const KParams& p, int l, typename C::R v) {
+    if constexpr (C::split) return v - p.Whi[l]; else return v;
+}
 
 // Storage value -> f_l and back, in precision R (used off the hot path: init, moments,
 // reductions, walls); ref = R_l, the deviation reference of velocity l.
@@ -221,10 +242,11 @@ __device__ __forceinline__ R from_f(R f, R w, R ref) { if constexpr (C::dev) ret
 // with D = 2.  In deviation space f = w (R + d) with R the reference's f_eq / w, whose moments
 // are (rho0, rho0 u_ref, rho0 (D T_ref + u_ref^2)) by exact quadrature, so rho = rho0 + sum w d,
 // rho u = jref + sum w c d, and T - 1 = ((eref + sum w |c|^2 d - D sum w d)/rho - u^2)/D.
-// ref3: the cell row's reference moments (jref_x, jref_y, eref) of a per-row reference, or null.
+// ref4: the cell row's reference moments (jref_x, jref_y, eref, rref) of a per-row reference, or
+// null; rref is the reference's mass beyond rho0 (rho = rho0 + rref + sum w d).
 template <int N1, bool DEV, class R>
 __device__ __forceinline__ void cell_moments(const R (&s)[N1 * N1], const KParams& p, R& rho, R& ux, R& uy, R& th,
-                                             const R* ref3 = nullptr) {
+                                             const R* ref4 = nullptr) {
     R m0 = 0, mx = 0, my = 0, me = 0;
 #pragma unroll
     for (int j = 0; j < N1; ++j) {
@@ -245,11 +267,12 @@ __device__ __forceinline__ void cell_moments(const R (&s)[N1 * N1], const KParam
         me = fma(wj, fma(kx2<R>(p, j), r, rxx), me);
     }
     if constexpr (DEV) {
+        if (ref4) m0 += ref4[3];
         rho = krho0<R>(p) + m0;
         const R inv = R(1) / rho;
-        ux = ((ref3 ? ref3[0] : kjref<R>(p, 0)) + mx) * inv;
-        uy = ((ref3 ? ref3[1] : kjref<R>(p, 1)) + my) * inv;
-        th = R(0.5) * (((ref3 ? ref3[2] : keref<R>(p)) + me - R(2) * m0) * inv - (ux * ux + uy * uy));
+        ux = ((ref4 ? ref4[0] : kjref<R>(p, 0)) + mx) * inv;
+        uy = ((ref4 ? ref4[1] : kjref<R>(p, 1)) + my) * inv;
+        th = R(0.5) * (((ref4 ? ref4[2] : keref<R>(p)) + me - R(2) * m0) * inv - (ux * ux + uy * uy));
     } else {
         rho = m0;
         const R inv = R(1) / rho;
@@ -417,6 +440,10 @@ struct KernelTable {
     cudaError_t (*row_means)(int storage, const void* f, double* prof, const KParams& p, cudaStream_t s);
     // per-row reference tables (KParams::rowd / rowf layout, p.rows rows) of the profile prof [3][ny]
     cudaError_t (*ref_tables)(const double* prof, double* rowd, float* rowf, const KParams& p, cudaStream_t s);
+    // row averages of Pref_l + d_l per velocity of buffer f into prof [Q][ny] (deviation storage)
+    cudaError_t (*row_pop_means)(int storage, const void* f, double* prof, const KParams& p, cudaStream_t s);
+    // per-row reference tables whose Pref is the profile prof [Q][ny] itself
+    cudaError_t (*ref_tables_mean)(const double* prof, double* rowd, float* rowf, const KParams& p, cudaStream_t s);
 };
 
 const KernelTable* kernel_table_q3();

@@ -39,8 +39,8 @@ __global__ void __launch_bounds__(256) sweep_plain_kernel(const typename C::T* _
             const T* b = fin + (long long)(i + N1 * j) * p.plane + (long long)ys * p.pitch + xs;
             const R v00 = C::ld(b), v01 = C::ld(b - 1);
             const R v10 = C::ld(b - p.pitch), v11 = C::ld(b - p.pitch - 1);
-            const R r0 = fma(ax, v01 - v00, v00);
-            const R r1 = fma(ax, v11 - v10, v10);
+            const R r0 = fma(ax, v01 - v00, split_rest<C>(p, i + N1 * j, v00));
+            const R r1 = fma(ax, v11 - v10, split_rest<C>(p, i + N1 * j, v10));
             s[i + N1 * j] = fma(ay, r1 - r0, r0);
         }
     }
@@ -90,10 +90,10 @@ __global__ void moments_kernel(const typename C::T* __restrict__ f, double* __re
     for (int l = 0; l < Q; ++l) s[l] = (double)C::ld(f + sidx(p, l, x, y));
     double rho, ux, uy, th;
     if (p.rowd) {
-        double ref3[3];
+        double ref4[4];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) ref3[k] = ld_row(p.rowd + (long long)(y + HY) * kRowD + kMaxQ + k);
-        cell_moments<N1, C::dev, double>(s, p, rho, ux, uy, th, ref3);
+        for (int k = 0; k < 4; ++k) ref4[k] = ld_row(p.rowd + (long long)(y + HY) * kRowD + kMaxQ + k);
+        cell_moments<N1, C::dev, double>(s, p, rho, ux, uy, th, ref4);
     } else {
         cell_moments<N1, C::dev, double>(s, p, rho, ux, uy, th);
     }
@@ -326,16 +326,16 @@ __global__ void __launch_bounds__(256) row_means_kernel(const typename C::T* __r
     __shared__ double sh[3][256];
     const int y = blockIdx.x, t = threadIdx.x;
     const bool rows = p.rowd != nullptr;
-    R ref3[3] = {R(0), R(0), R(0)};
+    R ref4[4] = {R(0), R(0), R(0), R(0)};
     if (rows)
-        for (int k = 0; k < 3; ++k) ref3[k] = (R)ld_row(p.rowd + (long long)(y + HY) * kRowD + kMaxQ + k);
+        for (int k = 0; k < 4; ++k) ref4[k] = (R)ld_row(p.rowd + (long long)(y + HY) * kRowD + kMaxQ + k);
     double acc[3] = {0.0, 0.0, 0.0};
     for (int x = t; x < p.nx; x += blockDim.x) {
         R v[Q];
 #pragma unroll
         for (int l = 0; l < Q; ++l) v[l] = C::ld(f + sidx(p, l, x, y));
         R rho, ux, uy, th;
-        if (rows) cell_moments<N1, C::dev, R>(v, p, rho, ux, uy, th, ref3);
+        if (rows) cell_moments<N1, C::dev, R>(v, p, rho, ux, uy, th, ref4);
         else cell_moments<N1, C::dev, R>(v, p, rho, ux, uy, th);
         acc[0] += (double)ux;
         acc[1] += (double)uy;
@@ -388,6 +388,7 @@ __global__ void ref_rows_kernel(const double* __restrict__ prof, double* __restr
     d[kMaxQ] = p.rho0d * ux;
     d[kMaxQ + 1] = p.rho0d * uy;
     d[kMaxQ + 2] = p.rho0d * (2.0 * (T - 1.0) + ux * ux + uy * uy);
+    d[kMaxQ + 3] = 0.0;  // an equilibrium of density rho0: no mass beyond rho0
     fr[kRowJ] = (float)d[kMaxQ];
     fr[kRowJ + 1] = (float)d[kMaxQ + 1];
     fr[kRowE] = (float)d[kMaxQ + 2];
@@ -397,9 +398,77 @@ __global__ void ref_rows_kernel(const double* __restrict__ prof, double* __restr
     fr[kRowRD + 3] = (float)(-(me - (double)fr[kRowE]));
 }
 
+// Row averages of the stored populations themselves, per velocity: prof[l][y] = mean over x of
+// Pref_l(y) + d_l(x, y), i.e. of f_l / w_l - rho0 (the reference the "mean" kind installs).  One
+// block of 256 threads per (fluid row, velocity), values in the storage's arithmetic, sums in FP64
+// in a fixed order.
+template <int N1, class C>
+__global__ void __launch_bounds__(256) row_pop_means_kernel(const typename C::T* __restrict__ f, double* __restrict__ prof,
+                                                            const KParams p) {
+    __shared__ double sh[256];
+    const int y = blockIdx.x, l = blockIdx.y, t = threadIdx.x;
+    double acc = 0.0;
+    for (int x = t; x < p.nx; x += blockDim.x) acc += (double)C::ld(f + sidx(p, l, x, y));
+    sh[t] = acc;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (t < h) sh[t] += sh[t + h];
+        __syncthreads();
+    }
+    if (t == 0) prof[(long long)l * p.ny + y] = kPrefRow<double>(p, l, y) + sh[0] / p.nx;
+}
+
+// Reference entries of every stored row r from a per-velocity profile prof[l][y] of Pref (fluid
+// row y = r - HY clamped into the fluid; a row with a non-finite entry takes the default
+// reference): Pref_l, and the reference's moments beyond the rest state rho0 w in FP64 with the
+// exact weights, jref = sum w c Pref, eref = sum w |c|^2 Pref, rref = sum w Pref (a general
+// reference need not have density rho0); jref, eref and refD in the float table as in
+// ref_rows_kernel, refD's mass entry against rref.  One thread per row.
+template <int N1>
+__global__ void ref_rows_mean_kernel(const double* __restrict__ prof, double* __restrict__ rowd, float* __restrict__ rowf,
+                                     const KParams p) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= p.rows) return;
+    const int y = min(max(r - HY, 0), p.ny - 1);
+    bool ok = true;
+    for (int l = 0; l < N1 * N1; ++l) ok = ok && isfinite(prof[(long long)l * p.ny + y]);
+    double* d = rowd + (long long)r * kRowD;
+    float* fr = rowf + (long long)r * kRowF;
+    double rr = 0.0, jx = 0.0, jy = 0.0, e = 0.0;
+    double m = 0.0, mx = 0.0, my = 0.0, me = 0.0;
+    for (int j = 0; j < N1; ++j)
+        for (int i = 0; i < N1; ++i) {
+            const int l = i + N1 * j;
+            const double pr = ok ? prof[(long long)l * p.ny + y] : 0.0;
+            d[l] = pr;
+            const double w = p.wd[i] * p.wd[j];
+            rr += w * pr;
+            jx += w * p.xd[i] * pr;
+            jy += w * p.xd[j] * pr;
+            e += w * (p.xd[i] * p.xd[i] + p.xd[j] * p.xd[j]) * pr;
+            const double v = (double)(float)pr;
+            m += (double)p.wf[i] * p.wf[j] * v;
+            mx += (double)p.wxf[i] * p.wf[j] * v;
+            my += (double)p.wf[i] * p.wxf[j] * v;
+            me += ((double)p.wx2f[i] * p.wf[j] + (double)p.wf[i] * p.wx2f[j]) * v;
+        }
+    d[kMaxQ] = jx;
+    d[kMaxQ + 1] = jy;
+    d[kMaxQ + 2] = e;
+    d[kMaxQ + 3] = rr;
+    fr[kRowJ] = (float)jx;
+    fr[kRowJ + 1] = (float)jy;
+    fr[kRowE] = (float)e;
+    fr[kRowRD] = (float)(-(m - rr));
+    fr[kRowRD + 1] = (float)(-(mx - (double)fr[kRowJ]));
+    fr[kRowRD + 2] = (float)(-(my - (double)fr[kRowJ + 1]));
+    fr[kRowRD + 3] = (float)(-(me - (double)fr[kRowE]));
+}
+
 // Gather shift of every fluid row from the FP64 Pref table (the sources of row y lie within FILL
-// rows of it): C_l = (1 - omega) S_l - omega Pref_l and the FP32-constant moments of float(S).
-// Ghost rows collide nowhere and get zeros.  One thread per stored row.
+// rows of it): C_l = (1 - omega) S_l - omega Pref_l and the FP32-constant moments of float(S), the
+// mass entry with the row reference's rref added.  Ghost rows collide nowhere and get zeros.  One
+// thread per stored row.
 template <int N1>
 __global__ void ref_shift_kernel(const double* __restrict__ rowd, float* __restrict__ rowf, const KParams p) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -429,7 +498,9 @@ __global__ void ref_shift_kernel(const double* __restrict__ rowd, float* __restr
             me += ((double)p.wx2f[i] * p.wf[j] + (double)p.wf[i] * p.wx2f[j]) * v;
         }
     for (int l = N1 * N1; l < kMaxQ; ++l) fr[l] = 0.0f;
-    fr[kRowSM] = (float)m;
+    // the row reference's own mass beyond rho0 (zero for an equilibrium reference) joins the
+    // shift's: the collision's rho - rho0 is their sum plus the gathered deviations' mass
+    fr[kRowSM] = (float)(m + rowd[(long long)r * kRowD + kMaxQ + 3]);
     fr[kRowSM + 1] = (float)mx;
     fr[kRowSM + 2] = (float)my;
     fr[kRowSM + 3] = (float)me;
@@ -562,9 +633,24 @@ struct Launch {
     static cudaError_t row_means(int storage, const void* f, double* prof, const KParams& p, cudaStream_t s) {
         TVLBM_DISPATCH(row_means_c, (f, prof, p, s))
     }
+    template <class C>
+    static cudaError_t row_pop_means_c(const void* f, double* prof, const KParams& p, cudaStream_t s) {
+        if constexpr (!C::dev) return cudaErrorInvalidValue;
+        row_pop_means_kernel<N1, C><<<dim3(p.ny, N1 * N1), 256, 0, s>>>((const typename C::T*)f, prof, p);
+        return cudaGetLastError();
+    }
+    static cudaError_t row_pop_means(int storage, const void* f, double* prof, const KParams& p, cudaStream_t s) {
+        TVLBM_DISPATCH(row_pop_means_c, (f, prof, p, s))
+    }
     static cudaError_t ref_tables(const double* prof, double* rowd, float* rowf, const KParams& p, cudaStream_t s) {
         const int blocks = (p.rows + 127) / 128;
         ref_rows_kernel<N1><<<blocks, 128, 0, s>>>(prof, rowd, rowf, p);
+        ref_shift_kernel<N1><<<blocks, 128, 0, s>>>(rowd, rowf, p);
+        return cudaGetLastError();
+    }
+    static cudaError_t ref_tables_mean(const double* prof, double* rowd, float* rowf, const KParams& p, cudaStream_t s) {
+        const int blocks = (p.rows + 127) / 128;
+        ref_rows_mean_kernel<N1><<<blocks, 128, 0, s>>>(prof, rowd, rowf, p);
         ref_shift_kernel<N1><<<blocks, 128, 0, s>>>(rowd, rowf, p);
         return cudaGetLastError();
     }
@@ -592,7 +678,8 @@ struct Launch {
 
     static const KernelTable* table() {
         static const KernelTable t = {&sweep, &init, &moments, &reduce, &wall, &halo, &decode, &encode, &tiled_available,
-                                      &box, &shape, &reencode, &flow, &batch, &row_means, &ref_tables};
+                                      &box, &shape, &reencode, &flow, &batch, &row_means, &ref_tables,
+                                      &row_pop_means, &ref_tables_mean};
         return &t;
     }
 };

@@ -136,6 +136,7 @@ __device__ __forceinline__ void collide_cell(typename C::R (&s)[N1 * N1], const 
         if constexpr (ROWS) cell_collide_dev<N1, true>(s, p, g.omegaf, p.rowf + (long long)(y + HY) * kRowF);
         else cell_collide_dev<N1, false>(s, p, g.omegaf, nullptr);
     }
+    else if constexpr (C::split) cell_collide_split<N1>(s, p, g.omegaf);
     else if constexpr (std::is_same<typename C::R, double>::value) cell_collide<N1, false, double>(s, p, g.omegad);
     else cell_collide<N1, false, float>(s, p, g.omegaf);
 }
@@ -247,7 +248,7 @@ __device__ __forceinline__ void tile_compute(const unsigned char* base, int x0, 
         for (int i = 0; i < N1; ++i) {
             const unsigned char* q = wrow + (i + N1 * j) * WIN + off[i];
             const R a = lds<C>(q + ES), b = lds<C>(q);
-            hprev[i + N1 * j] = fma(ka<R>(p, i), b - a, a);
+            hprev[i + N1 * j] = fma(ka<R>(p, i), b - a, split_rest<C>(p, i + N1 * j, a));
         }
 #pragma unroll 1
     for (int kk = 0; kk < RR; ++kk) {
@@ -261,7 +262,7 @@ __device__ __forceinline__ void tile_compute(const unsigned char* base, int x0, 
                 const int l = i + N1 * j;
                 const unsigned char* q = wrow + l * WIN + off[i];
                 const R a = lds<C>(q + ES), b = lds<C>(q);
-                const R h = fma(ka<R>(p, i), b - a, a);
+                const R h = fma(ka<R>(p, i), b - a, split_rest<C>(p, i + N1 * j, a));
                 s[l] = fma(ay, hprev[l] - h, h);
                 hprev[l] = h;
             }

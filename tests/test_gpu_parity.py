@@ -139,11 +139,10 @@ def test_integer_shift_bit_exact(tv, storage, walls):
 # FP32 and half-deviation storage against the FP64 oracle
 # ---------------------------------------------------------------------------------------------
 
-# FP32 populations are stored as scaled deviations (fp32_dev) in the shipped form: bar 1e-5.
-# Raw f in FP32 with the straightforward arithmetic (fp32) drifts by ~1e-8 per step (the float
-# quadrature tables miss their identities and the same rounding repeats every step); it is kept
-# as the plain baseline with a looser regression bound.
-FP32_BOUND = {"fp32_dev": 1e-5, "fp32": 1e-3}
+# FP32 storage, both forms, bar 1e-5: scaled deviations (fp32_dev, the shipped form) and raw f
+# (fp32, the plain form), whose arithmetic splits the rest populations off exactly so that only
+# the store rounds relative to f.
+FP32_BOUND = {"fp32_dev": 1e-5, "fp32": 1e-5}
 
 
 @pytest.mark.parametrize("storage", ["fp32", "fp32_dev"])
@@ -161,10 +160,12 @@ def test_c1_recipe_reduced_fp32(tv, storage, form):
     assert max(errs) < FP32_BOUND[storage], errs
 
 
-# Half-deviation storage after 1000 steps: FP16 (11-bit significand) with the storage reference at
-# the flow's mean state meets 1e-3 on the 96 x 64 walls case (measured 6.9e-4) and reaches 1.4e-3
-# on the 4096 x 512 channel; BF16 (8-bit significand) rounds 8x coarser (measured 1.6e-2).  The
-# bounds below are those measured levels with margin, so a regression shows.
+# Half-deviation storage after 1000 steps with ONE reference, the flow's mean state.  FP16
+# (11-bit significand) meets the 1e-3 bar on the 96 x 64 walls case (measured 6.9e-4).  These are
+# not the half-storage parity claims on the channel workload -- those take a per-row reference
+# (tests/test_gpu_reference_rows.py, bar 1e-3 for both FP16 and BF16) -- but regression checks of
+# the single-reference encoding at its measured levels with margin: on the 4096 x 512 channel FP16
+# reaches 1.4e-3, and BF16 (8-bit significand) rounds 8x coarser than FP16 (1.6e-2 measured).
 HALF_BOUND = {"fp16_dev": 1e-3, "bf16_dev": 3e-2}
 HALF_BOUND_C2 = {"fp16_dev": 2e-3, "bf16_dev": 3e-2}
 
@@ -194,10 +195,11 @@ def test_half_storage_walls_d2q36(tv, storage, form):
 
 
 @pytest.mark.parametrize("storage", ["bf16_dev", "fp16_dev"])
-def test_c2_thermal_couette_full_width(tv, storage):
+def test_c2_single_reference_regression(tv, storage):
     """4096 x 512 D2Q36 channel (walls T = 1.0 / 1.1, top wall u = 0.1, tau = 0.9), half
-    storage, 1000 steps.  The flow is x-invariant, so the oracle runs an 8 x 512 periodic strip
-    and every GPU column must match it."""
+    storage against one mean-state reference, 1000 steps (a regression check, see HALF_BOUND).
+    The flow is x-invariant, so the oracle runs an 8 x 512 periodic strip and every GPU column
+    must match it."""
     nx, ny, steps = 4096, 512, 1000
     walls = (0.0, 1.0, 0.1, 1.1)
     sim = tv.Simulation(nx, ny, "D2Q36", tau=0.9, walls=walls, storage=storage)
@@ -237,8 +239,7 @@ def test_c1_full_size_fp32(tv, storage, form):
     drift = (s1[:4] - s0[:4]) / s0[0]
     print("C1 1024^2 1000 steps", storage, form, "errors (rho, u, T):", errs, "drift (M, Px, Py, E)/M:", drift)
     assert max(errs) < FP32_BOUND[storage], errs
-    if storage == "fp32_dev":
-        assert np.all(np.abs(drift) < 1e-7), drift
+    assert np.all(np.abs(drift) < 1e-7), drift
 
 
 _C1_REF = {}
@@ -257,7 +258,7 @@ def _c1_reference(fields, steps):
 # Diagnostics, checkpoint, graphs
 # ---------------------------------------------------------------------------------------------
 
-@pytest.mark.parametrize("storage,tol", [("fp64", 1e-13), ("fp32", 1e-4), ("fp32_dev", 2e-8), ("fp16_dev", 1e-5)])
+@pytest.mark.parametrize("storage,tol", [("fp64", 1e-13), ("fp32", 1e-7), ("fp32_dev", 2e-8), ("fp16_dev", 1e-5)])
 def test_conservation_on_gpu(tv, storage, tol):
     n = 96
     sim = tv.Simulation(n, n, "D2Q16", tau=0.7, storage=storage)

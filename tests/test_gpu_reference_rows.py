@@ -81,8 +81,10 @@ def test_fp32_dev_matches_oracle(tv, velset, form):
 @pytest.mark.parametrize("form", ["plain", "tiled"])
 def test_half_storage_walls_d2q36(tv, storage, bound, form):
     """96 x 64, 1000 steps, the x-varying perturbation of the single-reference test (u and T
-    perturbed by 2 %, which the row reference does not follow: it dominates the deviations here,
-    so both references end at similar errors)."""
+    perturbed by 2 %, which no row reference follows: it dominates the deviations here, so both
+    references end at similar errors).  FP16 meets the 1e-3 bar; BF16's bound is a regression
+    check at its measured level (its 8-bit significand resolves a 2 % x-varying perturbation only
+    to ~1e-2), not a parity claim: BF16 parity is claimed on the channel workload below."""
     nx, ny = 96, 64
     fields = perturbed_couette(nx, ny, 8)
     want = oracle_run(nx, ny, "D2Q36", fields, 1000).moments()
@@ -95,44 +97,66 @@ def test_half_storage_walls_d2q36(tv, storage, bound, form):
     assert max(errs[True]) < bound, errs
 
 
-# (storage, refresh period, bound): with the start's profile held fixed (refresh 0) the top
-# wall's shear layer, where u climbs to 0.1 against u_ref = 0, dominates the FP16 u error; a
-# reference refreshed from the row averages follows it
-C2_CASES = [("fp16_dev", 100, 1e-3), ("fp16_dev", 0, 2e-3), ("bf16_dev", 100, 1e-2), ("bf16_dev", 0, 1e-2)]
+# The half-storage parity claims on the channel workload (bar 1e-3 after 1000 steps): the per-row
+# reference refreshed every 20 steps from the rows' mean populations (kind "mean"), which leaves
+# only the departures from the row averages in the stored deviations -- for both BF16 and FP16 --
+# and FP16 with the rows' mean equilibria refreshed every 100 steps.
+C2_PARITY = [("bf16_dev", 20, "mean"), ("fp16_dev", 20, "mean"), ("fp16_dev", 100, "equilibrium")]
+# Regression checks at measured levels with margin, not parity claims: with the start's profile
+# held fixed (refresh 0) the top wall's shear layer, where u climbs to 0.1 against u_ref = 0,
+# dominates the FP16 u error; BF16 against the rows' mean equilibria keeps their non-equilibrium
+# part in the deviations (4.1e-3 measured).
+C2_REGRESSION = [("fp16_dev", 0, "equilibrium", 2e-3), ("bf16_dev", 100, "equilibrium", 1e-2),
+                 ("bf16_dev", 0, "equilibrium", 1e-2)]
 
 
-@pytest.mark.parametrize("storage,refresh,bound", C2_CASES)
-def test_c2_channel_full_width(tv, storage, refresh, bound):
-    """4096 x 512 D2Q36 thermal Couette channel, tau = 0.9, 1000 steps (the tiled form the bench
-    times).  The flow is x-invariant, so the oracle runs an 8 x 512 strip; every column must
-    match it to the half-storage bar."""
-    nx, ny, steps = 4096, 512, 1000
+def c2_run(tv, storage, refresh, kind, steps=1000):
+    nx, ny = 4096, 512
     sim = tv.Simulation(nx, ny, "D2Q36", tau=0.9, walls=WALLS, storage=storage, form="tiled")
     sim.set_reference_rows(*couette_profile(ny))
     sim.init_moments(*workloads.couette_linear(nx, ny, WALLS[1], WALLS[3]))
-    sim.set_reference_refresh(refresh)
+    sim.set_reference_refresh(refresh, kind=kind)
     sim.step(steps)
     got = sim.moments()
     ref = oracle_run(8, ny, "D2Q36", workloads.couette_linear(8, ny, WALLS[1], WALLS[3]), steps)
     want = [np.broadcast_to(a[:, :1], (ny, nx)) for a in ref.moments()]
     errs = field_errors(got, want)
-    print("C2 4096x512 1000 steps row reference", storage, "refresh", refresh, "errors (rho, u, T):", errs)
-    assert max(errs) < bound, errs
     assert sim.conserved_sums()[4] == 0
     sim.close()
+    return errs
 
 
+@pytest.mark.parametrize("storage,refresh,kind", C2_PARITY)
+def test_c2_channel_full_width(tv, storage, refresh, kind):
+    """4096 x 512 D2Q36 thermal Couette channel, tau = 0.9, 1000 steps (the tiled form the bench
+    times).  The flow is x-invariant, so the oracle runs an 8 x 512 strip; every column must
+    match it to the half-storage bar 1e-3."""
+    errs = c2_run(tv, storage, refresh, kind)
+    print("C2 4096x512 1000 steps row reference", storage, kind, "refresh", refresh, "errors (rho, u, T):", errs)
+    assert max(errs) < 1e-3, errs
+
+
+@pytest.mark.parametrize("storage,refresh,kind,bound", C2_REGRESSION)
+def test_c2_channel_regression(tv, storage, refresh, kind, bound):
+    errs = c2_run(tv, storage, refresh, kind)
+    print("C2 4096x512 1000 steps (regression)", storage, kind, "refresh", refresh, "errors (rho, u, T):", errs)
+    assert max(errs) < bound, errs
+
+
+@pytest.mark.parametrize("kind", ["equilibrium", "mean"])
 @pytest.mark.parametrize("form,every", [("plain", 7), ("tiled", 7), ("tiled", 40)])
-def test_refresh_is_a_reencoding(tv, form, every):
+def test_refresh_is_a_reencoding(tv, form, every, kind):
     """FP32 deviation storage: a run whose reference is refreshed every 7 steps (single launches)
     or every 40 (a captured 32-step graph and single launches between refreshes) matches the
     oracle as tightly as one with a fixed reference; turning the refresh on without a row
-    reference takes the state's own row averages."""
+    reference takes the state's own row averages.  Kind "mean" takes the rows' mean
+    populations, whose density is the row's own (not rho0): the reference's mass enters the
+    collision's density and every diagnostic."""
     nx, ny, steps = 64, 48, 100
     fields = perturbed_couette(nx, ny, 44)
     sim = tv.Simulation(nx, ny, "D2Q36", tau=0.9, walls=WALLS, storage="fp32_dev", form=form)
     sim.init_moments(*fields)
-    sim.set_reference_refresh(every)
+    sim.set_reference_refresh(every, kind=kind)
     sim.step(steps)
     errs = field_errors(sim.moments(), oracle_run(nx, ny, "D2Q36", fields, steps).moments())
     print("refresh every", every, "steps fp32_dev", form, "errors (rho, u, T):", errs)
@@ -229,4 +253,25 @@ def test_rejections(tv):
     with pytest.raises(tv.TvlbmError):
         s.set_reference_refresh(10)
     s.set_reference_refresh(0)  # off is always accepted
+    with pytest.raises(tv.TvlbmError):
+        tv.tvlbm_set_reference_kind(s.ctx, tv.REFERENCE_KINDS["mean"])  # periodic
     s.close()
+    s = tv.Simulation(32, 32, "D2Q16", walls=WALLS, storage="bf16_dev")
+    with pytest.raises(tv.TvlbmError) as e:
+        tv.tvlbm_set_reference_kind(s.ctx, 7)
+    assert e.value.code == tv.TVLBM_EINVAL
+    s.close()
+
+
+def test_mass_conserved_mean_reference(tv):
+    """The mean-population reference carries each row's own density: refreshing it every 7 steps
+    (FP32 deviations) keeps the channel's mass to FP32 rounding over 500 steps."""
+    nx, ny = 64, 48
+    sim = tv.Simulation(nx, ny, "D2Q36", tau=0.9, walls=WALLS, storage="fp32_dev", form="tiled")
+    sim.init_moments(*perturbed_couette(nx, ny, 71))
+    s0 = sim.conserved_sums()
+    sim.set_reference_refresh(7, kind="mean")
+    sim.step(500)
+    s1 = sim.conserved_sums()
+    assert abs(s1[0] - s0[0]) <= 1e-6 * abs(s0[0]), (s0, s1)
+    sim.close()
