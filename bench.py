@@ -7,10 +7,13 @@ stream+collide sweep over the grid).  Inputs are resident in HBM when a timed st
 L2 is flushed (a 512 MiB write) between timed steps, outside the timed events.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload c1|c1_4096|c0|c2|c3|c4|fv] [--form tiled|flow|plain] [--no-cpu-baseline]
+                  [--workload c1|c1_4096|c0|c2|c2_bf16|c3|c4|fv] [--form tiled|flow|plain]
+                  [--no-cpu-baseline] [--no-extras]
 
-Prints one JSON line.  --impl reference times the FP64 CPU oracle on this machine's host
-cores on the same workload (each step a bounded sample of the time steps).  Under torchrun
+Prints one JSON line.  With the default workload the line also carries sub-records of the other
+configurations (4096^2 FP32, the 4096x512 channel in FP16 and BF16 deviations, the 256-domain
+batch), each timed on its own with its oracle check.  --impl reference times the FP64 CPU oracle
+on this machine's host cores on the same workload (each step a bounded sample of the time steps).  Under torchrun
 (N > 1) every rank advances its own replica of the workload (no data exchange) and the line
 reports the aggregate.
 """
@@ -44,8 +47,15 @@ WORKLOADS = {
                nx=64, ny=64, velset="D2Q16", storage="fp64", plain_storage="fp64", tau=0.8, walls=None, tsteps=200),
     "c2": dict(desc="D2Q36 4096x512 thermal Couette FP16-deviation storage tau=0.9, walls T=1.0/1.1, u_top=0.1, "
                     "1000 time steps", nx=4096, ny=512, velset="D2Q36", storage="fp16_dev", plain_storage="fp16_dev",
-               tau=0.9, walls=(0.0, 1.0, 0.1, 1.1), tsteps=1000, reference="rows", refresh=100),
+               tau=0.9, walls=(0.0, 1.0, 0.1, 1.1), tsteps=1000, reference="rows", refresh=20, ref_kind="mean"),
+    "c2_bf16": dict(desc="D2Q36 4096x512 thermal Couette BF16-deviation storage tau=0.9, walls T=1.0/1.1, "
+                         "u_top=0.1, 1000 time steps", nx=4096, ny=512, velset="D2Q36", storage="bf16_dev",
+                    plain_storage="bf16_dev", tau=0.9, walls=(0.0, 1.0, 0.1, 1.1), tsteps=1000, reference="rows",
+                    refresh=20, ref_kind="mean"),
 }
+
+# configurations measured beside the default line (their own sub-records in the JSON line)
+EXTRA = ("c1_4096", "c2", "c2_bf16", "c3")
 
 BATCH = dict(desc="256 independent periodic D2Q16 domains, sides drawn from {128,256,512,768,1024}, tau~U[0.55,1.5], "
                    "Mach~U[0.05,0.3], seeded fields, FP32 populations; one persistent launch per time step over all "
@@ -61,13 +71,23 @@ METRIC = "MLUPS (million lattice-cell updates per second) of the fused TVLBM swe
 UNIT = "MLUPS"
 
 
-def fields_for(name, w):
-    nx, ny = w["nx"], w["ny"]
+def fields_for(name, w, nx=None):
+    nx, ny = nx or w["nx"], w["ny"]
     if name.startswith("c1"):
         return workloads.gaussian_bump_random_flow(nx, ny, seed=1, sigma=64.0 * nx / 1024)
     if name == "c0":
         return workloads.shear_wave(nx, ny, eps=0.01)
     return workloads.couette_linear(nx, ny, 1.0, 1.1)
+
+
+def field_errors(got, want):
+    """Max relative errors of (rho, u, T), each against the field's own max |value| (u: both
+    components against max |u_ref|)."""
+    e_rho = float(np.max(np.abs(got[0] - want[0])) / np.max(np.abs(want[0])))
+    umax = max(np.max(np.abs(want[1])), np.max(np.abs(want[2])))
+    e_u = float(max(np.max(np.abs(got[1] - want[1])), np.max(np.abs(got[2] - want[2]))) / umax)
+    e_T = float(np.max(np.abs(got[3] - want[3])) / np.max(np.abs(want[3])))
+    return {"max_rel_err_rho": e_rho, "max_rel_err_u": e_u, "max_rel_err_T": e_T}
 
 
 def max_over_ranks(x, world, device):
@@ -204,18 +224,21 @@ def traffic_per_time_step(workload, form, tile=None):
     return b / d["%s/%s" % (workload, form)].get("time_steps_per_launch", 1)
 
 
-def run_ours(args, w, rank, world, local_rank):
+def run_ours(args, w, rank, world, local_rank, sub=None):
+    """The workload's bench line.  sub: the name of a configuration measured beside the default
+    line -- then only its timed sweep, roofline fraction and oracle check (no e2e, plain form or
+    process-group set-up), as a compact record."""
     import torch
     import paper_1004_5059_gb300 as tv
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    if world > 1:
+    if world > 1 and sub is None:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     nx, ny, tsteps = w["nx"], w["ny"], w["tsteps"]
     cells = nx * ny
-    fields = fields_for(args.workload, w)
+    fields = fields_for(sub or args.workload, w)
     stream = torch.cuda.current_stream(dev)
 
     def make(form, storage=None):
@@ -228,13 +251,13 @@ def run_ours(args, w, rank, world, local_rank):
             s.set_reference(*w["reference"])
         s.init_moments(*fields)
         if w.get("refresh") and (storage or w["storage"]).endswith("_dev"):
-            s.set_reference_refresh(w["refresh"])
+            s.set_reference_refresh(w["refresh"], kind=w.get("ref_kind"))
         return s
 
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
     def barrier():
-        if world > 1:
+        if world > 1 and sub is None:
             import torch.distributed as dist
             dist.barrier()
 
@@ -290,6 +313,8 @@ def run_ours(args, w, rank, world, local_rank):
     if probe is None:
         raise RuntimeError("no sweep form available for workload %s" % args.workload)
     probe.init_moments(*fields)
+    if sub is not None:
+        return sub_record(sub, w, probe, chosen, tuning, trials, timed, fields, tv)
     clocks = Clocks(local_rank)
     clocks.start()
     ms_total = timed(probe, args.steps, args.warmup)
@@ -303,7 +328,7 @@ def run_ours(args, w, rank, world, local_rank):
     value = aggregate_mlups(world, cells, tsteps, args.steps, ms_max / 1e3)
 
     # plain form beside the chosen one (the metric reports both)
-    plain = None
+    plain, sp = None, None
     if chosen != "plain" or w["plain_storage"] != w["storage"]:
         sp = make("plain", w["plain_storage"])
         kp = max(1, args.steps // 2)
@@ -311,7 +336,6 @@ def run_ours(args, w, rank, world, local_rank):
         plain_launch_s = msp / 1e3 / (kp * tsteps)
         plain = {"value": cells * tsteps * kp / (msp / 1e3) / 1e6, "unit": UNIT, "form": "plain",
                  "storage": w["plain_storage"], "bytes_per_cell": sp.bytes_per_cell(), "roofline_frac": None}
-        sp.close()
 
     # end to end through the C ABI with host buffers: init from pinned host fields (H2D),
     # run the time steps, read the moments back (D2H), every step
@@ -348,8 +372,11 @@ def run_ours(args, w, rank, world, local_rank):
         "data": "synthetic (seeded fields shaped like the paper's test problems)",
         "config": {"workload": w["desc"], "nx": nx, "ny": ny, "velset": w["velset"], "storage": w["storage"],
                    "tau": w["tau"], "time_steps_per_bench_step": tsteps, "form": chosen,
-                   "deviation_reference": ("per row: u = 0, T linear between the walls (the start), reset to the "
-                                           "row averages every %d steps inside the timed region" % w.get("refresh", 0)
+                   "deviation_reference": ("per row: the start's equilibria (u = 0, T linear between the walls), "
+                                           "reset every %d steps inside the timed region to the rows' %s" % (
+                                               w.get("refresh", 0),
+                                               "mean populations" if w.get("ref_kind") == "mean"
+                                               else "mean-state equilibria")
                                            if w.get("reference") == "rows" else w.get("reference")),
                    "tile": line_tile,
                    "autotune_us_per_time_step": trials or None,
@@ -372,8 +399,25 @@ def run_ours(args, w, rank, world, local_rank):
     if plain is not None:
         line["plain_form"] = plain
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.workload, w, fields, probe)
-    probe.close()
+        sims = {"chosen": probe}
+        if sp is not None:
+            sims["plain"] = sp
+        line["cpu_baseline"], acc = cpu_baseline(args.workload, w, fields, sims)
+        line["accuracy_vs_oracle"] = acc
+        if plain is not None and acc:
+            plain["max_rel_err_vs_oracle"] = acc["plain"]
+            plain["time_steps_checked"] = acc["time_steps"]
+    if sp is not None:
+        sp.close()
+    if rank == 0 and world == 1 and not args.no_extras and args.workload == "c1":
+        line["extra_keys"] = list(EXTRA)
+        probe.close()
+        probe = None
+        for name in EXTRA:
+            line[name] = (run_batch(args, rank, world, local_rank, sub=True) if name == "c3" else
+                          run_ours(args, WORKLOADS[name], rank, world, local_rank, sub=name))
+    if probe is not None:
+        probe.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -387,9 +431,12 @@ def _oracle_threads():
         return os.cpu_count() or 1
 
 
-def cpu_baseline(name, w, fields, sim=None, target_s=12.0):
-    """The FP64 oracle, as it stands, on this machine's host cores, over a bounded sample of the
-    workload's time steps (whole grid); also compares the GPU after the same number of steps."""
+def cpu_baseline(name, w, fields, sims=None, target_s=10.0):
+    """The FP64 oracle, as it stands, on this machine's host cores over a bounded sample of the
+    workload's time steps (whole grid), with all threads and with one; then the oracle continued
+    to the workload's full run (untimed) and every GPU form in `sims` run as far from the same
+    start, compared field by field.  A channel (x-invariant flow) is checked on an 8-column strip
+    of the oracle, every GPU column against it."""
     import oracle
     cores = _oracle_threads()
     o = oracle.Oracle(w["nx"], w["ny"], w["velset"], tau=w["tau"], dt=1.0, walls=w["walls"], threads=cores)
@@ -404,18 +451,91 @@ def cpu_baseline(name, w, fields, sim=None, target_s=12.0):
     out = {"value": w["nx"] * w["ny"] * n / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
            "sample": "%d of the workload's %d time steps on the full %dx%d grid (after 1 untimed step)" % (
                n, w["tsteps"], w["nx"], w["ny"])}
-    if sim is not None:
+    if cores > 1:
+        o1 = oracle.Oracle(w["nx"], w["ny"], w["velset"], tau=w["tau"], dt=1.0, walls=w["walls"], threads=1)
+        o1.init_moments(*fields)
+        t0 = time.perf_counter()
+        o1.run(1)
+        one1 = time.perf_counter() - t0
+        n1 = int(max(1, min(w["tsteps"], 0.4 * target_s / max(one1, 1e-6))))
+        t0 = time.perf_counter()
+        o1.run(n1)
+        dt1 = time.perf_counter() - t0
+        out["one_thread"] = {"value": w["nx"] * w["ny"] * n1 / dt1 / 1e6, "unit": UNIT, "cores": 1,
+                             "sample": "%d time steps on the full grid (after 1 untimed step)" % n1}
+        del o1
+    if not sims:
+        return out, None
+    if w["walls"]:
+        o = oracle.Oracle(8, w["ny"], w["velset"], tau=w["tau"], dt=1.0, walls=w["walls"], threads=cores)
+        o.init_moments(*[a[:, :8] for a in fields])
+        o.run(w["tsteps"])
+    else:
+        o.run(w["tsteps"] - 1 - n)
+    want = o.moments()
+    if w["walls"]:
+        want = [np.broadcast_to(a[:, :1], (w["ny"], w["nx"])) for a in want]
+    acc = {"time_steps": w["tsteps"]}
+    for label, sim in sims.items():
         sim.init_moments(*fields)
-        sim.step(n + 1)
-        got = sim.moments()
+        if w.get("refresh") and w["storage"].endswith("_dev"):
+            sim.set_reference_refresh(w["refresh"], kind=w.get("ref_kind"))  # restarts the refresh count
+        sim.step(w["tsteps"])
+        acc[label] = field_errors(sim.moments(), want)
+    return out, acc
+
+
+def sub_record(name, w, sim, form, tuning, trials, timed, fields, tv, K=3, W=2):
+    """Compact record of a configuration measured beside the default line: K timed bench steps
+    after W, MLUPS and the HBM roofline fraction, and the GPU against the oracle (a channel: after
+    the full run on an 8-column strip; a periodic grid: after a few time steps on the full grid)."""
+    import oracle
+    nx, ny, tsteps = w["nx"], w["ny"], w["tsteps"]
+    ms = timed(sim, K, W)
+    s_per_tstep = ms / 1e3 / (K * tsteps)
+    bpc = sim.bytes_per_cell()
+    peak, peak_kind = measured_peak_hbm()
+    achieved = bpc * nx * ny / s_per_tstep / 1e9
+    rec = {"workload": w["desc"], "value": nx * ny / s_per_tstep / 1e6, "unit": UNIT, "ms_per_step": ms / K,
+           "steps": K, "warmup": W, "form": form, "storage": w["storage"],
+           "tile": list(tv.tvlbm_tile_shape(sim.ctx, tuning["best"])) if tuning else None,
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                        "peak_kind": peak_kind, "bytes_per_cell": bpc,
+                        "traffic": kernel_traffic(name, form, list(tv.tvlbm_tile_shape(sim.ctx, tuning["best"]))
+                                                  if tuning else None)}}
+    if w.get("refresh"):
+        rec["deviation_reference"] = "per row, %s kind, refreshed every %d time steps inside the timed region" % (
+            w.get("ref_kind", "equilibrium"), w["refresh"])
+    cores = _oracle_threads()
+    if w["walls"]:
+        o = oracle.Oracle(8, ny, w["velset"], tau=w["tau"], dt=1.0, walls=w["walls"], threads=cores)
+        o.init_moments(*[a[:, :8] for a in fields])
+        t0 = time.perf_counter()
+        o.run(tsteps)
+        dt = time.perf_counter() - t0
+        checked = tsteps
+        want = [np.broadcast_to(a[:, :1], (ny, nx)) for a in o.moments()]
+        rec["cpu_baseline"] = {"value": 8 * ny * tsteps / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": "the full run of an 8x%d strip of the channel (the flow is x-invariant)" % ny}
+    else:
+        o = oracle.Oracle(nx, ny, w["velset"], tau=w["tau"], dt=1.0, walls=w["walls"], threads=cores)
+        o.init_moments(*fields)
+        checked = 3
+        t0 = time.perf_counter()
+        o.run(checked)
+        dt = time.perf_counter() - t0
         want = o.moments()
-        e_rho = float(np.max(np.abs(got[0] - want[0])) / np.max(np.abs(want[0])))
-        umax = max(np.max(np.abs(want[1])), np.max(np.abs(want[2])))
-        e_u = float(max(np.max(np.abs(got[1] - want[1])), np.max(np.abs(got[2] - want[2]))) / umax)
-        e_T = float(np.max(np.abs(got[3] - want[3])) / np.max(np.abs(want[3])))
-        out["gpu_vs_oracle_after_sample"] = {"time_steps": n + 1, "max_rel_err_rho": e_rho, "max_rel_err_u": e_u,
-                                             "max_rel_err_T": e_T}
-    return out
+        rec["cpu_baseline"] = {"value": nx * ny * checked / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": "%d time steps on the full grid" % checked}
+    sim.init_moments(*fields)
+    if w.get("refresh"):
+        sim.set_reference_refresh(w["refresh"], kind=w.get("ref_kind"))  # restarts the refresh count
+    sim.step(checked)
+    rec["accuracy_vs_oracle"] = dict(time_steps=checked, **field_errors(sim.moments(), want))
+    if trials:
+        rec["autotune_us_per_time_step"] = trials
+    sim.close()
+    return rec
 
 
 def run_reference(args, w, rank, world):
@@ -460,14 +580,16 @@ def batch_fields(spec):
     return workloads.gaussian_bump_random_flow(n, n, seed=spec["seed"], amp_u=spec["mach"], sigma=n / 16.0)
 
 
-def run_batch(args, rank, world, local_rank):
+def run_batch(args, rank, world, local_rank, sub=False):
+    """The batched workload's bench line; sub: a compact record measured beside the default line
+    (3 timed bench steps after 2, the roofline fraction, the smallest domains against the oracle)."""
     import torch
     import paper_1004_5059_gb300 as tv
     from paper_1004_5059_gb300 import autotune
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    if world > 1:
+    if world > 1 and not sub:
         import torch.distributed as dist
         dist.init_process_group("nccl")
     specs = workloads.batched_domains(BATCH["count"], seed=BATCH["seed"])
@@ -495,16 +617,17 @@ def run_batch(args, rank, world, local_rank):
         b.init_moments(d, *f)
     cells = b.cells()
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
-    for _ in range(args.warmup):
+    K, W = (3, 2) if sub else (args.steps, args.warmup)
+    for _ in range(W):
         b.step(tsteps)
     torch.cuda.synchronize()
-    if world > 1:
+    if world > 1 and not sub:
         import torch.distributed as dist
         dist.barrier()
     clocks = Clocks(local_rank)
     clocks.start()
     evs = []
-    for _ in range(args.steps):
+    for _ in range(K):
         flush.zero_()
         a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
@@ -514,9 +637,35 @@ def run_batch(args, rank, world, local_rank):
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = sum(a.elapsed_time(e) for a, e in evs)
+    peak, peak_kind = measured_peak_hbm()
+    if sub:
+        achieved = b.bytes_per_cell() * cells / (ms / 1e3 / (K * tsteps)) / 1e9
+        rec = {"workload": BATCH["desc"], "value": cells * tsteps * K / (ms / 1e3) / 1e6, "unit": UNIT,
+               "ms_per_step": ms / K, "steps": K, "warmup": W, "storage": BATCH["storage"], "domains": b.count,
+               "cells": cells, "tile": list(b.tile_shape(best)),
+               "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                            "frac": achieved / peak, "peak_kind": peak_kind, "bytes_per_cell": b.bytes_per_cell(),
+                            "traffic": None}}
+        # the 8 smallest domains after the bench step's time steps, against the oracle
+        import oracle
+        order = sorted(range(b.count), key=lambda d: specs[d]["n"])[:8]
+        for d in order:
+            b.init_moments(d, *fields[d])
+        b.step(tsteps)
+        worst = {"max_rel_err_rho": 0.0, "max_rel_err_u": 0.0, "max_rel_err_T": 0.0}
+        for d in order:
+            o = oracle.Oracle(specs[d]["n"], specs[d]["n"], BATCH["velset"], tau=specs[d]["tau"],
+                              threads=_oracle_threads())
+            o.init_moments(*fields[d])
+            o.run(tsteps)
+            e = field_errors(b.moments(d), o.moments())
+            worst = {k: max(worst[k], e[k]) for k in worst}
+        rec["accuracy_vs_oracle"] = dict(time_steps=tsteps, domains=len(order), **worst)
+        b.close()
+        rec["cpu_baseline"] = batch_cpu_baseline(target_s=4.0)
+        return rec
     ms_max = max_over_ranks(ms, world, dev)
     value = aggregate_mlups(world, cells, tsteps, args.steps, ms_max / 1e3)
-    peak, peak_kind = measured_peak_hbm()
     achieved = b.bytes_per_cell() * cells / (ms / 1e3 / (args.steps * tsteps)) / 1e9
     # end to end: host fields of every domain in (pinned), time steps, every domain's moments out
     pinned = [[torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in f] for f in fields]
@@ -915,6 +1064,8 @@ def main():
     ap.add_argument("--form", default=None, choices=["tiled", "flow", "plain"],
                     help="sweep form (default: the fastest of tiled and, on periodic domains, flow)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload only: skip the configurations measured beside it")
     ap.add_argument("--tile", type=int, default=-1, help="tile configuration of the tiled form (-1: autotune)")
     args = ap.parse_args()
     rank, world, local_rank = dist_env()
