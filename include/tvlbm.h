@@ -240,8 +240,20 @@ int tvlbm_moments(tvlbm_ctx *ctx, double *rho, double *ux, double *uy, double *T
  * TVLBM model"):
  *   out[0] = M  = sum f,  out[1] = P_x = sum c_x f,  out[2] = P_y = sum c_y f,
  *   out[3] = E  = (1/2) sum |c|^2 f,  out[4] = number of non-finite stored populations.
- * Synchronises the stream. */
+ * Synchronises the stream.  Returns TVLBM_ENONFINITE, with out filled, when out[4] > 0 (a
+ * device wait that gave up since the last synchronising call is reported first, as
+ * TVLBM_ETIMEOUT). */
 int tvlbm_conserved_sums(tvlbm_ctx *ctx, double out[5]);
+
+/* Failure-path hook of the dataflow form (TVLBM_FORM_FLOW), for tests: limit_s is the limit of
+ * the wait of a launch's producer for a task's 3 x 3 neighbourhood (default 2 s; accepted
+ * 1e-6 .. 2 s); unmet != 0 makes that wait require a completion count no tile reaches.  A wait
+ * that gives up raises the launch's abort word and the device status; the other CTAs stop at
+ * their next wait, every CTA drains the loads it started, and the launch ends early with the
+ * populations partly advanced.  tvlbm_step still returns TVLBM_OK (it does not synchronise); the
+ * next synchronising call returns TVLBM_ETIMEOUT and clears the status.  Restore the state with
+ * tvlbm_set_populations (or tvlbm_init_moments).  Errors: EINVAL. */
+int tvlbm_set_flow_wait(tvlbm_ctx *ctx, double limit_s, int unmet);
 
 /* Conserved sums that allocate nothing, for callers that cannot call cudaMalloc or any other
  * allocator on this path (code running inside another framework's memory pool or a
@@ -319,8 +331,8 @@ int tvlbm_batch_init_moments(tvlbm_batch *b, int domain, const double *rho, cons
                              const double *T);
 /* Advance every domain n time steps (asynchronous). */
 int tvlbm_batch_step(tvlbm_batch *b, int n);
-/* Diagnostics and populations of domain d, as tvlbm_moments / tvlbm_conserved_sums /
- * tvlbm_get_populations_f64 (synchronise). */
+/* Diagnostics and populations of domain d, as tvlbm_moments / tvlbm_conserved_sums (including
+ * its TVLBM_ENONFINITE) / tvlbm_get_populations_f64 (synchronise). */
 int tvlbm_batch_moments(tvlbm_batch *b, int domain, double *rho, double *ux, double *uy, double *T);
 int tvlbm_batch_conserved_sums(tvlbm_batch *b, int domain, double out[5]);
 int tvlbm_batch_get_populations_f64(tvlbm_batch *b, int domain, double *host);

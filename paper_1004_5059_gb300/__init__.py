@@ -87,6 +87,7 @@ def _load_library() -> ctypes.CDLL:
         "tvlbm_step": (_I, [_P, _I]),
         "tvlbm_moments": (_I, [_P, _DP, _DP, _DP, _DP]),
         "tvlbm_conserved_sums": (_I, [_P, _DP]),
+        "tvlbm_set_flow_wait": (_I, [_P, _D, _I]),
         "tvlbm_population_bytes": (_SZ, [_P]),
         "tvlbm_get_populations": (_I, [_P, _P, _SZ]),
         "tvlbm_set_populations": (_I, [_P, _P, _SZ]),
@@ -250,10 +251,18 @@ def tvlbm_moments(ctx, nx, ny, out=None):
     return tuple(outs)
 
 
-def tvlbm_conserved_sums(ctx) -> np.ndarray:
+def tvlbm_conserved_sums(ctx, allow_nonfinite: bool = False) -> np.ndarray:
+    """(M, P_x, P_y, E, non-finite count); raises TvlbmError (TVLBM_ENONFINITE) when the count
+    is not zero, unless allow_nonfinite."""
     out = np.zeros(5)
-    _check(_lib.tvlbm_conserved_sums(ctx, _dp(out)), ctx)
+    rc = _lib.tvlbm_conserved_sums(ctx, _dp(out))
+    if not (allow_nonfinite and rc == TVLBM_ENONFINITE):
+        _check(rc, ctx)
     return out
+
+
+def tvlbm_set_flow_wait(ctx, limit_s: float, unmet: bool = False):
+    _check(_lib.tvlbm_set_flow_wait(ctx, float(limit_s), 1 if unmet else 0), ctx)
 
 
 def tvlbm_population_bytes(ctx) -> int:
@@ -388,8 +397,8 @@ class Simulation:
     def moments(self):
         return tvlbm_moments(self.ctx, self.nx, self.ny)
 
-    def conserved_sums(self):
-        return tvlbm_conserved_sums(self.ctx)
+    def conserved_sums(self, allow_nonfinite: bool = False):
+        return tvlbm_conserved_sums(self.ctx, allow_nonfinite)
 
     def populations_f64(self):
         out = np.empty((self.Q, self.ny, self.nx))
@@ -491,9 +500,11 @@ class Batch:
         _bcheck(_lib.tvlbm_batch_moments(self.handle, int(d), *[_dp(o) for o in outs]), self.handle)
         return tuple(outs)
 
-    def conserved_sums(self, d):
+    def conserved_sums(self, d, allow_nonfinite: bool = False):
         out = np.zeros(5)
-        _bcheck(_lib.tvlbm_batch_conserved_sums(self.handle, int(d), _dp(out)), self.handle)
+        rc = _lib.tvlbm_batch_conserved_sums(self.handle, int(d), _dp(out))
+        if not (allow_nonfinite and rc == TVLBM_ENONFINITE):
+            _bcheck(rc, self.handle)
         return out
 
     def populations_f64(self, d):

@@ -108,6 +108,8 @@ cudaError_t launch_flow(tvlbm_ctx* c, int n, cudaStream_t s) {
         src.next_task = ctr;
         src.abort = ctr + 1;
         src.done = ctr + kFlowDone;
+        src.wait_ns = c->flow_wait_ns;
+        src.wait_extra = c->flow_wait_extra;
         cudaError_t e = cudaMemsetAsync(ctr, 0, ((size_t)kFlowDone + ntiles) * sizeof(int), s);
         if (e == cudaSuccess) e = c->kt->flow_sweep(c->storage, c->tile_cfg, src, c->kp, s);
         if (e != cudaSuccess) return e;
@@ -183,6 +185,8 @@ int create_common(int nx, int ny, int velset, double tau, double dt, const tvlbm
     c->scheme = TVLBM_SCHEME_VOLUMETRIC;
     c->tau_g = INFINITY;
     c->rho0 = rho0;
+    c->flow_wait_ns = (long long)kWaitLimitNs;
+    c->flow_wait_extra = 0;
     if (bc) c->bc = *bc; else c->bc.kind = TVLBM_BC_PERIODIC;
     gauss_hermite_rule(c->n1, &c->rule);
     c->L = make_layout(nx, ny, c->Q, storage);
@@ -604,7 +608,19 @@ int tvlbm_conserved_sums(tvlbm_ctx* c, double out[5]) {
     TVLBM_CUDA(c, c->kt->reduce(c->storage, fcur(c), part, sums, c->kp, c->stream), "reduction kernels");
     TVLBM_CUDA(c, cudaMemcpyAsync(out, sums, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "cudaMemcpyAsync sums");
     TVLBM_CUDA(c, cudaStreamSynchronize(c->stream), "sums synchronize");
-    return check_status(c);
+    const int rc = check_status(c);
+    if (rc) return rc;
+    if (out[4] > 0.0) return fail(c, TVLBM_ENONFINITE, "%.0f stored populations are not finite", out[4]);
+    return TVLBM_OK;
+}
+
+int tvlbm_set_flow_wait(tvlbm_ctx* c, double limit_s, int unmet) {
+    if (!c) return TVLBM_EINVAL;
+    if (!(limit_s >= 1e-6 && limit_s <= 2.0)) return fail(c, TVLBM_EINVAL, "wait limit %g s outside [1e-6, 2]", limit_s);
+    if (unmet < 0) return fail(c, TVLBM_EINVAL, "negative unmet count");
+    c->flow_wait_ns = (long long)(limit_s * 1e9);
+    c->flow_wait_extra = unmet ? (1 << 30) : 0;
+    return TVLBM_OK;
 }
 
 size_t tvlbm_population_bytes(const tvlbm_ctx* c) {

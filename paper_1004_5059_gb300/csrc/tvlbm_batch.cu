@@ -451,7 +451,10 @@ int tvlbm_batch_conserved_sums(tvlbm_batch* b, int domain, double out[5]) {
           "reduction");
     BCUDA(b, cudaMemcpyAsync(out, sums, 5 * sizeof(double), cudaMemcpyDeviceToHost, b->stream), "copy sums");
     BCUDA(b, cudaStreamSynchronize(b->stream), "sums synchronize");
-    return check_batch_status(b);
+    const int rc = check_batch_status(b);
+    if (rc) return rc;
+    if (out[4] > 0.0) return bfail(b, TVLBM_ENONFINITE, "domain %d: %.0f stored populations are not finite", domain, out[4]);
+    return TVLBM_OK;
 }
 
 int tvlbm_batch_get_populations_f64(tvlbm_batch* b, int domain, double* host) {

@@ -42,6 +42,8 @@ struct tvlbm_ctx {
     double* ref_prof;                 //   and the profile ([3][ny] (ux, uy, T), or [Q][ny] Pref)
     int ref_every, ref_count;         // refresh period in steps (0: off), steps since the last refresh
     int ref_kind;                     // what a refresh installs: TVLBM_REF_EQUILIBRIUM or TVLBM_REF_MEAN
+    long long flow_wait_ns;           // dataflow form: limit of the producer's neighbourhood wait
+    int flow_wait_extra;              //   and the unreachable count a failure-path test adds (0)
     cudaGraphExec_t cl_graph[2];      // learned coarse steps: two steps per graph, by start parity
     unsigned long long cl_key_net;    // the network and constants the graphs were captured with
     float cl_key[24];

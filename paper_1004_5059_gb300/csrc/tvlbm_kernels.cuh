@@ -25,6 +25,7 @@ constexpr int FILL = 4;
 constexpr int kRedBlocks = 1024;  // fixed partial count of the FP64 reduction (deterministic)
 constexpr int kTileConfigs = 4;  // tile shapes of the tiled form
 constexpr int kFlowDone = 16;    // first per-tile counter in the dataflow scratch (64-byte aligned)
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s: a TMA load never takes that long
 // Per-row deviation reference tables (KParams::rowf / rowd): entries per stored row and the
 // offsets of the float table's fields.
 constexpr int kRowD = kMaxQ + 4;   // doubles per row: Pref_l, jref (2), eref, rref
@@ -409,6 +410,9 @@ struct FlowSrc {
     int* done;       // [ntiles] compute-warp completions in this launch (zeroed before it)
     int* next_task;  // task counter (zeroed before the launch)
     int* abort;      // raised by a CTA whose bounded wait gave up (zeroed before the launch)
+    long long wait_ns;  // limit of the producer's wait for a task's neighbourhood (default 2 s)
+    int wait_extra;     // added to the completion count that wait needs (0; > 0 only to test the
+                        // timeout path: no neighbour reaches it, so the wait gives up)
 };
 
 struct BatchSrc;  // tile source of the batched sweep (tvlbm_tiled.cuh)

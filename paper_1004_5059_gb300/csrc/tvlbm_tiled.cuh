@@ -124,7 +124,6 @@ __device__ __forceinline__ typename C::R lds(const unsigned char* p) {
     else return v;
 }
 
-constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s: a TMA load never takes that long
 
 // Collision of one gathered cell (fluid row y) in the codec's arithmetic, relaxation rate of the
 // domain; with a per-row deviation reference, against the row's reference (ROWS = false: the
@@ -556,12 +555,13 @@ __global__ void __launch_bounds__(FlowCfg<N1, C, CFG>::THREADS, FlowCfg<N1, C, C
                     nb[d] = src.done + yy * src.tiles_x + xx;
                 }
                 const uint64_t t0 = global_ns();
+                const int need = k * NCW + src.wait_extra;
                 for (;;) {
                     int ready = 0;
 #pragma unroll
-                    for (int d = 0; d < 9; ++d) ready += ld_relaxed_gpu(nb[d]) >= k * NCW ? 1 : 0;
+                    for (int d = 0; d < 9; ++d) ready += ld_relaxed_gpu(nb[d]) >= need ? 1 : 0;
                     if (ready == 9) break;
-                    if (*(volatile int*)src.abort || global_ns() - t0 > kWaitLimitNs) {
+                    if (*(volatile int*)src.abort || global_ns() - t0 > (uint64_t)src.wait_ns) {
                         code = -2;
                         break;
                     }
