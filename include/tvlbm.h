@@ -145,6 +145,14 @@ int tvlbm_set_form(tvlbm_ctx *ctx, int form);
  * caller memory).  Errors: EINVAL (storage, unknown scheme, tau_g = 0 or NaN), ENOMEM. */
 int tvlbm_set_scheme(tvlbm_ctx *ctx, int scheme, double tau_g);
 
+/* Finite-volume scheme: enable (1) or disable (0, default) the scaling of both relaxation times
+ * with the local pressure, tau -> tau / p and tau_g -> tau_g / p with p = rho T (Sec. "Boundary
+ * Conditions: Avoiding temperature and velocity slip", and the grid-refinement section): the
+ * dynamic viscosity tau tau_g / (tau_g - 2 tau) and the conductivity c_P tau (c_P = 2) no longer
+ * vary with density and temperature, as the closed-form thermal Couette profiles assume.  Call
+ * after tvlbm_set_scheme(TVLBM_SCHEME_FVLB).  Errors: EINVAL (not the finite-volume scheme). */
+int tvlbm_set_fv_pressure_scaling(tvlbm_ctx *ctx, int enable);
+
 /* Finite-volume scheme on a channel (a context created with TVLBM_BC_WALLS): the first and
  * last node rows are wall nodes (walls on the nodes, unlike the volumetric scheme's faces).
  * Populations arriving at a wall node advance with the one-sided stencils of Eq. FVLB2; the

@@ -53,9 +53,13 @@ def average9(w: np.ndarray) -> np.ndarray:
 class FVLB:
     """FP64 finite-volume TVLBM on an nx x ny periodic grid; state f[Q][ny][nx]."""
 
-    def __init__(self, nx, ny, velset="D2Q16", tau=0.5, tau_g=np.inf, dt=0.01):
+    def __init__(self, nx, ny, velset="D2Q16", tau=0.5, tau_g=np.inf, dt=0.01, pressure_scaled=False):
         self.nx, self.ny = int(nx), int(ny)
         self.tau, self.tau_g, self.dt = float(tau), float(tau_g), float(dt)
+        # tau -> tau / p and tau_g -> tau_g / p, p = rho T, for a viscosity and a conductivity
+        # that do not vary with the local state (Sec. "Boundary Conditions: Avoiding temperature
+        # and velocity slip")
+        self.pressure_scaled = bool(pressure_scaled)
         # the oracle's collision with dt / tau = 1 gives f_eq at each cell's moments
         self._eq = Oracle(nx, ny, velset, tau=1.0, dt=1.0)
         self.vs = self._eq.vs
@@ -73,9 +77,13 @@ class FVLB:
         """Omega_l of every cell (Eq. OMEGAFVLB)."""
         f = self.f if f is None else f
         feq = self.equilibrium(f)
-        om = -(f - feq) / self.tau
+        p = 1.0
+        if self.pressure_scaled:
+            rho, _, _, T = self._eq.moments(f)
+            p = rho * T
+        om = -(f - feq) * p / self.tau
         if np.isfinite(self.tau_g):
-            om += self.prandtl_term(f, feq)
+            om += p * self.prandtl_term(f, feq)
         return om
 
     def prandtl_term(self, f, feq) -> np.ndarray:
@@ -129,8 +137,8 @@ class FVLBChannel(FVLB):
     wall node's velocity and temperature are the wall's."""
 
     def __init__(self, nx, ny, y, walls, velset="D2Q16", tau=0.5, tau_g=np.inf, dt=0.01, exact=False,
-                 nr_iters=32):
-        super().__init__(nx, ny, velset, tau=tau, tau_g=tau_g, dt=dt)
+                 nr_iters=32, pressure_scaled=False):
+        super().__init__(nx, ny, velset, tau=tau, tau_g=tau_g, dt=dt, pressure_scaled=pressure_scaled)
         self.y = np.asarray(y, dtype=np.float64)
         assert self.y.shape == (ny,) and np.all(np.diff(self.y) > 0)
         self.walls = [float(v) for v in walls]  # u_lo, T_lo, u_hi, T_hi

@@ -29,6 +29,7 @@ struct FvParams {
     double ginv[4][4];
     double inv_tau, inv_tau_g, dt;
     int prandtl;
+    int pscale;         // relaxation times divided by the local pressure: tau -> tau / p, p = rho T
     int walls;          // channel: wall nodes on the first and last rows
     const double* dy;   // node spacings in y [ny - 1], or null for unit spacing
 };
@@ -73,9 +74,12 @@ __global__ void __launch_bounds__(256, fv_omega_minb<N1, C>()) fv_omega_kernel(c
     const R T = R(0.5) * (e2 / rho - (ux * ux + uy * uy));
     R eq[Q];
     cell_equilibrium<N1, false, R>(p, rho, ux, uy, T - R(1), eq);
+    // tau -> tau / p and tau_g -> tau_g / p (constant dynamic viscosity and conductivity)
+    const R ps = fp.pscale ? rho * T : R(1);
     R w[Q];
+    const R itau = (R)fp.inv_tau * ps;
 #pragma unroll
-    for (int l = 0; l < Q; ++l) w[l] = -(s[l] - eq[l]) * (R)fp.inv_tau;
+    for (int l = 0; l < Q; ++l) w[l] = -(s[l] - eq[l]) * itau;
     if (fp.prandtl) {
         R pxx = 0, pxy = 0, pyy = 0;
 #pragma unroll
@@ -88,7 +92,7 @@ __global__ void __launch_bounds__(256, fv_omega_minb<N1, C>()) fv_omega_kernel(c
                 pxy += n * dx * dy;
                 pyy += n * dy * dy;
             }
-        const R scale = (R)fp.inv_tau_g / (rho * T * T);
+        const R scale = (R)fp.inv_tau_g * ps / (rho * T * T);
         R raw[Q], m[4] = {0, 0, 0, 0};
 #pragma unroll
         for (int j = 0; j < N1; ++j)
@@ -374,6 +378,7 @@ int fvlb_steps(tvlbm_ctx* c, int n) {
     fp.prandtl = isfinite(c->tau_g) ? 1 : 0;
     fp.inv_tau_g = fp.prandtl ? 1.0 / c->tau_g : 0.0;
     fp.dt = c->dt;
+    fp.pscale = c->fv_pscale;
     fp.walls = c->kp.walls ? 1 : 0;
     fp.dy = c->fv_dy;
     WallParams wp;
@@ -436,6 +441,16 @@ extern "C" int tvlbm_set_scheme(tvlbm_ctx* c, int scheme, double tau_g) {
     }
     c->scheme = scheme;
     c->tau_g = tau_g;
+    return TVLBM_OK;
+}
+
+extern "C" int tvlbm_set_fv_pressure_scaling(tvlbm_ctx* c, int enable) {
+    if (!c) return TVLBM_EINVAL;
+    if (c->scheme != TVLBM_SCHEME_FVLB) {
+        snprintf(c->err, sizeof(c->err), "pressure scaling applies to the finite-volume scheme");
+        return TVLBM_EINVAL;
+    }
+    c->fv_pscale = enable ? 1 : 0;
     return TVLBM_OK;
 }
 

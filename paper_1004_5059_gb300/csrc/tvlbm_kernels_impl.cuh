@@ -400,22 +400,31 @@ __global__ void ref_rows_kernel(const double* __restrict__ prof, double* __restr
 
 // Row averages of the stored populations themselves, per velocity: prof[l][y] = mean over x of
 // Pref_l(y) + d_l(x, y), i.e. of f_l / w_l - rho0 (the reference the "mean" kind installs).  One
-// block of 256 threads per (fluid row, velocity), values in the storage's arithmetic, sums in FP64
-// in a fixed order.
+// block of 128 threads per (fluid row, velocity): 16-byte vector loads of the row, FP32 partial
+// sums in a fixed order (any reference is an exact re-encoding, so FP32 means suffice), a
+// warp-shuffle and shared-memory tree.
 template <int N1, class C>
-__global__ void __launch_bounds__(256) row_pop_means_kernel(const typename C::T* __restrict__ f, double* __restrict__ prof,
+__global__ void __launch_bounds__(128) row_pop_means_kernel(const typename C::T* __restrict__ f, double* __restrict__ prof,
                                                             const KParams p) {
-    __shared__ double sh[256];
+    using T = typename C::T;
+    constexpr int V = 16 / (int)sizeof(T);
+    __shared__ float sh[4];
     const int y = blockIdx.x, l = blockIdx.y, t = threadIdx.x;
-    double acc = 0.0;
-    for (int x = t; x < p.nx; x += blockDim.x) acc += (double)C::ld(f + sidx(p, l, x, y));
-    sh[t] = acc;
-    __syncthreads();
-    for (int h = 128; h > 0; h >>= 1) {
-        if (t < h) sh[t] += sh[t + h];
-        __syncthreads();
+    const T* row = f + sidx(p, l, 0, y);  // 32-byte aligned (hx columns of frame, pitch a multiple of 32)
+    float acc = 0.f;
+    const int nv = p.nx / V;
+    for (int v = t; v < nv; v += blockDim.x) {
+        const uint4 u = __ldg(reinterpret_cast<const uint4*>(row) + v);
+        const T* e = reinterpret_cast<const T*>(&u);
+#pragma unroll
+        for (int k = 0; k < V; ++k) acc += lds<C>(reinterpret_cast<const unsigned char*>(e + k));
     }
-    if (t == 0) prof[(long long)l * p.ny + y] = kPrefRow<double>(p, l, y) + sh[0] / p.nx;
+    for (int x = nv * V + t; x < p.nx; x += blockDim.x) acc += (float)C::ld(row + x);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((t & 31) == 0) sh[t >> 5] = acc;
+    __syncthreads();
+    if (t == 0) prof[(long long)l * p.ny + y] = kPrefRow<double>(p, l, y) + (double)((sh[0] + sh[1]) + (sh[2] + sh[3])) / p.nx;
 }
 
 // Reference entries of every stored row r from a per-velocity profile prof[l][y] of Pref (fluid
@@ -423,87 +432,117 @@ __global__ void __launch_bounds__(256) row_pop_means_kernel(const typename C::T*
 // reference): Pref_l, and the reference's moments beyond the rest state rho0 w in FP64 with the
 // exact weights, jref = sum w c Pref, eref = sum w |c|^2 Pref, rref = sum w Pref (a general
 // reference need not have density rho0); jref, eref and refD in the float table as in
-// ref_rows_kernel, refD's mass entry against rref.  One thread per row.
+// ref_rows_kernel, refD's mass entry against rref.  One block of 64 threads per row, thread l
+// holding velocity l; the sums in a fixed shared-memory order.
 template <int N1>
-__global__ void ref_rows_mean_kernel(const double* __restrict__ prof, double* __restrict__ rowd, float* __restrict__ rowf,
-                                     const KParams p) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= p.rows) return;
+__global__ void __launch_bounds__(64) ref_rows_mean_kernel(const double* __restrict__ prof, double* __restrict__ rowd,
+                                                           float* __restrict__ rowf, const KParams p) {
+    constexpr int Q = N1 * N1;
+    __shared__ double part[8][64];
+    __shared__ int bad;
+    const int r = blockIdx.x, l = threadIdx.x;
     const int y = min(max(r - HY, 0), p.ny - 1);
-    bool ok = true;
-    for (int l = 0; l < N1 * N1; ++l) ok = ok && isfinite(prof[(long long)l * p.ny + y]);
+    if (l == 0) bad = 0;
+    __syncthreads();
+    const double v = l < Q ? prof[(long long)l * p.ny + y] : 0.0;
+    if (l < Q && !isfinite(v)) atomicOr(&bad, 1);
+    __syncthreads();
+    const double pr = (l < Q && !bad) ? v : 0.0;
     double* d = rowd + (long long)r * kRowD;
     float* fr = rowf + (long long)r * kRowF;
-    double rr = 0.0, jx = 0.0, jy = 0.0, e = 0.0;
-    double m = 0.0, mx = 0.0, my = 0.0, me = 0.0;
-    for (int j = 0; j < N1; ++j)
-        for (int i = 0; i < N1; ++i) {
-            const int l = i + N1 * j;
-            const double pr = ok ? prof[(long long)l * p.ny + y] : 0.0;
-            d[l] = pr;
-            const double w = p.wd[i] * p.wd[j];
-            rr += w * pr;
-            jx += w * p.xd[i] * pr;
-            jy += w * p.xd[j] * pr;
-            e += w * (p.xd[i] * p.xd[i] + p.xd[j] * p.xd[j]) * pr;
-            const double v = (double)(float)pr;
-            m += (double)p.wf[i] * p.wf[j] * v;
-            mx += (double)p.wxf[i] * p.wf[j] * v;
-            my += (double)p.wf[i] * p.wxf[j] * v;
-            me += ((double)p.wx2f[i] * p.wf[j] + (double)p.wf[i] * p.wx2f[j]) * v;
-        }
-    d[kMaxQ] = jx;
-    d[kMaxQ + 1] = jy;
-    d[kMaxQ + 2] = e;
-    d[kMaxQ + 3] = rr;
-    fr[kRowJ] = (float)jx;
-    fr[kRowJ + 1] = (float)jy;
-    fr[kRowE] = (float)e;
-    fr[kRowRD] = (float)(-(m - rr));
-    fr[kRowRD + 1] = (float)(-(mx - (double)fr[kRowJ]));
-    fr[kRowRD + 2] = (float)(-(my - (double)fr[kRowJ + 1]));
-    fr[kRowRD + 3] = (float)(-(me - (double)fr[kRowE]));
+    if (l < Q) d[l] = pr;
+    double c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (l < Q) {
+        const int i = l % N1, j = l / N1;
+        const double w = p.wd[i] * p.wd[j];
+        c[0] = w * pr;
+        c[1] = w * p.xd[i] * pr;
+        c[2] = w * p.xd[j] * pr;
+        c[3] = w * (p.xd[i] * p.xd[i] + p.xd[j] * p.xd[j]) * pr;
+        const double vf = (double)(float)pr;
+        c[4] = (double)p.wf[i] * p.wf[j] * vf;
+        c[5] = (double)p.wxf[i] * p.wf[j] * vf;
+        c[6] = (double)p.wf[i] * p.wxf[j] * vf;
+        c[7] = ((double)p.wx2f[i] * p.wf[j] + (double)p.wf[i] * p.wx2f[j]) * vf;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) part[k][l] = c[k];
+    __syncthreads();
+    for (int h = 32; h > 0; h >>= 1) {
+        if (l < h)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) part[k][l] += part[k][l + h];
+        __syncthreads();
+    }
+    if (l == 0) {
+        const double rr = part[0][0], jx = part[1][0], jy = part[2][0], e = part[3][0];
+        d[kMaxQ] = jx;
+        d[kMaxQ + 1] = jy;
+        d[kMaxQ + 2] = e;
+        d[kMaxQ + 3] = rr;
+        fr[kRowJ] = (float)jx;
+        fr[kRowJ + 1] = (float)jy;
+        fr[kRowE] = (float)e;
+        fr[kRowRD] = (float)(-(part[4][0] - rr));
+        fr[kRowRD + 1] = (float)(-(part[5][0] - (double)fr[kRowJ]));
+        fr[kRowRD + 2] = (float)(-(part[6][0] - (double)fr[kRowJ + 1]));
+        fr[kRowRD + 3] = (float)(-(part[7][0] - (double)fr[kRowE]));
+    }
 }
 
 // Gather shift of every fluid row from the FP64 Pref table (the sources of row y lie within FILL
 // rows of it): C_l = (1 - omega) S_l - omega Pref_l and the FP32-constant moments of float(S), the
 // mass entry with the row reference's rref added.  Ghost rows collide nowhere and get zeros.  One
-// thread per stored row.
+// block of 64 threads per stored row, thread l holding velocity l; the moments summed in a fixed
+// shared-memory order.
 template <int N1>
-__global__ void ref_shift_kernel(const double* __restrict__ rowd, float* __restrict__ rowf, const KParams p) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= p.rows) return;
+__global__ void __launch_bounds__(64) ref_shift_kernel(const double* __restrict__ rowd, float* __restrict__ rowf,
+                                                       const KParams p) {
+    constexpr int Q = N1 * N1;
+    __shared__ double part[4][64];
+    const int r = blockIdx.x, l = threadIdx.x;
     const int y = r - HY;
     float* fr = rowf + (long long)r * kRowF;
     if (y < 0 || y >= p.ny) {
-        for (int l = 0; l < kMaxQ; ++l) fr[l] = 0.0f;
-        for (int k = 0; k < 4; ++k) fr[kRowSM + k] = 0.0f;
+        if (l < kMaxQ) fr[l] = 0.0f;
+        if (l < 4) fr[kRowSM + l] = 0.0f;
         return;
     }
-    const double om = (double)p.omegaf;
-    double m = 0.0, mx = 0.0, my = 0.0, me = 0.0;
-    for (int j = 0; j < N1; ++j)
-        for (int i = 0; i < N1; ++i) {
-            const int l = i + N1 * j;
-            const double a = p.ad[j];
-            const double r0 = rowd[(long long)(y - p.sh[j] + HY) * kRowD + l];
-            const double r1 = rowd[(long long)(y - p.sh[j] - 1 + HY) * kRowD + l];
-            const double self = rowd[(long long)r * kRowD + l];
-            const double S = (1.0 - a) * r0 + a * r1 - self;
-            fr[l] = (float)((1.0 - om) * S - om * self);
-            const double v = (double)(float)S;
-            m += (double)p.wf[i] * p.wf[j] * v;
-            mx += (double)p.wxf[i] * p.wf[j] * v;
-            my += (double)p.wf[i] * p.wxf[j] * v;
-            me += ((double)p.wx2f[i] * p.wf[j] + (double)p.wf[i] * p.wx2f[j]) * v;
-        }
-    for (int l = N1 * N1; l < kMaxQ; ++l) fr[l] = 0.0f;
-    // the row reference's own mass beyond rho0 (zero for an equilibrium reference) joins the
-    // shift's: the collision's rho - rho0 is their sum plus the gathered deviations' mass
-    fr[kRowSM] = (float)(m + rowd[(long long)r * kRowD + kMaxQ + 3]);
-    fr[kRowSM + 1] = (float)mx;
-    fr[kRowSM + 2] = (float)my;
-    fr[kRowSM + 3] = (float)me;
+    double c[4] = {0, 0, 0, 0};
+    if (l < Q) {
+        const int i = l % N1, j = l / N1;
+        const double om = (double)p.omegaf;
+        const double a = p.ad[j];
+        const double r0 = rowd[(long long)(y - p.sh[j] + HY) * kRowD + l];
+        const double r1 = rowd[(long long)(y - p.sh[j] - 1 + HY) * kRowD + l];
+        const double self = rowd[(long long)r * kRowD + l];
+        const double S = (1.0 - a) * r0 + a * r1 - self;
+        fr[l] = (float)((1.0 - om) * S - om * self);
+        const double v = (double)(float)S;
+        c[0] = (double)p.wf[i] * p.wf[j] * v;
+        c[1] = (double)p.wxf[i] * p.wf[j] * v;
+        c[2] = (double)p.wf[i] * p.wxf[j] * v;
+        c[3] = ((double)p.wx2f[i] * p.wf[j] + (double)p.wf[i] * p.wx2f[j]) * v;
+    } else if (l < kMaxQ) {
+        fr[l] = 0.0f;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) part[k][l] = c[k];
+    __syncthreads();
+    for (int h = 32; h > 0; h >>= 1) {
+        if (l < h)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) part[k][l] += part[k][l + h];
+        __syncthreads();
+    }
+    if (l == 0) {
+        // the row reference's own mass beyond rho0 (zero for an equilibrium reference) joins the
+        // shift's: the collision's rho - rho0 is their sum plus the gathered deviations' mass
+        fr[kRowSM] = (float)(part[0][0] + rowd[(long long)r * kRowD + kMaxQ + 3]);
+        fr[kRowSM + 1] = (float)part[1][0];
+        fr[kRowSM + 2] = (float)part[2][0];
+        fr[kRowSM + 3] = (float)part[3][0];
+    }
 }
 
 // =============================================================================================
@@ -636,7 +675,7 @@ struct Launch {
     template <class C>
     static cudaError_t row_pop_means_c(const void* f, double* prof, const KParams& p, cudaStream_t s) {
         if constexpr (!C::dev) return cudaErrorInvalidValue;
-        row_pop_means_kernel<N1, C><<<dim3(p.ny, N1 * N1), 256, 0, s>>>((const typename C::T*)f, prof, p);
+        row_pop_means_kernel<N1, C><<<dim3(p.ny, N1 * N1), 128, 0, s>>>((const typename C::T*)f, prof, p);
         return cudaGetLastError();
     }
     static cudaError_t row_pop_means(int storage, const void* f, double* prof, const KParams& p, cudaStream_t s) {
@@ -645,13 +684,12 @@ struct Launch {
     static cudaError_t ref_tables(const double* prof, double* rowd, float* rowf, const KParams& p, cudaStream_t s) {
         const int blocks = (p.rows + 127) / 128;
         ref_rows_kernel<N1><<<blocks, 128, 0, s>>>(prof, rowd, rowf, p);
-        ref_shift_kernel<N1><<<blocks, 128, 0, s>>>(rowd, rowf, p);
+        ref_shift_kernel<N1><<<p.rows, 64, 0, s>>>(rowd, rowf, p);
         return cudaGetLastError();
     }
     static cudaError_t ref_tables_mean(const double* prof, double* rowd, float* rowf, const KParams& p, cudaStream_t s) {
-        const int blocks = (p.rows + 127) / 128;
-        ref_rows_mean_kernel<N1><<<blocks, 128, 0, s>>>(prof, rowd, rowf, p);
-        ref_shift_kernel<N1><<<blocks, 128, 0, s>>>(rowd, rowf, p);
+        ref_rows_mean_kernel<N1><<<p.rows, 64, 0, s>>>(prof, rowd, rowf, p);
+        ref_shift_kernel<N1><<<p.rows, 64, 0, s>>>(rowd, rowf, p);
         return cudaGetLastError();
     }
     static cudaError_t flow(int storage, int cfg, const FlowSrc& src, const KParams& p, cudaStream_t s) {
