@@ -99,6 +99,8 @@ cudaError_t launch_flow(tvlbm_ctx* c, int n, cudaStream_t s) {
         memset(&src, 0, sizeof(src));
         src.map[0] = c->tmap[c->cur];
         src.map[1] = c->tmap[1 - c->cur];
+        src.smap[0] = c->smap[c->cur];
+        src.smap[1] = c->smap[1 - c->cur];
         src.buf[0] = dptr(c, c->L.off_f[c->cur]);
         src.buf[1] = dptr(c, c->L.off_f[1 - c->cur]);
         src.tiles_x = tiles_x;
@@ -121,10 +123,13 @@ cudaError_t launch_flow(tvlbm_ctx* c, int n, cudaStream_t s) {
 
 bool make_tensor_maps(tvlbm_ctx* c) {
     if (!c->kt->tiled_available(c->storage)) return false;
-    int bx = 0, by = 0;
+    int bx = 0, by = 0, tx = 0, ty = 0, r = 0;
     c->kt->tiled_box(c->storage, c->tile_cfg, &bx, &by);
-    for (int b = 0; b < 2; ++b)
+    c->kt->tile_shape(c->storage, c->tile_cfg, &tx, &ty, &r);
+    for (int b = 0; b < 2; ++b) {
         if (!encode_tensor_map(&c->tmap[b], dptr(c, c->L.off_f[b]), c->storage, c->L, c->Q, bx, by)) return false;
+        if (!encode_tensor_map(&c->smap[b], dptr(c, c->L.off_f[b]), c->storage, c->L, c->Q, tx, ty)) return false;
+    }
     return true;
 }
 

@@ -405,6 +405,7 @@ struct SweepMaps {
 // time steps, tasks (step, tile) handed out in step-major order.
 struct FlowSrc {
     CUtensorMap map[2];  // input descriptors: [0] the buffer holding the state at launch, [1] the other
+    CUtensorMap smap[2]; // output descriptors of the same buffers (box: one tile), for TMA stores
     void* buf[2];        // the same two buffers
     int tiles_x, tiles_y, ntiles, nsteps;
     int* done;       // [ntiles] compute-warp completions in this launch (zeroed before it)

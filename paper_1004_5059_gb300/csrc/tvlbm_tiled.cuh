@@ -115,6 +115,19 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
+// Shared -> global TMA tensor store of one box (bulk-group completion), its commit, and the waits
+// for the group's reads of shared memory / for its writes to complete.
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, const void* src, int x, int y, int z) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(map),
+                 "r"(smem_addr(src)), "r"(x), "r"(y), "r"(z)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// This thread's generic-proxy shared-memory writes, visible to the async proxy (a TMA store).
+__device__ __forceinline__ void fence_proxy_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 template <class C>
 __device__ __forceinline__ typename C::R lds(const unsigned char* p) {
     using T = typename C::T;
@@ -172,6 +185,31 @@ __device__ __forceinline__ void store_collided(typename C::T* f, const Geom& g, 
         }
 }
 
+// Store one collided cell at its periodic images only (not at (x, y) itself); true if it has any.
+// Used where the cell's own position is written from shared memory by a TMA tensor store.
+template <int N1, class C>
+__device__ __forceinline__ bool store_images(typename C::T* f, const Geom& g, int x, int y,
+                                             const typename C::R (&s)[N1 * N1]) {
+    const bool edge = x < FILL || x >= g.nx - FILL || (!g.walls && (y < FILL || y >= g.ny - FILL));
+    if (!edge) return false;
+    const int x0 = x - g.nx * ((x + FILL) / g.nx);
+    const int y0 = g.walls ? y : y - g.ny * ((y + FILL) / g.ny);
+    const int y1 = g.walls ? y + 1 : g.ny + FILL;
+#pragma unroll 1
+    for (int yy = y0; yy < y1; yy += g.ny)
+#pragma unroll 1
+        for (int xx = x0; xx < g.nx + FILL; xx += g.nx) {
+            if (xx == x && yy == y) continue;
+            typename C::T* q = f + ((long long)(yy + HY) * g.pitch + (xx + g.hx));
+#pragma unroll
+            for (int l = 0; l < N1 * N1; ++l) {
+                stg(q, C::enc(s[l]));
+                q += g.plane;
+            }
+        }
+    return true;
+}
+
 // ---- tile sources: where tile t lives --------------------------------------------------------
 // One domain: tiles in row-major order over a tiles_x-wide grid; the input descriptor is a
 // kernel parameter.
@@ -224,10 +262,14 @@ struct BatchSrc {
     }
 };
 
-// Gather, collide and store one tile whose Q windows are in shared memory at base.
+// Gather, collide and store one tile whose Q windows are in shared memory at base.  With sout,
+// each cell's own position goes to the shared-memory output tile sout ([Q][TY][TX], the layout a
+// TMA tensor store of a TX x TY box reads) and only its periodic images to global memory; the
+// return value then says whether this thread stored any image.
 template <int N1, class C, int CFG, bool ROWS>
-__device__ __forceinline__ void tile_compute(const unsigned char* base, int x0, int y0, const Geom& g,
-                                             typename C::T* fout, const KParams& p, int tid) {
+__device__ __forceinline__ bool tile_compute(const unsigned char* base, int x0, int y0, const Geom& g,
+                                             typename C::T* fout, const KParams& p, int tid,
+                                             typename C::T* sout = nullptr) {
     using Cfg = TileCfg<N1, C, CFG>;
     using R = typename C::R;
     constexpr int Q = N1 * N1, TX = Cfg::TX, RR = Cfg::R, BX = Cfg::BX, A = Cfg::A, ES = Cfg::ES;
@@ -240,6 +282,7 @@ __device__ __forceinline__ void tile_compute(const unsigned char* base, int x0, 
 #pragma unroll
     for (int i = 0; i < N1; ++i) off[i] = (cx + ((g.hx - p.sh[i] - 1) & (A - 1))) * ES;
     const unsigned char* wrow = base + r0 * BX * ES;
+    bool imaged = false;
     R hprev[Q];
 #pragma unroll
     for (int j = 0; j < N1; ++j)
@@ -269,9 +312,17 @@ __device__ __forceinline__ void tile_compute(const unsigned char* base, int x0, 
         const int y = y0 + r0 + kk;
         if (x < g.nx && y < g.ny) {
             collide_cell<N1, C, ROWS>(s, p, g, y);
-            store_collided<N1, C>(fout, g, x, y, s);
+            if (sout) {
+                typename C::T* q = sout + (r0 + kk) * TX + cx;
+#pragma unroll
+                for (int l = 0; l < Q; ++l) q[l * (TX * Cfg::TY)] = C::enc(s[l]);
+                imaged |= store_images<N1, C>(fout, g, x, y, s);
+            } else {
+                store_collided<N1, C>(fout, g, x, y, s);
+            }
         }
     }
+    return imaged;
 }
 
 // Tiled sweep: CTA b owns tile b.  It lets the next step's launch be scheduled at once, and
@@ -470,6 +521,10 @@ __device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence
 
 // Layout of the dataflow kernel: the tiled form's compute threads plus one producer warp, and two
 // stages of Q windows so that the next task's windows load while the current task is computed.
+// Where shared memory also holds a whole output tile ([Q][TY][TX]), the compute threads write the
+// collided cells there and a storer warp writes the tile out with TMA tensor stores (TMA_OUT):
+// every access to the population buffers then goes through the async proxy but the periodic
+// images, so no compute thread waits on a global proxy fence after its stores.
 template <int N1, class C, int CFG>
 struct FlowCfg {
     using Tile = TileCfg<N1, C, CFG>;
@@ -477,11 +532,15 @@ struct FlowCfg {
     // two stages where they fit (one otherwise: the producer then only overlaps the next
     // task's dependency wait with the current compute)
     static constexpr int STAGES = 2 * STAGE_BYTES + 256 <= 227 * 1024 ? 2 : 1;  // (3 measured slower: fewer CTAs)
+    static constexpr int OUT_BYTES = Tile::Q * Tile::TX * Tile::TY * Tile::ES;
+    static constexpr bool TMA_OUT = STAGES == 2 && STAGES * STAGE_BYTES + OUT_BYTES + 256 <= 227 * 1024;
     static constexpr int CONSUMERS = Tile::THREADS;          // compute threads (whole warps)
-    static constexpr int THREADS = CONSUMERS + 32;           // + the producer warp
+    static constexpr int THREADS = CONSUMERS + 32 + (TMA_OUT ? 32 : 0);  // + the producer (+ storer) warp
     static constexpr uint32_t TX_BYTES = (uint32_t)(Tile::Q * Tile::BX * Tile::BY * Tile::ES);
-    static constexpr int SMEM = STAGES * STAGE_BYTES + 128 + 128;  // stages, barriers + task slots, alignment
-    static_assert(STAGES * 16 + 2 * STAGES * 4 <= 128, "barriers and slots exceed their area");
+    // stages, the output tile, barriers + task slots, alignment
+    static constexpr int SMEM = STAGES * STAGE_BYTES + (TMA_OUT ? OUT_BYTES : 0) + 128 + 128;
+    static_assert(STAGES * 16 + 2 * STAGES * 4 + 16 + 8 <= 128, "barriers and slots exceed their area");
+    static_assert(OUT_BYTES % (Tile::Q * 128) == 0 || !TMA_OUT, "output planes must stay 128-byte aligned");
     // resident CTAs per SM to compile for: as many as shared memory holds (228 KB per SM, 1 KB
     // reserved per CTA), but not so many that a thread gets fewer registers than the cell's
     // state needs: 96 for D2Q9/D2Q16 in FP32 (72 measured slower at five CTAs per SM than 96
@@ -490,6 +549,9 @@ struct FlowCfg {
     static constexpr int REG_FLOOR = N1 >= 6 ? (Tile::ES == 8 ? 255 : 168) : (Tile::ES == 8 ? 128 : 96);
     static constexpr int REG_FIT = 65536 / (THREADS * REG_FLOOR);
     static constexpr int MINB = FIT < 1 ? 1 : (FIT < REG_FIT ? FIT : (REG_FIT < 1 ? 1 : REG_FIT));
+    // what a finished task adds to its tile's completion counter: the storer's one release, or
+    // one per compute warp
+    static constexpr int DONE_PER_TASK = TMA_OUT ? 1 : CONSUMERS / 32;
     static_assert(CONSUMERS % 32 == 0, "compute threads must be whole warps");
     static_assert(SMEM <= 227 * 1024, "dataflow stages exceed shared memory");
 };
@@ -498,11 +560,14 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
-// Producer (lane 0 of the last warp): take a task, wait for its neighbourhood, wait for a free
-// stage, publish the task in the stage's slot and start its Q window loads.  A negative slot
+// Producer (lane 0 of the first extra warp): take a task, wait for its neighbourhood, wait for a
+// free stage, publish the task in the stage's slot and start its Q window loads.  A negative slot
 // value ends the consumers' loop (-1: no tasks left, -2: a wait gave up).  Consumers (the tiled
 // form's threads): wait for a stage, compute the tile, free the stage, and publish the tile's
-// completion.  Every wait is bounded; a consumer's wait allows for the producer's own ones.
+// completion -- or, with TMA_OUT, hand the tile in shared memory to the storer (lane 0 of the
+// second extra warp), which writes it with Q tensor stores, frees the output tile once they have
+// read it, and publishes the completion once they are written.  Every wait is bounded; a
+// consumer's wait allows for the producer's own ones.
 template <int N1, class C, int CFG>
 __global__ void __launch_bounds__(FlowCfg<N1, C, CFG>::THREADS, FlowCfg<N1, C, CFG>::MINB)
     sweep_flow_kernel(const __grid_constant__ FlowSrc src, const KParams p) {
@@ -514,9 +579,13 @@ __global__ void __launch_bounds__(FlowCfg<N1, C, CFG>::THREADS, FlowCfg<N1, C, C
     constexpr uint64_t kConsumerLimitNs = 3 * kWaitLimitNs;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
-    uint64_t* full = reinterpret_cast<uint64_t*>(base + F::STAGES * F::STAGE_BYTES);
+    T* out = reinterpret_cast<T*>(base + F::STAGES * F::STAGE_BYTES);  // output tile (TMA_OUT)
+    uint64_t* full = reinterpret_cast<uint64_t*>(base + F::STAGES * F::STAGE_BYTES + (F::TMA_OUT ? F::OUT_BYTES : 0));
     uint64_t* empty = full + F::STAGES;
-    volatile int* slot = reinterpret_cast<volatile int*>(empty + F::STAGES);
+    uint64_t* ofull = empty + F::STAGES;   // output tile written (NCW warp arrivals)
+    uint64_t* oempty = ofull + 1;          // output tile read by the stores (storer's arrival)
+    volatile int* slot = reinterpret_cast<volatile int*>(oempty + 1);
+    volatile int* oslot = slot + 2 * F::STAGES;  // the output tile's (tile, step) or end code
     const int tid = threadIdx.x;
     if (tid == 0) {
 #pragma unroll
@@ -524,11 +593,39 @@ __global__ void __launch_bounds__(FlowCfg<N1, C, CFG>::THREADS, FlowCfg<N1, C, C
             mbar_init(&full[st], 1);
             mbar_init(&empty[st], NCW);
         }
+        mbar_init(ofull, NCW);
+        mbar_init(oempty, 1);
         fence_barrier_init();
     }
     __syncthreads();
     const Geom g = geom_of(p);
     const int total = src.ntiles * src.nsteps;
+
+    if (tid >= F::CONSUMERS + 32) {  // ---- storer warp (TMA_OUT) ----
+        if constexpr (F::TMA_OUT) {
+            if (tid != F::CONSUMERS + 32) return;
+            for (int n = 0;; ++n) {
+                if (!mbar_wait_bounded(ofull, n & 1, kConsumerLimitNs)) {
+                    atomicExch(src.abort, 1);
+                    if (p.status) atomicOr(p.status, 1);
+                    return;
+                }
+                const int t = oslot[0], k = oslot[1];
+                if (t < 0) return;  // no tiles left (every store of this thread has completed)
+                const int x0 = (t % src.tiles_x) * TX, y0 = (t / src.tiles_x) * TY;
+                const CUtensorMap* map = &src.smap[(k + 1) & 1];
+#pragma unroll 1
+                for (int l = 0; l < Q; ++l) tma_store_3d(map, out + l * (TX * TY), x0 + g.hx, y0 + HY, l);
+                bulk_commit();
+                bulk_wait_read_all();
+                mbar_arrive(oempty);  // the compute threads may write the next tile
+                bulk_wait_all();
+                fence_proxy_async_global();
+                red_release_gpu_add(src.done + t, 1);
+            }
+        }
+        return;
+    }
 
     if (tid >= F::CONSUMERS) {  // ---- producer warp ----
         if (tid != F::CONSUMERS) return;
@@ -555,7 +652,7 @@ __global__ void __launch_bounds__(FlowCfg<N1, C, CFG>::THREADS, FlowCfg<N1, C, C
                     nb[d] = src.done + yy * src.tiles_x + xx;
                 }
                 const uint64_t t0 = global_ns();
-                const int need = k * NCW + src.wait_extra;
+                const int need = k * F::DONE_PER_TASK + src.wait_extra;
                 for (;;) {
                     int ready = 0;
 #pragma unroll
@@ -604,19 +701,53 @@ __global__ void __launch_bounds__(FlowCfg<N1, C, CFG>::THREADS, FlowCfg<N1, C, C
                 atomicExch(src.abort, 1);
                 if (p.status) atomicOr(p.status, 1);
             }
+            if constexpr (F::TMA_OUT) {  // end the storer's loop too
+                if (tid == 0) oslot[0] = -2;
+                if ((tid & 31) == 0) mbar_arrive(ofull);
+            }
             return;
         }
         const int code = slot[st];
-        if (code < 0) return;  // no tasks left, or the producer gave up
-        const int t = code, k = slot[F::STAGES + st];
-        const int x0 = (t % src.tiles_x) * TX, y0 = (t / src.tiles_x) * TY;
-        tile_compute<N1, C, CFG, false>(base + st * F::STAGE_BYTES, x0, y0, g, reinterpret_cast<T*>(src.buf[(k + 1) & 1]), p,
-                                 tid);
-        fence_proxy_async_global();  // this thread's stores, visible to the TMA reads of later tasks
-        __syncwarp();                // orders the lanes' stores before lane 0's release
-        if ((tid & 31) == 0) {
-            mbar_arrive(&empty[st]);  // this warp is done with the stage
-            red_release_gpu_add(src.done + t, 1);
+        if constexpr (F::TMA_OUT) {
+            // the output tile must have been read by the previous tile's stores (first use: free)
+            const bool free_ok = __all_sync(0xffffffffu, mbar_wait_bounded(oempty, (n & 1) ^ 1, kConsumerLimitNs));
+            if (code < 0 || !free_ok) {
+                if (!free_ok && (tid & 31) == 0) {
+                    atomicExch(src.abort, 1);
+                    if (p.status) atomicOr(p.status, 1);
+                }
+                if (tid == 0) oslot[0] = code < 0 ? code : -2;
+                __syncwarp();
+                if ((tid & 31) == 0) mbar_arrive(ofull);  // the storer ends once every warp is here
+                return;
+            }
+            const int t = code, k = slot[F::STAGES + st];
+            const int x0 = (t % src.tiles_x) * TX, y0 = (t / src.tiles_x) * TY;
+            const bool imaged = tile_compute<N1, C, CFG, false>(base + st * F::STAGE_BYTES, x0, y0, g,
+                                                                reinterpret_cast<T*>(src.buf[(k + 1) & 1]), p, tid, out);
+            fence_proxy_async_shared();          // this thread's output tile writes, visible to the stores
+            if (imaged) fence_proxy_async_global();  // its periodic images, visible to later TMA reads
+            __syncwarp();
+            if ((tid & 31) == 0) {
+                mbar_arrive(&empty[st]);  // this warp is done with the stage
+                if (tid == 0) {
+                    oslot[0] = t;
+                    oslot[1] = k;
+                }
+                mbar_arrive(ofull);
+            }
+        } else {
+            if (code < 0) return;  // no tasks left, or the producer gave up
+            const int t = code, k = slot[F::STAGES + st];
+            const int x0 = (t % src.tiles_x) * TX, y0 = (t / src.tiles_x) * TY;
+            tile_compute<N1, C, CFG, false>(base + st * F::STAGE_BYTES, x0, y0, g, reinterpret_cast<T*>(src.buf[(k + 1) & 1]),
+                                            p, tid);
+            fence_proxy_async_global();  // this thread's stores, visible to the TMA reads of later tasks
+            __syncwarp();                // orders the lanes' stores before lane 0's release
+            if ((tid & 31) == 0) {
+                mbar_arrive(&empty[st]);  // this warp is done with the stage
+                red_release_gpu_add(src.done + t, 1);
+            }
         }
     }
 }
