@@ -58,8 +58,9 @@ WORKLOADS = {
 EXTRA = ("c1_4096", "c2", "c2_bf16", "c3")
 
 BATCH = dict(desc="256 independent periodic D2Q16 domains, sides drawn from {128,256,512,768,1024}, tau~U[0.55,1.5], "
-                   "Mach~U[0.05,0.3], seeded fields, FP32 populations; one persistent launch per time step over all "
-                   "tiles, CUDA-graph replay, autotuned tile shape; 20 time steps per bench step",
+                   "Mach~U[0.05,0.3], seeded fields, FP32 populations; the bench step's 20 time steps as one "
+                   "persistent dataflow launch or 20 launches over all tiles (autotuned with the tile shape), "
+                   "CUDA-graph replay",
              count=256, seed=3, velset="D2Q16", storage="fp32_dev", tsteps=20)
 
 CLOSURE = dict(desc="learned closure: D2Q16 256x256 periodic coarse run with the 54-128-128-12 GELU network "
@@ -600,19 +601,30 @@ def run_batch(args, rank, world, local_rank, sub=False):
     for d, f in enumerate(fields):
         b.init_moments(d, *f)
     tsteps = BATCH["tsteps"]
-    # autotune the tile shape on the batch itself (untimed), then restart from the initial state
+    # autotune form and tile shape on the batch itself (untimed), then restart from the initial
+    # state: the tiled form (one launch per time step) and the dataflow form (the bench step's
+    # time steps in one persistent launch, replayed from a captured graph)
     trials = {}
-    for cfg in range(b.tile_count()):
-        b.set_tile(cfg)
-        b.step(tsteps)
-        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        b.step(tsteps)
-        e.record(stream)
-        e.synchronize()
-        trials[cfg] = a.elapsed_time(e) / tsteps
-    best = min(trials, key=trials.get)
+    for form in ("tiled", "flow"):
+        for cfg in range(b.tile_count()):
+            b.set_form("tiled")
+            b.set_tile(cfg)
+            try:
+                b.set_form(form)
+            except tv.TvlbmError:
+                continue
+            b.step(tsteps)
+            b.step(tsteps)
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            b.step(tsteps)
+            e.record(stream)
+            e.synchronize()
+            trials[(form, cfg)] = a.elapsed_time(e) / tsteps
+    best_form, best = min(trials, key=trials.get)
+    b.set_form("tiled")
     b.set_tile(best)
+    b.set_form(best_form)
     for d, f in enumerate(fields):
         b.init_moments(d, *f)
     cells = b.cells()
@@ -642,7 +654,7 @@ def run_batch(args, rank, world, local_rank, sub=False):
         achieved = b.bytes_per_cell() * cells / (ms / 1e3 / (K * tsteps)) / 1e9
         rec = {"workload": BATCH["desc"], "value": cells * tsteps * K / (ms / 1e3) / 1e6, "unit": UNIT,
                "ms_per_step": ms / K, "steps": K, "warmup": W, "storage": BATCH["storage"], "domains": b.count,
-               "cells": cells, "tile": list(b.tile_shape(best)),
+               "cells": cells, "form": best_form, "tile": list(b.tile_shape(best)),
                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                             "frac": achieved / peak, "peak_kind": peak_kind, "bytes_per_cell": b.bytes_per_cell(),
                             "traffic": None}}
@@ -686,14 +698,14 @@ def run_batch(args, rank, world, local_rank, sub=False):
         "dtype": "f32", "data": "synthetic (seeded fields)",
         "config": {"workload": BATCH["desc"], "domains": b.count, "cells": cells, "velset": BATCH["velset"],
                    "storage": BATCH["storage"], "time_steps_per_bench_step": tsteps,
-                   "tile": list(b.tile_shape(best)), "autotune_ms_per_time_step": {
-                       str(b.tile_shape(k)): round(v, 4) for k, v in trials.items()},
+                   "form": best_form, "tile": list(b.tile_shape(best)), "autotune_ms_per_time_step": {
+                       "%s %s" % (f, b.tile_shape(k)): round(v, 4) for (f, k), v in trials.items()},
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "L2 flushed between timed steps; state %.1f GB" % (b.bytes_per_cell() * cells / 1e9)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": peak_kind, "bytes_per_cell": b.bytes_per_cell(), "traffic": None},
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 32 * cells, "d2h_bytes_per_step": 32 * cells},
-        "gpu_launches": args.steps * tsteps,
+        "gpu_launches": args.steps * (1 if best_form == "flow" else tsteps),
         "clocks": clk,
     }
     b.close()

@@ -312,8 +312,9 @@ double tvlbm_bytes_per_cell(const tvlbm_ctx *ctx);
 
 /* ---- batched domains ------------------------------------------------------------------------
  * Many independent periodic domains of different sizes and relaxation times (one velocity set,
- * storage and dt), advanced together: each time step is one persistent launch of the tiled
- * sweep over the tiles of every domain, and multi-step runs replay captured CUDA graphs.
+ * storage and dt), advanced together: each time step one launch of the tiled sweep over the
+ * tiles of every domain (multi-step runs replay captured CUDA graphs), or many time steps in one
+ * persistent dataflow launch (tvlbm_batch_set_form).
  * Domain d is nx[d] x ny[d] cells with relaxation time tau[d]; everything else follows the
  * single-domain calls above (layouts, errors, ownership, stream semantics). */
 typedef struct tvlbm_batch tvlbm_batch;
@@ -330,6 +331,15 @@ int tvlbm_batch_create_in(int count, const int *nx, const int *ny, const double 
 int tvlbm_batch_destroy(tvlbm_batch *b);
 int tvlbm_batch_set_stream(tvlbm_batch *b, void *stream);
 int tvlbm_batch_set_graphs(tvlbm_batch *b, int enable);
+/* Batch form: TVLBM_FORM_TILED (default; one launch per time step over every domain's tiles,
+ * 32-step captured graphs) or TVLBM_FORM_FLOW (tvlbm_batch_step(b, n) advances every domain n
+ * steps in ONE persistent launch of the dataflow sweep over the batch's tile list: a tile starts
+ * step k once the 3 x 3 periodic neighbourhood of tiles of its own domain has finished step
+ * k - 1; the launch is captured as a CUDA graph on the first call and replayed for calls with the
+ * same n; its device waits are bounded as in the single-domain form).  The populations are the
+ * same, bit for bit.  Errors: EINVAL (unknown form; the dataflow form with a tile configuration
+ * that does not cover every domain exactly). */
+int tvlbm_batch_set_form(tvlbm_batch *b, int form);
 /* Tile configurations of the batched sweep (as tvlbm_tile_*); set_tile rebuilds the tile list. */
 int tvlbm_batch_tile_count(const tvlbm_batch *b);
 int tvlbm_batch_tile_shape(const tvlbm_batch *b, int config, int *tx, int *ty, int *rows_per_thread);

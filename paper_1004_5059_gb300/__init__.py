@@ -101,6 +101,7 @@ def _load_library() -> ctypes.CDLL:
         "tvlbm_batch_create_in": (_I, [_I, _IP, _IP, _DP, _I, _I, _D, _D, _P, _SZ, ctypes.POINTER(_P)]),
         "tvlbm_batch_destroy": (_I, [_P]),
         "tvlbm_batch_set_stream": (_I, [_P, _P]),
+        "tvlbm_batch_set_form": (_I, [_P, _I]),
         "tvlbm_batch_set_graphs": (_I, [_P, _I]),
         "tvlbm_batch_tile_count": (_I, [_P]),
         "tvlbm_batch_tile_shape": (_I, [_P, _I, _IP, _IP, _IP]),
@@ -492,6 +493,11 @@ class Batch:
 
     def set_tile(self, config: int):
         _bcheck(_lib.tvlbm_batch_set_tile(self.handle, int(config)), self.handle)
+
+    def set_form(self, form):
+        """"tiled" (one launch per time step) or "flow" (n steps in one persistent launch)."""
+        _bcheck(_lib.tvlbm_batch_set_form(self.handle, FORMS[form] if isinstance(form, str) else int(form)),
+                self.handle)
 
     def init_moments(self, d, rho, ux, uy, T):
         arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (rho, ux, uy, T)]

@@ -1,9 +1,12 @@
 // Batched domains: many independent periodic grids of different sizes and relaxation times,
-// advanced together.  Each time step is ONE persistent launch of the tiled sweep over a
+// advanced together.  Tiled form: each time step is one launch of the tiled sweep over a
 // work-list of the tiles of every domain (per-tile domain index, per-domain geometry and
-// relaxation table, two TMA descriptors per domain), and multi-step runs replay captured CUDA
-// graphs.  Per-domain operations off the hot path (initialisation, moments, sums, population
-// I/O) reuse the single-domain kernels with that domain's parameters.
+// relaxation table, TMA descriptors per domain), and multi-step runs replay captured CUDA
+// graphs.  Dataflow form: n time steps of every domain are one persistent launch (the
+// single-domain dataflow kernel over the batch's tile list, each tile waiting on its domain's
+// 3 x 3 neighbourhood), replayed from a captured graph.  Per-domain operations off the hot path
+// (initialisation, moments, sums, population I/O) reuse the single-domain kernels with that
+// domain's parameters.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -36,6 +39,7 @@ struct DomainHost {
 
 struct BatchLayout {
     size_t tables_off, dom_bytes, maps_off, maps_bytes, tiles_off, tiles_bytes;
+    size_t smaps_off, flow_off, flow_bytes;  // tile-store descriptors, dataflow counters
     size_t scratch_off, scratch_bytes, part_off, sums_off, status_off, total;
     int max_tiles;
 };
@@ -44,6 +48,9 @@ struct BatchLayout {
 
 struct tvlbm_batch {
     int count, velset, n1, Q, N, storage, tile_cfg, graphs, device, cur, ntiles;
+    int form;                      // TVLBM_FORM_TILED or TVLBM_FORM_FLOW
+    cudaGraphExec_t flow_graph[2]; // dataflow form: one captured launch of flow_graph_n steps, by start parity
+    int flow_graph_n;
     double dt, rho0;
     Rule rule;
     std::vector<DomainHost> dom;
@@ -107,7 +114,10 @@ bool make_batch_layout(std::vector<DomainHost>& dom, int Q, int storage, BatchLa
     B->maps_bytes = align_up(dom.size() * 2 * sizeof(CUtensorMap), 256);
     B->tiles_off = B->maps_off + B->maps_bytes;
     B->tiles_bytes = align_up((size_t)max_tiles * sizeof(int), 256);
-    B->scratch_off = B->tiles_off + B->tiles_bytes;
+    B->smaps_off = B->tiles_off + B->tiles_bytes;
+    B->flow_off = B->smaps_off + B->maps_bytes;
+    B->flow_bytes = align_up(((size_t)kFlowDone + max_tiles) * sizeof(int), 256);
+    B->scratch_off = B->flow_off + B->flow_bytes;
     B->scratch_bytes = align_up((size_t)max_cells * 4 * sizeof(double), 256);
     B->part_off = B->scratch_off + B->scratch_bytes;
     B->sums_off = B->part_off + align_up((size_t)kRedBlocks * 5 * sizeof(double), 256);
@@ -136,7 +146,7 @@ int upload_tables(tvlbm_batch* b) {
     b->kt->tiled_box(b->storage, b->tile_cfg, &bx, &by);
     const size_t es = elem_size(b->storage);
     std::vector<BatchDomain> tab(b->count);
-    std::vector<CUtensorMap> maps(2 * b->count);
+    std::vector<CUtensorMap> maps(2 * b->count), smaps(2 * b->count);
     std::vector<int> tiles;
     tiles.reserve(b->B.max_tiles);
     for (int d = 0; d < b->count; ++d) {
@@ -150,19 +160,23 @@ int upload_tables(tvlbm_batch* b) {
         T.ny = D.ny;
         T.pitch = D.L.pitch;
         T.tiles_x = (D.nx + tx - 1) / tx;
+        T.tiles_y = (D.ny + ty - 1) / ty;
         T.tile_begin = (int)tiles.size();
         T.omegad = b->dt / D.tau;
         T.omegaf = (float)T.omegad;
         const int nt = T.tiles_x * ((D.ny + ty - 1) / ty);
         for (int k = 0; k < nt; ++k) tiles.push_back(d);
         for (int w = 0; w < 2; ++w)
-            if (!encode_tensor_map(&maps[2 * d + w], dom_buf(b, d, w), b->storage, D.L, b->Q, bx, by))
+            if (!encode_tensor_map(&maps[2 * d + w], dom_buf(b, d, w), b->storage, D.L, b->Q, bx, by) ||
+                !encode_tensor_map(&smaps[2 * d + w], dom_buf(b, d, w), b->storage, D.L, b->Q, tx, ty))
                 return bfail(b, TVLBM_ECUDA, "could not encode the TMA descriptors of domain %d", d);
     }
     b->ntiles = (int)tiles.size();
     BCUDA(b, cudaMemcpyAsync(bptr(b, b->B.tables_off), tab.data(), tab.size() * sizeof(BatchDomain),
                              cudaMemcpyHostToDevice, b->stream), "upload domain table");
     BCUDA(b, cudaMemcpyAsync(bptr(b, b->B.maps_off), maps.data(), maps.size() * sizeof(CUtensorMap),
+                             cudaMemcpyHostToDevice, b->stream), "upload descriptors");
+    BCUDA(b, cudaMemcpyAsync(bptr(b, b->B.smaps_off), smaps.data(), smaps.size() * sizeof(CUtensorMap),
                              cudaMemcpyHostToDevice, b->stream), "upload descriptors");
     BCUDA(b, cudaMemcpyAsync(bptr(b, b->B.tiles_off), tiles.data(), tiles.size() * sizeof(int),
                              cudaMemcpyHostToDevice, b->stream), "upload tile list");
@@ -171,11 +185,81 @@ int upload_tables(tvlbm_batch* b) {
 }
 
 void drop_batch_graphs(tvlbm_batch* b) {
-    for (int k = 0; k < 2; ++k)
+    for (int k = 0; k < 2; ++k) {
         if (b->graph[k]) {
             cudaGraphExecDestroy(b->graph[k]);
             b->graph[k] = nullptr;
         }
+        if (b->flow_graph[k]) {
+            cudaGraphExecDestroy(b->flow_graph[k]);
+            b->flow_graph[k] = nullptr;
+        }
+    }
+    b->flow_graph_n = 0;
+}
+
+// Whether tile configuration cfg covers every domain exactly with tiles of at least 4 rows (what
+// the dataflow form needs: a tile's sources and frame images lie in its 3 x 3 neighbourhood).
+bool batch_flow_tiles(const tvlbm_batch* b, int cfg) {
+    int tx = 0, ty = 0, r = 0;
+    b->kt->tile_shape(b->storage, cfg, &tx, &ty, &r);
+    if (tx < 32 || ty < 4) return false;
+    for (const DomainHost& D : b->dom)
+        if (D.nx % tx || D.ny % ty) return false;
+    return true;
+}
+
+// n time steps of every domain in dataflow launches from start parity `parity` on stream s (tasks
+// per launch below 2^30, steps per launch at most 2^24: the completion counters stay in an int).
+cudaError_t launch_batch_flow(tvlbm_batch* b, int n, int parity, cudaStream_t s) {
+    const int chunk_max = (1 << 30) / b->ntiles < (1 << 24) ? (1 << 30) / b->ntiles : (1 << 24);
+    int* ctr = (int*)bptr(b, b->B.flow_off);
+    while (n > 0) {
+        const int chunk = n < chunk_max ? n : chunk_max;
+        BatchFlowSrc src;
+        memset(&src, 0, sizeof(src));
+        src.dom = (const BatchDomain*)bptr(b, b->B.tables_off);
+        src.lmaps = (const CUtensorMap*)bptr(b, b->B.maps_off);
+        src.smaps = (const CUtensorMap*)bptr(b, b->B.smaps_off);
+        src.tile_dom = (const int*)bptr(b, b->B.tiles_off);
+        src.base = b->mem;
+        src.es = (int)elem_size(b->storage);
+        src.cur = parity;
+        src.ntiles = b->ntiles;
+        src.nsteps = chunk;
+        src.next_task = ctr;
+        src.abort = ctr + 1;
+        src.done = ctr + kFlowDone;
+        src.wait_ns = (long long)kWaitLimitNs;
+        src.wait_extra = 0;
+        cudaError_t e = cudaMemsetAsync(ctr, 0, ((size_t)kFlowDone + b->ntiles) * sizeof(int), s);
+        if (e == cudaSuccess) e = b->kt->batch_flow(b->storage, b->tile_cfg, src, b->kp0, s);
+        if (e != cudaSuccess) return e;
+        parity ^= chunk & 1;
+        n -= chunk;
+    }
+    return cudaSuccess;
+}
+
+// The dataflow form's n steps from start parity `parity`, captured once as a graph (n fixed by
+// the first call; a call with another n launches directly).
+int build_flow_graph(tvlbm_batch* b, int n, int parity) {
+    cudaGraph_t g = nullptr;
+    BCUDA(b, cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+    const cudaError_t le = launch_batch_flow(b, n, parity, b->capture_stream);
+    const cudaError_t ce = cudaStreamEndCapture(b->capture_stream, &g);
+    if (le != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return bfail(b, TVLBM_ECUDA, "launch during capture: %s", cudaGetErrorString(le));
+    }
+    if (ce != cudaSuccess) return bfail(b, TVLBM_ECUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(ce));
+    const cudaError_t ie = cudaGraphInstantiate(&b->flow_graph[parity], g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+        b->flow_graph[parity] = nullptr;
+        return bfail(b, TVLBM_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ie));
+    }
+    return TVLBM_OK;
 }
 
 cudaError_t launch_batch_step(tvlbm_batch* b, int parity, cudaStream_t s) {
@@ -269,6 +353,9 @@ int create_batch(int count, const int* nx, const int* ny, const double* tau, int
     b->stream = nullptr;
     b->capture_stream = nullptr;
     b->graph[0] = b->graph[1] = nullptr;
+    b->flow_graph[0] = b->flow_graph[1] = nullptr;
+    b->flow_graph_n = 0;
+    b->form = TVLBM_FORM_TILED;
     b->err[0] = 0;
     gauss_hermite_rule(b->n1, &b->rule);
     b->kt = table_for(b->n1);
@@ -379,10 +466,23 @@ int tvlbm_batch_tile_shape(const tvlbm_batch* b, int config, int* tx, int* ty, i
     return TVLBM_OK;
 }
 
+int tvlbm_batch_set_form(tvlbm_batch* b, int form) {
+    if (!b) return TVLBM_EINVAL;
+    if (form != TVLBM_FORM_TILED && form != TVLBM_FORM_FLOW) return bfail(b, TVLBM_EINVAL, "unknown batch form %d", form);
+    if (form == TVLBM_FORM_FLOW && !batch_flow_tiles(b, b->tile_cfg))
+        return bfail(b, TVLBM_EINVAL, "dataflow form needs every domain covered exactly by tile configuration %d",
+                     b->tile_cfg);
+    if (form != b->form) drop_batch_graphs(b);
+    b->form = form;
+    return TVLBM_OK;
+}
+
 int tvlbm_batch_set_tile(tvlbm_batch* b, int config) {
     if (!b) return TVLBM_EINVAL;
     if (config < 0 || config >= kTileConfigs) return bfail(b, TVLBM_EINVAL, "tile configuration %d out of range", config);
     if (config == b->tile_cfg) return TVLBM_OK;
+    if (b->form == TVLBM_FORM_FLOW && !batch_flow_tiles(b, config))
+        return bfail(b, TVLBM_EINVAL, "tile configuration %d does not cover every domain exactly (dataflow form)", config);
     cudaSetDevice(b->device);
     cudaStreamSynchronize(b->stream);
     b->tile_cfg = config;
@@ -408,6 +508,21 @@ int tvlbm_batch_step(tvlbm_batch* b, int n) {
     if (!b) return TVLBM_EINVAL;
     if (n < 0) return bfail(b, TVLBM_EINVAL, "negative step count");
     cudaSetDevice(b->device);
+    if (b->form == TVLBM_FORM_FLOW) {
+        if (n == 0) return TVLBM_OK;
+        if (b->graphs && (b->flow_graph_n == 0 || b->flow_graph_n == n)) {
+            if (!b->flow_graph[b->cur]) {
+                const int rc = build_flow_graph(b, n, b->cur);
+                if (rc) return rc;
+                b->flow_graph_n = n;
+            }
+            BCUDA(b, cudaGraphLaunch(b->flow_graph[b->cur], b->stream), "cudaGraphLaunch");
+        } else {
+            BCUDA(b, launch_batch_flow(b, n, b->cur, b->stream), "batch dataflow launch");
+        }
+        b->cur ^= n & 1;
+        return TVLBM_OK;
+    }
     int left = n;
     if (b->graphs) {
         while (left >= kBatchGraphSteps) {

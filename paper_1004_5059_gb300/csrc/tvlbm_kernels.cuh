@@ -416,7 +416,8 @@ struct FlowSrc {
                         // timeout path: no neighbour reaches it, so the wait gives up)
 };
 
-struct BatchSrc;  // tile source of the batched sweep (tvlbm_tiled.cuh)
+struct BatchSrc;      // tile source of the batched sweep (tvlbm_tiled.cuh)
+struct BatchFlowSrc;  // task source of the batched multi-step dataflow launch (tvlbm_tiled.cuh)
 
 
 // ---- kernel table (one per N1, defined in tvlbm_kernels_q*.cu) ----------------------------
@@ -439,8 +440,10 @@ struct KernelTable {
     cudaError_t (*reencode)(int storage, void* f, const float* delta, const KParams& p, cudaStream_t s);
     // n time steps of one periodic domain in a single dataflow launch
     cudaError_t (*flow_sweep)(int storage, int cfg, const FlowSrc& src, const KParams& p, cudaStream_t s);
-    // one time step of every domain of a batch (persistent launch over all tiles)
+    // one time step of every domain of a batch (one launch over all tiles)
     cudaError_t (*batch_sweep)(int storage, int cfg, const BatchSrc& src, const KParams& p, cudaStream_t s);
+    // n time steps of every domain of a batch in one persistent dataflow launch
+    cudaError_t (*batch_flow)(int storage, int cfg, const BatchFlowSrc& src, const KParams& p, cudaStream_t s);
     // row averages of (ux, uy, T) of buffer f into prof [3][ny] (device)
     cudaError_t (*row_means)(int storage, const void* f, double* prof, const KParams& p, cudaStream_t s);
     // per-row reference tables (KParams::rowd / rowf layout, p.rows rows) of the profile prof [3][ny]

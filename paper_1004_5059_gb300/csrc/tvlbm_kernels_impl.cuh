@@ -702,6 +702,16 @@ struct Launch {
             default: return cudaErrorInvalidValue;
         }
     }
+    static cudaError_t batch_flow(int storage, int cfg, const BatchFlowSrc& src, const KParams& p, cudaStream_t s) {
+        switch (storage) {
+            case ST_FP64: return flow_sweep<N1, CodecF64>(cfg, src, p, s);
+            case ST_FP32: return flow_sweep<N1, CodecF32>(cfg, src, p, s);
+            case ST_BF16_DEV: return flow_sweep<N1, CodecBF16Dev>(cfg, src, p, s);
+            case ST_FP16_DEV: return flow_sweep<N1, CodecF16Dev>(cfg, src, p, s);
+            case ST_FP32_DEV: return flow_sweep<N1, CodecF32Dev>(cfg, src, p, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     static cudaError_t batch(int storage, int cfg, const BatchSrc& src, const KParams& p, cudaStream_t s) {
         switch (storage) {
             case ST_FP64: return batch_sweep<N1, CodecF64>(cfg, src, p, s);
@@ -716,7 +726,7 @@ struct Launch {
 
     static const KernelTable* table() {
         static const KernelTable t = {&sweep, &init, &moments, &reduce, &wall, &halo, &decode, &encode, &tiled_available,
-                                      &box, &shape, &reencode, &flow, &batch, &row_means, &ref_tables,
+                                      &box, &shape, &reencode, &flow, &batch, &batch_flow, &row_means, &ref_tables,
                                       &row_pop_means, &ref_tables_mean};
         return &t;
     }

@@ -232,7 +232,7 @@ struct SingleSrc {
 struct BatchDomain {
     long long off[2];  // element offsets of the two population buffers from the batch base
     long long plane;
-    int nx, ny, pitch, tiles_x, tile_begin, pad;
+    int nx, ny, pitch, tiles_x, tile_begin, tiles_y;
     float omegaf;
     double omegad;
 };
@@ -519,6 +519,87 @@ __device__ __forceinline__ void fence_acquire_gpu() { asm volatile("fence.acq_re
 // Generic-proxy global writes (made visible by the acquire) become visible to TMA reads.
 __device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 
+// Task sources of the dataflow kernel.  flow_task(): the step k and tile t of task number `task` and
+// the completion counters of t's 3 x 3 periodic neighbourhood; flow_tile(): where tile t is, its
+// domain's geometry, the descriptors it loads its step-k windows with and stores its step-k output
+// with, and the buffer its periodic images go to.
+// One domain (FlowSrc, see tvlbm_kernels.cuh): step k visits tile rows starting at row k (the
+// first rows of step k + 1 then depend on the first rows that step k finished).
+__device__ __forceinline__ void flow_task(const FlowSrc& src, int task, int& k, int& t, const int* (&nb)[9]) {
+    k = task / src.ntiles;
+    const int r = task - k * src.ntiles;
+    const int tx = r % src.tiles_x, ty = (r / src.tiles_x + k) % src.tiles_y;
+    t = ty * src.tiles_x + tx;
+#pragma unroll
+    for (int d = 0; d < 9; ++d) {
+        const int xx = (tx + d % 3 - 1 + src.tiles_x) % src.tiles_x;
+        const int yy = (ty + d / 3 - 1 + src.tiles_y) % src.tiles_y;
+        nb[d] = src.done + yy * src.tiles_x + xx;
+    }
+}
+__device__ __forceinline__ void flow_tile(const FlowSrc& src, int t, int k, const KParams& p, int TX, int TY, int& x0,
+                                          int& y0, Geom& g, const CUtensorMap*& lmap, const CUtensorMap*& smap,
+                                          void*& out) {
+    x0 = (t % src.tiles_x) * TX;
+    y0 = (t / src.tiles_x) * TY;
+    g = geom_of(p);
+    lmap = &src.map[k & 1];
+    smap = &src.smap[(k + 1) & 1];
+    out = src.buf[(k + 1) & 1];
+}
+
+// Many periodic domains (the batch): the tiles of every domain in one list, tasks in step-major
+// order; a tile's neighbourhood wraps within its own domain; per-domain geometry, relaxation and
+// descriptors (two per domain for the windows, two for the tile stores) from global tables.
+struct BatchFlowSrc {
+    const BatchDomain* dom;
+    const CUtensorMap* lmaps;  // [domain][buffer], window boxes
+    const CUtensorMap* smaps;  // [domain][buffer], tile boxes
+    const int* tile_dom;
+    unsigned char* base;
+    int es, cur;               // element size; the buffer holding every domain's state at launch
+    int ntiles, nsteps;
+    int* done;
+    int* next_task;
+    int* abort;
+    long long wait_ns;
+    int wait_extra;
+};
+__device__ __forceinline__ void flow_task(const BatchFlowSrc& src, int task, int& k, int& t, const int* (&nb)[9]) {
+    k = task / src.ntiles;
+    t = task - k * src.ntiles;
+    const BatchDomain& D = src.dom[__ldg(src.tile_dom + t)];
+    const int local = t - D.tile_begin;
+    const int tx = local % D.tiles_x, ty = local / D.tiles_x;
+#pragma unroll
+    for (int d = 0; d < 9; ++d) {
+        const int xx = (tx + d % 3 - 1 + D.tiles_x) % D.tiles_x;
+        const int yy = (ty + d / 3 - 1 + D.tiles_y) % D.tiles_y;
+        nb[d] = src.done + D.tile_begin + yy * D.tiles_x + xx;
+    }
+}
+__device__ __forceinline__ void flow_tile(const BatchFlowSrc& src, int t, int k, const KParams& p, int TX, int TY,
+                                          int& x0, int& y0, Geom& g, const CUtensorMap*& lmap,
+                                          const CUtensorMap*& smap, void*& out) {
+    const int d = __ldg(src.tile_dom + t);
+    const BatchDomain& D = src.dom[d];
+    const int local = t - D.tile_begin;
+    x0 = (local % D.tiles_x) * TX;
+    y0 = (local / D.tiles_x) * TY;
+    g.nx = D.nx;
+    g.ny = D.ny;
+    g.pitch = D.pitch;
+    g.hx = p.hx;
+    g.walls = 0;
+    g.plane = D.plane;
+    g.omegaf = D.omegaf;
+    g.omegad = D.omegad;
+    const int in = (src.cur + k) & 1;
+    lmap = src.lmaps + 2 * d + in;
+    smap = src.smaps + 2 * d + (in ^ 1);
+    out = src.base + D.off[in ^ 1] * src.es;
+}
+
 // Layout of the dataflow kernel: the tiled form's compute threads plus one producer warp, and two
 // stages of Q windows so that the next task's windows load while the current task is computed.
 // Where shared memory also holds a whole output tile ([Q][TY][TX]), the compute threads write the
@@ -568,9 +649,9 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // second extra warp), which writes it with Q tensor stores, frees the output tile once they have
 // read it, and publishes the completion once they are written.  Every wait is bounded; a
 // consumer's wait allows for the producer's own ones.
-template <int N1, class C, int CFG>
+template <int N1, class C, int CFG, class Src>
 __global__ void __launch_bounds__(FlowCfg<N1, C, CFG>::THREADS, FlowCfg<N1, C, CFG>::MINB)
-    sweep_flow_kernel(const __grid_constant__ FlowSrc src, const KParams p) {
+    sweep_flow_kernel(const __grid_constant__ Src src, const KParams p) {
     using Cfg = TileCfg<N1, C, CFG>;
     using F = FlowCfg<N1, C, CFG>;
     using T = typename C::T;
@@ -598,7 +679,6 @@ __global__ void __launch_bounds__(FlowCfg<N1, C, CFG>::THREADS, FlowCfg<N1, C, C
         fence_barrier_init();
     }
     __syncthreads();
-    const Geom g = geom_of(p);
     const int total = src.ntiles * src.nsteps;
 
     if (tid >= F::CONSUMERS + 32) {  // ---- storer warp (TMA_OUT) ----
@@ -612,8 +692,11 @@ __global__ void __launch_bounds__(FlowCfg<N1, C, CFG>::THREADS, FlowCfg<N1, C, C
                 }
                 const int t = oslot[0], k = oslot[1];
                 if (t < 0) return;  // no tiles left (every store of this thread has completed)
-                const int x0 = (t % src.tiles_x) * TX, y0 = (t / src.tiles_x) * TY;
-                const CUtensorMap* map = &src.smap[(k + 1) & 1];
+                int x0, y0;
+                Geom g;
+                const CUtensorMap *lmap, *map;
+                void* outp;
+                flow_tile(src, t, k, p, TX, TY, x0, y0, g, lmap, map, outp);
 #pragma unroll 1
                 for (int l = 0; l < Q; ++l) tma_store_3d(map, out + l * (TX * TY), x0 + g.hx, y0 + HY, l);
                 bulk_commit();
@@ -634,23 +717,10 @@ __global__ void __launch_bounds__(FlowCfg<N1, C, CFG>::THREADS, FlowCfg<N1, C, C
             const uint32_t par = ((n / F::STAGES) & 1) ^ 1;  // first use of each stage passes at once
             const int task = atomicAdd(src.next_task, 1);
             int code = task < total ? 0 : -1;
-            int k = 0, t = 0, x0 = 0, y0 = 0;
+            int k = 0, t = 0;
             if (!code) {
-                // step k visits tile rows starting at row k: the first rows of step k + 1 then
-                // depend on the first rows that step k finished
-                k = task / src.ntiles;
-                const int r = task - k * src.ntiles;
-                const int tx = r % src.tiles_x, ty = (r / src.tiles_x + k) % src.tiles_y;
-                t = ty * src.tiles_x + tx;
-                x0 = tx * TX;
-                y0 = ty * TY;
                 const int* nb[9];
-#pragma unroll
-                for (int d = 0; d < 9; ++d) {
-                    const int xx = (tx + d % 3 - 1 + src.tiles_x) % src.tiles_x;
-                    const int yy = (ty + d / 3 - 1 + src.tiles_y) % src.tiles_y;
-                    nb[d] = src.done + yy * src.tiles_x + xx;
-                }
+                flow_task(src, task, k, t, nb);
                 const uint64_t t0 = global_ns();
                 const int need = k * F::DONE_PER_TASK + src.wait_extra;
                 for (;;) {
@@ -677,11 +747,15 @@ __global__ void __launch_bounds__(FlowCfg<N1, C, CFG>::THREADS, FlowCfg<N1, C, C
             }
             fence_acquire_gpu();
             fence_proxy_async_global();
+            int x0, y0;
+            Geom g;
+            const CUtensorMap *map, *smap;
+            void* outp;
+            flow_tile(src, t, k, p, TX, TY, x0, y0, g, map, smap, outp);
             slot[st] = t;  // slots: [stage] tile (>= 0) or end code, [STAGES + stage] step
             slot[F::STAGES + st] = k;
             mbar_arrive_expect_tx(&full[st], F::TX_BYTES);
             unsigned char* sb = base + st * F::STAGE_BYTES;
-            const CUtensorMap* map = &src.map[k & 1];
 #pragma unroll
             for (int l = 0; l < Q; ++l) {
                 const int i = l % N1, j = l / N1;
@@ -722,9 +796,13 @@ __global__ void __launch_bounds__(FlowCfg<N1, C, CFG>::THREADS, FlowCfg<N1, C, C
                 return;
             }
             const int t = code, k = slot[F::STAGES + st];
-            const int x0 = (t % src.tiles_x) * TX, y0 = (t / src.tiles_x) * TY;
+            int x0, y0;
+            Geom g;
+            const CUtensorMap *lmap, *smap;
+            void* outp;
+            flow_tile(src, t, k, p, TX, TY, x0, y0, g, lmap, smap, outp);
             const bool imaged = tile_compute<N1, C, CFG, false>(base + st * F::STAGE_BYTES, x0, y0, g,
-                                                                reinterpret_cast<T*>(src.buf[(k + 1) & 1]), p, tid, out);
+                                                                reinterpret_cast<T*>(outp), p, tid, out);
             fence_proxy_async_shared();          // this thread's output tile writes, visible to the stores
             if (imaged) fence_proxy_async_global();  // its periodic images, visible to later TMA reads
             __syncwarp();
@@ -739,9 +817,12 @@ __global__ void __launch_bounds__(FlowCfg<N1, C, CFG>::THREADS, FlowCfg<N1, C, C
         } else {
             if (code < 0) return;  // no tasks left, or the producer gave up
             const int t = code, k = slot[F::STAGES + st];
-            const int x0 = (t % src.tiles_x) * TX, y0 = (t / src.tiles_x) * TY;
-            tile_compute<N1, C, CFG, false>(base + st * F::STAGE_BYTES, x0, y0, g, reinterpret_cast<T*>(src.buf[(k + 1) & 1]),
-                                            p, tid);
+            int x0, y0;
+            Geom g;
+            const CUtensorMap *lmap, *smap;
+            void* outp;
+            flow_tile(src, t, k, p, TX, TY, x0, y0, g, lmap, smap, outp);
+            tile_compute<N1, C, CFG, false>(base + st * F::STAGE_BYTES, x0, y0, g, reinterpret_cast<T*>(outp), p, tid);
             fence_proxy_async_global();  // this thread's stores, visible to the TMA reads of later tasks
             __syncwarp();                // orders the lanes' stores before lane 0's release
             if ((tid & 31) == 0) {
@@ -752,19 +833,19 @@ __global__ void __launch_bounds__(FlowCfg<N1, C, CFG>::THREADS, FlowCfg<N1, C, C
     }
 }
 
-template <int N1, class C, int CFG>
-inline cudaError_t flow_launch(const FlowSrc& src, const KParams& p, cudaStream_t s) {
+template <int N1, class C, int CFG, class Src>
+inline cudaError_t flow_launch(const Src& src, const KParams& p, cudaStream_t s) {
     using F = FlowCfg<N1, C, CFG>;
     static int grid_of[64] = {};  // per device: SMs x resident CTAs
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!grid_of[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(sweep_flow_kernel<N1, C, CFG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             F::SMEM);
+        cudaError_t e = cudaFuncSetAttribute(sweep_flow_kernel<N1, C, CFG, Src>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, F::SMEM);
         if (e != cudaSuccess) return e;
         int nb = 0, sms = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_flow_kernel<N1, C, CFG>, F::THREADS, F::SMEM);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_flow_kernel<N1, C, CFG, Src>, F::THREADS, F::SMEM);
         if (e != cudaSuccess) return e;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
@@ -772,12 +853,12 @@ inline cudaError_t flow_launch(const FlowSrc& src, const KParams& p, cudaStream_
     }
     const long long tasks = (long long)src.ntiles * src.nsteps;
     const int grid = tasks < grid_of[dev] ? (int)tasks : grid_of[dev];
-    sweep_flow_kernel<N1, C, CFG><<<grid, F::THREADS, F::SMEM, s>>>(src, p);
+    sweep_flow_kernel<N1, C, CFG, Src><<<grid, F::THREADS, F::SMEM, s>>>(src, p);
     return cudaGetLastError();
 }
 
-template <int N1, class C>
-inline cudaError_t flow_sweep(int cfg, const FlowSrc& src, const KParams& p, cudaStream_t s) {
+template <int N1, class C, class Src>
+inline cudaError_t flow_sweep(int cfg, const Src& src, const KParams& p, cudaStream_t s) {
     switch (cfg) {
         case 0: return flow_launch<N1, C, 0>(src, p, s);
         case 1: return flow_launch<N1, C, 1>(src, p, s);

@@ -1,6 +1,6 @@
-"""Batched domains (one persistent launch per time step over the tiles of every domain):
-each domain must evolve exactly as the same domain run alone, and, for FP64 storage, as the
-FP64 oracle."""
+"""Batched domains (tiled form: one launch per time step over the tiles of every domain;
+dataflow form: many time steps in one persistent launch): each domain must evolve exactly as
+the same domain run alone, and, for FP64 storage, as the FP64 oracle."""
 import numpy as np
 import pytest
 
@@ -44,6 +44,57 @@ def test_batch_equals_single_domain_runs(tv, storage, config):
     b.close()
 
 
+FLOW_SIZES = [(64, 48), (128, 64), (192, 96), (64, 32), (256, 16)]  # multiples of every tile shape
+
+
+@pytest.mark.parametrize("storage", ["fp32_dev", "fp16_dev", "fp64"])
+@pytest.mark.parametrize("config", [0, 1, 2, 3])
+def test_batch_flow_equals_single_domain_runs(tv, storage, config):
+    """The persistent multi-step launch (captured on the first call of each start parity,
+    replayed after, launched directly for another step count) gives every domain the populations
+    of the same domain run alone in the tiled form, bit for bit."""
+    nx = [s[0] for s in FLOW_SIZES]
+    ny = [s[1] for s in FLOW_SIZES]
+    taus = [0.6, 0.8, 1.3, 0.55, 0.9]
+    b = tv.Batch(nx, ny, taus, "D2Q16", storage=storage)
+    b.set_tile(config)
+    b.set_form("flow")
+    fields = [workloads.random_smooth(x, y, seed=80 + d, amp_u=0.06, amp_T=0.06) for d, (x, y) in enumerate(FLOW_SIZES)]
+    for d, f in enumerate(fields):
+        b.init_moments(d, *f)
+    b.step(21)  # captured (start parity 0)
+    b.step(21)  # captured (start parity 1)
+    b.step(21)  # replayed
+    b.step(5)   # another count: a direct launch
+    for d, (x, y) in enumerate(FLOW_SIZES):
+        s = tv.Simulation(x, y, "D2Q16", tau=taus[d], storage=storage, form="tiled")
+        s.set_tile(config)
+        s.init_moments(*fields[d])
+        s.step(68)
+        assert np.array_equal(b.populations_f64(d), s.populations_f64()), (d, config)
+        s.close()
+    assert all(b.conserved_sums(d)[4] == 0 for d in range(len(FLOW_SIZES)))
+    b.close()
+
+
+def test_batch_flow_rejections(tv):
+    nx = [s[0] for s in SIZES]
+    ny = [s[1] for s in SIZES]
+    b = tv.Batch(nx, ny, TAUS, "D2Q16", storage="fp32_dev")
+    with pytest.raises(tv.TvlbmError) as e:
+        b.set_form("flow")  # ragged domains
+    assert e.value.code == tv.TVLBM_EINVAL
+    b.close()
+    b = tv.Batch([64, 128], [24, 64], [0.7, 0.8], "D2Q16", storage="fp32_dev")
+    cfg8 = [k for k in range(b.tile_count()) if tuple(b.tile_shape(k))[:2] == (32, 8)][0]
+    cfg16 = [k for k in range(b.tile_count()) if tuple(b.tile_shape(k))[:2] == (32, 16)][0]
+    b.set_tile(cfg8)
+    b.set_form("flow")
+    with pytest.raises(tv.TvlbmError):
+        b.set_tile(cfg16)  # 16-row tiles do not cover 24 rows
+    b.close()
+
+
 def test_batch_fp64_matches_oracle(tv):
     nx = [s[0] for s in SIZES[:3]]
     ny = [s[1] for s in SIZES[:3]]
@@ -76,11 +127,12 @@ def test_batch_conservation_per_domain(tv):
 
 
 @pytest.mark.slow
-def test_batch_full_size_bench_workload(tv):
+@pytest.mark.parametrize("form", ["tiled", "flow"])
+def test_batch_full_size_bench_workload(tv, form):
     """The batched workload as the bench runs it: 256 periodic D2Q16 domains (sides from
     {128 .. 1024}, tau ~ U[0.55, 1.5], seeded Gaussian bump + random flow at each domain's Mach
-    number), FP32 deviation storage, the 64 x 16 tile the bench's autotuner picks, one bench step
-    of 20 time steps.  The smallest, a middle and the largest domain equal the same domain run
+    number), FP32 deviation storage, the 64 x 16 tile, one bench step of 20 time steps, in both
+    forms (the bench's autotuner picks the faster).  The smallest, a middle and the largest domain equal the same domain run
     alone bit for bit (single-domain runs are checked against the oracle elsewhere), and every
     domain conserves mass, momentum and energy to FP32 rounding."""
     specs = workloads.batched_domains(256, seed=3)
@@ -88,6 +140,7 @@ def test_batch_full_size_bench_workload(tv):
     b = tv.Batch(n, n, [s["tau"] for s in specs], "D2Q16", storage="fp32_dev")
     cfg = [k for k in range(b.tile_count()) if tuple(b.tile_shape(k)) == (64, 16, 4)][0]
     b.set_tile(cfg)
+    b.set_form(form)
 
     def fields(s):
         return workloads.gaussian_bump_random_flow(s["n"], s["n"], seed=s["seed"], amp_u=s["mach"], sigma=s["n"] / 16.0)
