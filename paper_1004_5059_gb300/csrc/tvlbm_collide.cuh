@@ -160,15 +160,42 @@ __device__ __forceinline__ void cell_collide_dev(float (&s)[N1 * N1], const KPar
     }
     const float wdr = om * (m0 - (Dm - G));
     const float keep = 1.f - om;
+    if constexpr (!ODD) {
+        // mirror pairs (i, n-1-i) side by side in packed FP32 pairs: half the instructions
+        float2 A2[H], X2[H][N > 1 ? N : 1];
 #pragma unroll
-    for (int j = 0; j < N1; ++j) {
-        const float bj = B[j] + wdr;
+        for (int i = 0; i < H; ++i) {
+            A2[i] = make_float2(A[i], A[N1 - 1 - i]);
 #pragma unroll
-        for (int i = 0; i < N1; ++i) {
-            float weq = A[i] + bj;
+            for (int a = 1; a < N; ++a) X2[i][a] = make_float2(Xp[i][a], Xp[N1 - 1 - i][a]);
+        }
+        const float2 keep2 = make_float2(keep, keep);
 #pragma unroll
-            for (int a = 1; a < N; ++a) weq = fmaf(Xp[i][a], P[j][N - a], weq);
-            s[i + N1 * j] = fmaf(keep, s[i + N1 * j], weq);
+        for (int j = 0; j < N1; ++j) {
+            const float bj = B[j] + wdr;
+            const float2 bj2 = make_float2(bj, bj);
+#pragma unroll
+            for (int i = 0; i < H; ++i) {
+                const int m = N1 - 1 - i;
+                float2 w2 = __fadd2_rn(A2[i], bj2);
+#pragma unroll
+                for (int a = 1; a < N; ++a) w2 = __ffma2_rn(X2[i][a], make_float2(P[j][N - a], P[j][N - a]), w2);
+                const float2 s2 = __ffma2_rn(keep2, make_float2(s[i + N1 * j], s[m + N1 * j]), w2);
+                s[i + N1 * j] = s2.x;
+                s[m + N1 * j] = s2.y;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < N1; ++j) {
+            const float bj = B[j] + wdr;
+#pragma unroll
+            for (int i = 0; i < N1; ++i) {
+                float weq = A[i] + bj;
+#pragma unroll
+                for (int a = 1; a < N; ++a) weq = fmaf(Xp[i][a], P[j][N - a], weq);
+                s[i + N1 * j] = fmaf(keep, s[i + N1 * j], weq);
+            }
         }
     }
     if constexpr (ROW) {  // the row's gather shift kept by the relaxation and its reference's deviation
