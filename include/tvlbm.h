@@ -275,12 +275,15 @@ int tvlbm_set_flow_wait(tvlbm_ctx *ctx, double limit_s, int unmet);
  *   out5         device pointer to 5 doubles, caller-owned: M, P_x, P_y, E, #non-finite
  *   stream       cudaStream_t the two kernels are queued on (asynchronous; NULL = default)
  * The per-block partial sums live in a fixed device array of 1024 x 5 doubles (40 KiB) that
- * every GPU which loads the library holds until the process exits.  The first call on a device
- * looks up that array's address (cudaGetSymbolAddress) with the device current: make it before
- * any stream capture.  Each call overwrites the whole array, so nothing needs clearing; calls
- * that overlap on the GPU race on it.  No cudaMalloc, cudaFree or allocating library call.
+ * every GPU which loads the library holds until the process exits.  A call on a stream that
+ * is not capturing looks up that array's address (cudaGetSymbolAddress, with the device
+ * current) every time, so a device reset that reloads the library's module is followed; a call
+ * on a capturing stream uses the address the last such call on this device saw, so make one
+ * call before any stream capture (else ECUDA).  Each call overwrites the whole array, so
+ * nothing needs clearing; calls that overlap on the GPU race on it.  No cudaMalloc, cudaFree
+ * or allocating library call, so a call can be captured in a CUDA graph.
  * Errors: EINVAL (null pointer, unknown set or storage, Q*nx*ny > 2^31 - 1 populations),
- * ECUDA. */
+ * ECUDA (including a first call under stream capture). */
 int tvlbm_conserved_sums_static(const void *populations, int velset, int storage, int nx, int ny, double rho0,
                                 double *out5, void *stream);
 

@@ -2,6 +2,7 @@
 #pragma once
 
 #include "tvlbm_kernels.cuh"
+#include "tvlbm_reduce.cuh"
 #include "tvlbm_tiled.cuh"
 
 namespace tvlbm {
@@ -102,80 +103,6 @@ __global__ void moments_kernel(const typename C::T* __restrict__ f, double* __re
     out4[n + c] = ux;
     out4[2 * n + c] = uy;
     out4[3 * n + c] = 1.0 + th;
-}
-
-// =============================================================================================
-// FP64 conserved sums, pass 1: a fixed grid of kRedBlocks blocks, each summing the cells
-// c = blockIdx.x + k*kRedBlocks (grid stride) in a fixed order, then a fixed-shape shuffle tree.
-// Partials [kRedBlocks][5] = (M, Px, Py, E, non-finite count).
-// =============================================================================================
-static __device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-
-template <int N1, class C>
-__global__ void __launch_bounds__(256) reduce_kernel(const typename C::T* __restrict__ f, double* __restrict__ partials,
-                                                     const KParams p) {
-    constexpr int Q = N1 * N1;
-    double acc[5] = {0, 0, 0, 0, 0};
-    const long long ncell = (long long)p.nx * p.ny;
-    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;
-         c += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(c / p.nx), x = (int)(c - (long long)y * p.nx);
-#pragma unroll
-        for (int j = 0; j < N1; ++j) {
-            double r = 0, rx = 0, rxx = 0;
-#pragma unroll
-            for (int i = 0; i < N1; ++i) {
-                const double v = (double)C::ld(f + sidx(p, i + N1 * j, x, y));
-                acc[4] += isfinite(v) ? 0.0 : 1.0;
-                const double fv = to_f<C, double>(v, p.wd[i] * p.wd[j], p.rho0d + kPrefRow<double>(p, i + N1 * j, y));
-                r += fv;
-                rx += p.xd[i] * fv;
-                rxx += p.xd[i] * p.xd[i] * fv;
-            }
-            acc[0] += r;
-            acc[1] += rx;
-            acc[2] += p.xd[j] * r;
-            acc[3] += 0.5 * (rxx + p.xd[j] * p.xd[j] * r);
-        }
-    }
-    __shared__ double sh[5][8];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-        const double v = warp_sum(acc[k]);
-        if (lane == 0) sh[k][warp] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < 5) {
-        double t = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[threadIdx.x][w];
-        partials[(long long)blockIdx.x * 5 + threadIdx.x] = t;
-    }
-}
-
-// Pass 2: one block folds the kRedBlocks partials in a fixed order.
-static __global__ void __launch_bounds__(256) reduce_final_kernel(const double* __restrict__ partials, double* __restrict__ out5) {
-    __shared__ double sh[5][8];
-    double acc[5] = {0, 0, 0, 0, 0};
-    for (int b = threadIdx.x; b < kRedBlocks; b += blockDim.x)
-#pragma unroll
-        for (int k = 0; k < 5; ++k) acc[k] += partials[(long long)b * 5 + k];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-        const double v = warp_sum(acc[k]);
-        if (lane == 0) sh[k][warp] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < 5) {
-        double t = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[threadIdx.x][w];
-        out5[threadIdx.x] = t;
-    }
 }
 
 // =============================================================================================
