@@ -287,7 +287,7 @@ def run_ours(args, w, rank, world, local_rank, sub=None):
         forms = ["tiled"] if w["walls"] else ["tiled", "flow"]
     else:
         forms = [args.form]
-    probe, chosen, tuning, trials = None, None, None, {}
+    probe, chosen, tuning, trials, predicted = None, None, None, {}, None
     for form in forms:
         try:
             sim = make(form)
@@ -298,7 +298,11 @@ def run_ours(args, w, rank, world, local_rank, sub=None):
                 sim.set_tile(args.tile)
             else:
                 from paper_1004_5059_gb300 import autotune
-                tr = autotune.autotune(sim, steps=min(tsteps, 100), repeats=3)
+                log = autotune_log_path(args)
+                if log and predicted is None:  # the log's model, before this run adds to it
+                    predicted = autotune.predict(autotune.read_log(log), w["nx"], w["ny"], sim.velset, sim.storage,
+                                                 form)
+                tr = autotune.autotune(sim, steps=min(tsteps, 100), repeats=3, log_path=log, form=form)
                 for t in tr["trials"]:
                     trials["%s %s" % (form, tuple(t["tile"]))] = round(t["s_per_step"] * 1e6, 2)
                 best_t = min(t["s_per_step"] for t in tr["trials"])
@@ -381,6 +385,7 @@ def run_ours(args, w, rank, world, local_rank, sub=None):
                                            if w.get("reference") == "rows" else w.get("reference")),
                    "tile": line_tile,
                    "autotune_us_per_time_step": trials or None,
+                   "autotune_log_prediction": predicted,
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "L2 flushed (512 MiB write) between timed steps; state %.0f MB" % (
                        bytes_per_cell * cells / 1e6)},
@@ -423,6 +428,16 @@ def run_ours(args, w, rank, world, local_rank, sub=None):
         import torch.distributed as dist
         dist.destroy_process_group()
     return line if rank == 0 else None
+
+
+def autotune_log_path(args):
+    """Where the autotuner appends its trials (None: not logged)."""
+    if args.autotune_log == "none":
+        return None
+    if args.autotune_log:
+        return args.autotune_log
+    from paper_1004_5059_gb300 import autotune
+    return autotune.default_log_path()
 
 
 def _oracle_threads():
@@ -1078,6 +1093,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="default workload only: skip the configurations measured beside it")
+    ap.add_argument("--autotune-log", default=None,
+                    help="file the autotuner appends its trials to (default: $TVLBM_AUTOTUNE_LOG, else the user's "
+                         "cache directory; 'none': no log)")
     ap.add_argument("--tile", type=int, default=-1, help="tile configuration of the tiled form (-1: autotune)")
     args = ap.parse_args()
     rank, world, local_rank = dist_env()
