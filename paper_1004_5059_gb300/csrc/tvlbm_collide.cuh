@@ -97,14 +97,21 @@ __device__ __forceinline__ void cell_collide_dev(float (&s)[N1 * N1], const KPar
     const float th = 0.5f * ((rje.z + me - 2.0f * m0) * inv - (ux * ux + uy * uy));
 
     // ---- Hermite coefficients of the Maxwellian, per axis ----------------------------------
-    float hx[N + 1], hy[N + 1];
-    hx[0] = hy[0] = 1.f;
-    hx[1] = ux;
-    hy[1] = uy;
+    // (x, y) side by side in packed FP32 pairs; each lane rounds as the scalar recurrence
+    // h_{n+1} = u h_n + (n th) h_{n-1}
+    float2 hxy[N + 1];
+    hxy[0] = make_float2(1.f, 1.f);
+    hxy[1] = make_float2(ux, uy);
 #pragma unroll
     for (int n = 1; n < N; ++n) {
-        hx[n + 1] = fmaf(ux, hx[n], (float)n * th * hx[n - 1]);
-        hy[n + 1] = fmaf(uy, hy[n], (float)n * th * hy[n - 1]);
+        const float nth = (float)n * th;
+        hxy[n + 1] = __ffma2_rn(hxy[1], hxy[n], __fmul2_rn(make_float2(nth, nth), hxy[n - 1]));
+    }
+    float hx[N + 1], hy[N + 1];
+#pragma unroll
+    for (int n = 0; n <= N; ++n) {
+        hx[n] = hxy[n].x;
+        hy[n] = hxy[n].y;
     }
 
     // ---- first-order cancellation of the table defects -------------------------------------
@@ -133,28 +140,29 @@ __device__ __forceinline__ void cell_collide_dev(float (&s)[N1 * N1], const KPar
     const float orho = om * rho;
 
     // ---- per-node tables: A_i (x part), B_j (y part), X'_ia, P_jk --------------------------
+    // the x and y parts of each node's odd and even sums side by side in packed FP32 pairs
+    // (oxy, exy), accumulated by fused multiply-adds
     float A[N1], B[N1], Xp[N1][N > 1 ? N : 1], P[N1][N + 1];
 #pragma unroll
     for (int i = 0; i < (ODD ? H + 1 : H); ++i) {
         const int m = N1 - 1 - i;
-        float se = 0.f, so = 0.f, pe = 0.f, po = 0.f;
+        float2 exy = make_float2(0.f, 0.f), oxy = make_float2(0.f, 0.f);
 #pragma unroll
         for (int a = 1; a <= N; ++a) {
-            const float xa = hx[a] * p.Ef[i][a];
-            const float ya = hy[a] * p.Ef[i][a];
-            if (a & 1) { so += xa; po += ya; } else { se += xa; pe += ya; }
-            P[i][a] = pe + po;
-            P[m][a] = pe - po;
+            const float2 e2 = make_float2(p.Ef[i][a], p.Ef[i][a]);
+            if (a & 1) oxy = __ffma2_rn(hxy[a], e2, oxy); else exy = __ffma2_rn(hxy[a], e2, exy);
+            P[i][a] = exy.y + oxy.y;
+            P[m][a] = exy.y - oxy.y;
             if (a < N) {
-                Xp[i][a] = orho * xa;
+                Xp[i][a] = orho * (hx[a] * p.Ef[i][a]);
                 Xp[m][a] = (a & 1) ? -Xp[i][a] : Xp[i][a];
             }
         }
         const float cx2 = 0.5f * G * p.x2f[i];
         const float ci = fmaf(Dx, p.xf[i], cx2), cim = fmaf(-Dx, p.xf[i], cx2);
         const float cj = fmaf(Dy, p.xf[i], cx2), cjm = fmaf(-Dy, p.xf[i], cx2);
-        A[i] = fmaf(orho, se + so, -om * ci);
-        A[m] = fmaf(orho, se - so, -om * cim);
+        A[i] = fmaf(orho, exy.x + oxy.x, -om * ci);
+        A[m] = fmaf(orho, exy.x - oxy.x, -om * cim);
         B[i] = fmaf(orho, P[i][N], -om * cj);
         B[m] = fmaf(orho, P[m][N], -om * cjm);
     }

@@ -136,6 +136,82 @@ __device__ __forceinline__ typename C::R lds(const unsigned char* p) {
     else if constexpr (std::is_same<T, __half>::value) return __half2float(v);
     else return v;
 }
+// b - a, b the stored value at p.  For 16-bit storage one mixed-precision subtraction: b is
+// widened to FP32 exactly inside the instruction, so the result is that of widening first.
+template <class C>
+__device__ __forceinline__ typename C::R lds_sub(const unsigned char* p, typename C::R a) {
+    using T = typename C::T;
+    if constexpr (std::is_same<T, __half>::value) {
+        float d;
+        asm("sub.rn.f32.f16 %0, %1, %2;" : "=f"(d) : "h"(*reinterpret_cast<const unsigned short*>(p)), "f"(a));
+        return d;
+    } else if constexpr (std::is_same<T, __nv_bfloat16>::value) {
+        float d;
+        asm("sub.rn.f32.bf16 %0, %1, %2;" : "=f"(d) : "h"(*reinterpret_cast<const unsigned short*>(p)), "f"(a));
+        return d;
+    } else {
+        return lds<C>(p) - a;
+    }
+}
+// a - b on FP32 pairs (one packed instruction, each lane rounded as the scalar subtraction).
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\t"
+        "mov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\t"
+        "mov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+
+// Gather one window row for every velocity: h_l = a + alpha_i (b - a), a and b the row's two
+// source cells of velocity l (split codecs: a less its rest value), and, unless FIRST, the
+// y-interpolation with the previous row's h, s_l = h_l + alpha_j (hprev_l - h_l); hprev <- h.
+// In FP32 with an even node count the mirror pairs (i, N1 - 1 - i) of each y-node go through
+// packed FP32 instructions, each lane rounded exactly as the scalar form.
+template <int N1, class C, int WIN, bool FIRST>
+__device__ __forceinline__ void gather_row(const unsigned char* wrow, const int (&off)[N1], const KParams& p,
+                                           typename C::R (&hprev)[N1 * N1], typename C::R (&s)[N1 * N1]) {
+    using R = typename C::R;
+    constexpr int ES = (int)sizeof(typename C::T), H = N1 / 2;
+    constexpr bool PACK = std::is_same<R, float>::value && (N1 % 2 == 0);
+#pragma unroll
+    for (int j = 0; j < N1; ++j) {
+        const R ay = ka<R>(p, j);
+        if constexpr (PACK) {
+#pragma unroll
+            for (int i = 0; i < H; ++i) {
+                const int m = N1 - 1 - i, l = i + N1 * j, lm = m + N1 * j;
+                const unsigned char* qi = wrow + l * WIN + off[i];
+                const unsigned char* qm = wrow + lm * WIN + off[m];
+                const float ai = lds<C>(qi + ES), am = lds<C>(qm + ES);
+                const float2 d2 = make_float2(lds_sub<C>(qi, ai), lds_sub<C>(qm, am));
+                const float2 a2 = make_float2(split_rest<C>(p, l, ai), split_rest<C>(p, lm, am));
+                const float2 h2 = __ffma2_rn(make_float2(ka<R>(p, i), ka<R>(p, m)), d2, a2);
+                if constexpr (!FIRST) {
+                    const float2 s2 =
+                        __ffma2_rn(make_float2(ay, ay), f2sub(make_float2(hprev[l], hprev[lm]), h2), h2);
+                    s[l] = s2.x;
+                    s[lm] = s2.y;
+                }
+                hprev[l] = h2.x;
+                hprev[lm] = h2.y;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < N1; ++i) {
+                const int l = i + N1 * j;
+                const unsigned char* q = wrow + l * WIN + off[i];
+                const R a = lds<C>(q + ES);
+                const R h = fma(ka<R>(p, i), lds_sub<C>(q, a), split_rest<C>(p, l, a));
+                if constexpr (!FIRST) s[l] = fma(ay, hprev[l] - h, h);
+                hprev[l] = h;
+            }
+        }
+    }
+}
 
 
 // Collision of one gathered cell (fluid row y) in the codec's arithmetic, relaxation rate of the
@@ -283,32 +359,12 @@ __device__ __forceinline__ bool tile_compute(const unsigned char* base, int x0, 
     for (int i = 0; i < N1; ++i) off[i] = (cx + ((g.hx - p.sh[i] - 1) & (A - 1))) * ES;
     const unsigned char* wrow = base + r0 * BX * ES;
     bool imaged = false;
-    R hprev[Q];
-#pragma unroll
-    for (int j = 0; j < N1; ++j)
-#pragma unroll
-        for (int i = 0; i < N1; ++i) {
-            const unsigned char* q = wrow + (i + N1 * j) * WIN + off[i];
-            const R a = lds<C>(q + ES), b = lds<C>(q);
-            hprev[i + N1 * j] = fma(ka<R>(p, i), b - a, split_rest<C>(p, i + N1 * j, a));
-        }
+    R hprev[Q], s[Q];
+    gather_row<N1, C, WIN, true>(wrow, off, p, hprev, s);
 #pragma unroll 1
     for (int kk = 0; kk < RR; ++kk) {
         wrow += BX * ES;
-        R s[Q];
-#pragma unroll
-        for (int j = 0; j < N1; ++j) {
-            const R ay = ka<R>(p, j);
-#pragma unroll
-            for (int i = 0; i < N1; ++i) {
-                const int l = i + N1 * j;
-                const unsigned char* q = wrow + l * WIN + off[i];
-                const R a = lds<C>(q + ES), b = lds<C>(q);
-                const R h = fma(ka<R>(p, i), b - a, split_rest<C>(p, i + N1 * j, a));
-                s[l] = fma(ay, hprev[l] - h, h);
-                hprev[l] = h;
-            }
-        }
+        gather_row<N1, C, WIN, false>(wrow, off, p, hprev, s);
         const int y = y0 + r0 + kk;
         if (x < g.nx && y < g.ny) {
             collide_cell<N1, C, ROWS>(s, p, g, y);
