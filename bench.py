@@ -282,9 +282,10 @@ def run_ours(args, w, rank, world, local_rank, sub=None):
         return ms
 
     # form and tile shape: the requested ones, else the fastest (form, tile) pair the autotuner
-    # finds among the tiled form and, on periodic domains, the multi-step dataflow form
+    # finds among the tiled form, the strip form (no tile shape) and, on periodic domains,
+    # the multi-step dataflow form
     if args.form == "auto":
-        forms = ["tiled"] if w["walls"] else ["tiled", "flow"]
+        forms = ["tiled", "strip"] if w["walls"] else ["tiled", "strip", "flow"]
     else:
         forms = [args.form]
     probe, chosen, tuning, trials, predicted = None, None, None, {}, None
@@ -293,7 +294,15 @@ def run_ours(args, w, rank, world, local_rank, sub=None):
             sim = make(form)
         except tv.TvlbmError:
             continue
-        if form != "plain":
+        if form == "strip" and len(forms) > 1:
+            from paper_1004_5059_gb300 import autotune
+            t = autotune.time_config(sim, 0, min(tsteps, 100), 3)
+            trials["strip"] = round(t * 1e6, 2)
+            if tuning is not None and t >= tuning["s_per_step"]:
+                sim.close()
+                continue
+            tuning = {"best": 0, "s_per_step": t}
+        elif form not in ("plain", "strip"):
             if args.tile >= 0:
                 sim.set_tile(args.tile)
             else:
@@ -367,8 +376,7 @@ def run_ours(args, w, rank, world, local_rank, sub=None):
     achieved = bytes_per_cell * cells / avg_launch_s / 1e9
     if plain is not None:
         plain["roofline_frac"] = plain["bytes_per_cell"] * cells / plain_launch_s / 1e9 / peak
-    line_tile = (list(tv.tvlbm_tile_shape(probe.ctx, tuning["best"])) if tuning else
-                 (list(tv.tvlbm_tile_shape(probe.ctx, max(args.tile, 0))) if chosen != "plain" else None))
+    line_tile = form_tile(tv, probe, chosen, tuning["best"] if tuning else max(args.tile, 0))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -428,6 +436,17 @@ def run_ours(args, w, rank, world, local_rank, sub=None):
         import torch.distributed as dist
         dist.destroy_process_group()
     return line if rank == 0 else None
+
+
+def form_tile(tv, sim, form, cfg):
+    """The sweep's work shape: (tile width, tile height, rows per thread) of the tiled and
+    dataflow forms; (128 columns, 1 row, 1 row) for the strip form, whose CTAs walk 128-column
+    strips a row at a time; None for the plain form."""
+    if form == "plain":
+        return None
+    if form == "strip":
+        return [128, 1, 1]
+    return list(tv.tvlbm_tile_shape(sim.ctx, cfg))
 
 
 def autotune_log_path(args):
@@ -514,10 +533,10 @@ def sub_record(name, w, sim, form, tuning, trials, timed, fields, tv, K=3, W=2):
     achieved = bpc * nx * ny / s_per_tstep / 1e9
     rec = {"workload": w["desc"], "value": nx * ny / s_per_tstep / 1e6, "unit": UNIT, "ms_per_step": ms / K,
            "steps": K, "warmup": W, "form": form, "storage": w["storage"],
-           "tile": list(tv.tvlbm_tile_shape(sim.ctx, tuning["best"])) if tuning else None,
+           "tile": form_tile(tv, sim, form, tuning["best"]) if tuning else None,
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                         "peak_kind": peak_kind, "bytes_per_cell": bpc,
-                        "traffic": kernel_traffic(name, form, list(tv.tvlbm_tile_shape(sim.ctx, tuning["best"]))
+                        "traffic": kernel_traffic(name, form, form_tile(tv, sim, form, tuning["best"])
                                                   if tuning else None)}}
     if w.get("refresh"):
         rec["deviation_reference"] = "per row, %s kind, refreshed every %d time steps inside the timed region" % (
@@ -1088,8 +1107,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c1", choices=sorted(WORKLOADS) + ["c3", "c4", "fv"])
-    ap.add_argument("--form", default=None, choices=["tiled", "flow", "plain"],
-                    help="sweep form (default: the fastest of tiled and, on periodic domains, flow)")
+    ap.add_argument("--form", default=None, choices=["tiled", "flow", "plain", "strip"],
+                    help="sweep form (default: the fastest of tiled, strip and, on periodic domains, flow)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="default workload only: skip the configurations measured beside it")

@@ -71,6 +71,10 @@ extern "C" {
                               tile starts a step as soon as its 3 x 3 periodic neighbourhood has
                               finished the previous one (no launch boundary between steps).
                               Periodic domains whose size is a multiple of the tile shape only */
+#define TVLBM_FORM_STRIP 3 /* 128-column strips: each CTA walks a run of rows of a strip, one
+                              column per thread, carrying the previous row in registers, with a
+                              ring of TMA row-chunk copies issued chunks ahead of the compute.
+                              Any domain, walls included; independent of the tile configuration */
 
 /* ---- evolution schemes ------------------------------------------------------------------- */
 #define TVLBM_SCHEME_VOLUMETRIC 0 /* fused BGK collide + area-overlap pull-gather stream (default)   */
@@ -124,9 +128,10 @@ int tvlbm_destroy(tvlbm_ctx *ctx);
  * The stream must belong to the context's device. */
 int tvlbm_set_stream(tvlbm_ctx *ctx, void *stream);
 
-/* Select the sweep kernel form (TVLBM_FORM_PLAIN / TVLBM_FORM_TILED / TVLBM_FORM_FLOW).  All
- * give the same populations up to floating-point rounding order; the tiled and dataflow forms
- * give identical ones.  Errors: EINVAL (unknown form; a tiled form without a TMA descriptor;
+/* Select the sweep kernel form (TVLBM_FORM_PLAIN / TVLBM_FORM_TILED / TVLBM_FORM_FLOW /
+ * TVLBM_FORM_STRIP).  All give the same populations up to floating-point rounding order; the
+ * tiled, dataflow and strip forms give identical ones.  Errors: EINVAL (unknown form; a
+ * TMA form without a TMA descriptor;
  * the dataflow form on walls or on a domain the current tile configuration does not cover
  * exactly).  With the dataflow form, tvlbm_step(ctx, n) is one launch (captured graphs are not
  * used) and a device-side wait that gives up is reported as ETIMEOUT by the next synchronising

@@ -27,7 +27,7 @@ TVLBM_ENONFINITE = -6
 
 TVLBM_D2Q9, TVLBM_D2Q16, TVLBM_D2Q36 = 9, 16, 36
 TVLBM_FP64, TVLBM_FP32, TVLBM_BF16_DEV, TVLBM_FP16_DEV, TVLBM_FP32_DEV = 0, 1, 2, 3, 4
-TVLBM_FORM_PLAIN, TVLBM_FORM_TILED, TVLBM_FORM_FLOW = 0, 1, 2
+TVLBM_FORM_PLAIN, TVLBM_FORM_TILED, TVLBM_FORM_FLOW, TVLBM_FORM_STRIP = 0, 1, 2, 3
 TVLBM_SCHEME_VOLUMETRIC, TVLBM_SCHEME_FVLB = 0, 1
 TVLBM_MLP_IN, TVLBM_MLP_IN_PAD, TVLBM_MLP_HIDDEN = 54, 64, 128
 TVLBM_MLP_OUT, TVLBM_MLP_OUT_PAD, TVLBM_MLP_PARAMS = 12, 16, 25100
@@ -36,7 +36,7 @@ TVLBM_BC_PERIODIC, TVLBM_BC_WALLS = 0, 1
 VELSETS = {"D2Q9": TVLBM_D2Q9, "D2Q16": TVLBM_D2Q16, "D2Q36": TVLBM_D2Q36}
 STORAGES = {"fp64": TVLBM_FP64, "fp32": TVLBM_FP32, "bf16_dev": TVLBM_BF16_DEV, "fp16_dev": TVLBM_FP16_DEV,
             "fp32_dev": TVLBM_FP32_DEV}
-FORMS = {"plain": TVLBM_FORM_PLAIN, "tiled": TVLBM_FORM_TILED, "flow": TVLBM_FORM_FLOW}
+FORMS = {"plain": TVLBM_FORM_PLAIN, "tiled": TVLBM_FORM_TILED, "flow": TVLBM_FORM_FLOW, "strip": TVLBM_FORM_STRIP}
 STORAGE_NUMPY = {TVLBM_FP64: np.float64, TVLBM_FP32: np.float32, TVLBM_FP32_DEV: np.float32,
                  TVLBM_BF16_DEV: np.uint16, TVLBM_FP16_DEV: np.float16}
 

@@ -67,7 +67,7 @@ cudaError_t launch_step(tvlbm_ctx* c, int from, cudaStream_t s) {
         const cudaError_t e = c->kt->wall(c->storage, fin, c->kp, s);
         if (e != cudaSuccess) return e;
     }
-    const SweepMaps maps = {&c->tmap[from], nullptr};
+    const SweepMaps maps = {c->form == FORM_STRIP ? &c->rmap[from] : &c->tmap[from], nullptr};
     return c->kt->sweep(c->storage, c->form, c->tile_cfg, fin, fout, &maps, c->kp, s);
 }
 
@@ -129,6 +129,10 @@ bool make_tensor_maps(tvlbm_ctx* c) {
     for (int b = 0; b < 2; ++b) {
         if (!encode_tensor_map(&c->tmap[b], dptr(c, c->L.off_f[b]), c->storage, c->L, c->Q, bx, by)) return false;
         if (!encode_tensor_map(&c->smap[b], dptr(c, c->L.off_f[b]), c->storage, c->L, c->Q, tx, ty)) return false;
+        if (!encode_tensor_map(&c->rmap[b], dptr(c, c->L.off_f[b]), c->storage, c->L, c->Q,
+                               strip_box_width((int)elem_size(c->storage)),
+                               strip_chunk_rows(c->n1, (int)elem_size(c->storage))))
+            return false;
     }
     return true;
 }
@@ -405,7 +409,7 @@ int tvlbm_set_stream(tvlbm_ctx* c, void* stream) {
 
 int tvlbm_set_form(tvlbm_ctx* c, int form) {
     if (!c) return TVLBM_EINVAL;
-    if (form != FORM_PLAIN && form != FORM_TILED && form != FORM_FLOW)
+    if (form != FORM_PLAIN && form != FORM_TILED && form != FORM_FLOW && form != FORM_STRIP)
         return fail(c, TVLBM_EINVAL, "unknown form %d", form);
     if (form != FORM_PLAIN && !c->have_tmap)
         return fail(c, TVLBM_EINVAL, "tiled forms not available (no TMA descriptor for this storage/driver)");

@@ -31,10 +31,18 @@
 
 namespace tvlbm {
 
-// ROW: row points at the cell row's entries of a per-row reference table (KParams::rowf); s then
-// holds the plain gather of the stored deviations (the row's shift enters through its table).
-// Without ROW, row is unused.
-template <int N1, bool ROW>
+// A row's reference entries: from global memory (read-only path), or, with SH, from a copy the
+// CTA staged in shared memory.
+template <bool SH>
+__device__ __forceinline__ float4 row_ld4(const float* q) {  // q 16-byte aligned
+    if constexpr (SH) return *reinterpret_cast<const float4*>(q);
+    else return ld_row4(q);
+}
+
+// ROW: row points at the cell row's entries of a per-row reference table (KParams::rowf, or its
+// shared-memory copy with ROW_SH); s then holds the plain gather of the stored deviations (the
+// row's shift enters through its table).  Without ROW, row is unused.
+template <int N1, bool ROW, bool ROW_SH = false>
 __device__ __forceinline__ void cell_collide_dev(float (&s)[N1 * N1], const KParams& p, float om, const float* row) {
     constexpr int N = N1 - 1, H = N1 / 2;
     constexpr bool ODD = (N1 & 1) != 0;
@@ -76,9 +84,9 @@ __device__ __forceinline__ void cell_collide_dev(float (&s)[N1 * N1], const KPar
     // (scalar selects: a pointer into the parameter block would copy it to local memory)
     float4 rsm, rje, rrd;
     if constexpr (ROW) {
-        rsm = ld_row4(row + kRowSM);
-        rje = ld_row4(row + kRowJ);
-        rrd = ld_row4(row + kRowJ + 4);
+        rsm = row_ld4<ROW_SH>(row + kRowSM);
+        rje = row_ld4<ROW_SH>(row + kRowJ);
+        rrd = row_ld4<ROW_SH>(row + kRowJ + 4);
     } else {
         rsm = make_float4(0.f, 0.f, 0.f, 0.f);
         rje = make_float4(p.jreff[0], p.jreff[1], p.ereff, p.refD[0]);
@@ -209,7 +217,7 @@ __device__ __forceinline__ void cell_collide_dev(float (&s)[N1 * N1], const KPar
     if constexpr (ROW) {  // the row's gather shift kept by the relaxation and its reference's deviation
 #pragma unroll
         for (int l4 = 0; l4 < (N1 * N1 + 3) / 4; ++l4) {
-            const float4 c = ld_row4(row + 4 * l4);
+            const float4 c = row_ld4<ROW_SH>(row + 4 * l4);
             const float cv[4] = {c.x, c.y, c.z, c.w};
 #pragma unroll
             for (int k = 0; k < 4; ++k)

@@ -28,6 +28,7 @@ struct tvlbm_ctx {
     int tile_cfg;                     // tiled-form tile configuration
     alignas(64) CUtensorMap tmap[2];  // TMA descriptors: input windows of buffer b
     alignas(64) CUtensorMap smap[2];  //   and one tile of buffer b (the dataflow form's TMA stores)
+    alignas(64) CUtensorMap rmap[2];  //   and one source row of buffer b (the warp-strip form)
     int scheme;                       // TVLBM_SCHEME_VOLUMETRIC or TVLBM_SCHEME_FVLB
     double tau_g;                     // Prandtl-term time of the finite-volume scheme (inf: none)
     void* fv_omega;                   // finite-volume scheme: collision-term buffer (own allocation)

@@ -24,6 +24,19 @@ constexpr int HY = 4;
 constexpr int FILL = 4;
 constexpr int kRedBlocks = 1024;  // fixed partial count of the FP64 reduction (deterministic)
 constexpr int kTileConfigs = 4;  // tile shapes of the tiled form
+// Strip form: its TMA box (per velocity) is strip_box_width(es) x strip_chunk_rows(n1, es)
+// elements of es bytes -- the 128-column strip, the +1 source column and the 16-byte alignment
+// slack, by 2 rows where two 2-row ring slots fit the shared memory a CTA may take (about 220 KB
+// over the CTAs per SM that registers allow), else 1 row; the ring has three slots where they
+// fit, else two.
+constexpr int strip_box_width(int es) { return 128 + 16 / es; }
+constexpr int strip_pop_bytes(int es, int ch) { return (ch * strip_box_width(es) * es + 127) / 128 * 128; }
+constexpr int strip_smem_budget(int n1) { return (n1 >= 6 ? 220 / 3 : n1 >= 4 ? 220 / 5 : 220 / 8) * 1024; }
+constexpr bool strip_fits(int n1, int es, int ch, int slots) {
+    return slots * n1 * n1 * strip_pop_bytes(es, ch) + 1024 <= strip_smem_budget(n1);
+}
+constexpr int strip_chunk_rows(int n1, int es) { return strip_fits(n1, es, 2, 2) ? 2 : 1; }
+constexpr int strip_slots(int n1, int es) { return strip_fits(n1, es, strip_chunk_rows(n1, es), 3) ? 3 : 2; }
 constexpr int kFlowDone = 16;    // first per-tile counter in the dataflow scratch (64-byte aligned)
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s: a TMA load never takes that long
 // Per-row deviation reference tables (KParams::rowf / rowd): entries per stored row and the
@@ -34,7 +47,7 @@ constexpr int kRowSM = kMaxQ, kRowJ = kMaxQ + 4, kRowE = kMaxQ + 6, kRowRD = kMa
 static_assert(kMaxQ % 4 == 0 && kRowF % 4 == 0, "row entries are read as float4");
 
 enum Storage { ST_FP64 = 0, ST_FP32 = 1, ST_BF16_DEV = 2, ST_FP16_DEV = 3, ST_FP32_DEV = 4 };
-enum Form { FORM_PLAIN = 0, FORM_TILED = 1, FORM_FLOW = 2 };
+enum Form { FORM_PLAIN = 0, FORM_TILED = 1, FORM_FLOW = 2, FORM_STRIP = 3 };
 
 // Everything a kernel needs, passed by value (lands in the constant bank).
 struct KParams {

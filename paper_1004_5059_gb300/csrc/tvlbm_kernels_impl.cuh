@@ -3,6 +3,7 @@
 
 #include "tvlbm_kernels.cuh"
 #include "tvlbm_reduce.cuh"
+#include "tvlbm_strip.cuh"
 #include "tvlbm_tiled.cuh"
 
 namespace tvlbm {
@@ -484,6 +485,7 @@ struct Launch {
                                cudaStream_t s) {
         using T = typename C::T;
         if (form == FORM_TILED) return tiled_sweep<N1, C>(cfg, maps, (T*)fout, p, s);
+        if (form == FORM_STRIP) return strip_sweep<N1, C>(maps, (T*)fout, p, s);
         const dim3 b(32, 8);
         if constexpr (C::dev) {
             if (p.rowf) return launch_pdl(sweep_plain_kernel<N1, C, true>, grid2d(p, b), b, 0, s, (const T*)fin, (T*)fout, p);

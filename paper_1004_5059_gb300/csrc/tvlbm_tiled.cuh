@@ -57,6 +57,10 @@ struct TileCfg {
     static constexpr int BY = TY + 1;
     static constexpr int WIN_BYTES = (BX * BY * ES + 127) / 128 * 128;
     static constexpr int SMEM = Q * WIN_BYTES + 8 * Q + 128;  // windows, Q barriers, alignment slack
+    // with a per-row reference: the tile rows' entries behind the barriers (16-byte aligned)
+    static constexpr int ROWS_OFF = (Q * WIN_BYTES + 8 * Q + 15) / 16 * 16;
+    static constexpr int SMEM_ROWS = SMEM + 16 + TY * kRowF * 4;
+    static_assert(SMEM_ROWS <= 227 * 1024, "tile windows and row entries exceed shared memory");
     static_assert(SMEM <= 227 * 1024, "tile windows exceed shared memory");
     // resident CTAs per SM to compile for: D2Q36 in 32-bit arithmetic is held to about 168
     // registers a thread (3 CTAs of 128 threads; left alone the compiler takes 253 and 2 fit).
@@ -218,11 +222,18 @@ __device__ __forceinline__ void gather_row(const unsigned char* wrow, const int 
 // domain; with a per-row deviation reference, against the row's reference (ROWS = false: the
 // launch never has one, e.g. a periodic-only form).
 // A ROWS launch always has the table (the launch checks it).
-template <int N1, class C, bool ROWS>
-__device__ __forceinline__ void collide_cell(typename C::R (&s)[N1 * N1], const KParams& p, const Geom& g, int y) {
+// SROW: srow holds the row's reference entries staged in shared memory (else they are read from
+// the table in global memory).
+template <int N1, class C, bool ROWS, bool SROW = false>
+__device__ __forceinline__ void collide_cell(typename C::R (&s)[N1 * N1], const KParams& p, const Geom& g, int y,
+                                             const float* srow = nullptr) {
     if constexpr (C::dev) {
-        if constexpr (ROWS) cell_collide_dev<N1, true>(s, p, g.omegaf, p.rowf + (long long)(y + HY) * kRowF);
-        else cell_collide_dev<N1, false>(s, p, g.omegaf, nullptr);
+        if constexpr (ROWS) {
+            if constexpr (SROW) cell_collide_dev<N1, true, true>(s, p, g.omegaf, srow);
+            else cell_collide_dev<N1, true>(s, p, g.omegaf, p.rowf + (long long)(y + HY) * kRowF);
+        } else {
+            cell_collide_dev<N1, false>(s, p, g.omegaf, nullptr);
+        }
     }
     else if constexpr (C::split) cell_collide_split<N1>(s, p, g.omegaf);
     else if constexpr (std::is_same<typename C::R, double>::value) cell_collide<N1, false, double>(s, p, g.omegad);
@@ -235,9 +246,10 @@ __device__ __forceinline__ void collide_cell(typename C::R (&s)[N1 * N1], const 
 template <int N1, class C>
 __device__ __forceinline__ void store_collided(typename C::T* f, const Geom& g, int x, int y,
                                                const typename C::R (&s)[N1 * N1]) {
+    using T = typename C::T;
     const bool edge = x < FILL || x >= g.nx - FILL || (!g.walls && (y < FILL || y >= g.ny - FILL));
     if (!edge) {
-        typename C::T* q = f + ((long long)(y + HY) * g.pitch + (x + g.hx));
+        T* q = f + ((long long)(y + HY) * g.pitch + (x + g.hx));
 #pragma unroll
         for (int l = 0; l < N1 * N1; ++l) {
             stg(q, C::enc(s[l]));
@@ -341,11 +353,12 @@ struct BatchSrc {
 // Gather, collide and store one tile whose Q windows are in shared memory at base.  With sout,
 // each cell's own position goes to the shared-memory output tile sout ([Q][TY][TX], the layout a
 // TMA tensor store of a TX x TY box reads) and only its periodic images to global memory; the
-// return value then says whether this thread stored any image.
+// return value then says whether this thread stored any image.  With ROWS, srows holds the tile
+// rows' reference entries ([TY][kRowF], staged by the caller).
 template <int N1, class C, int CFG, bool ROWS>
 __device__ __forceinline__ bool tile_compute(const unsigned char* base, int x0, int y0, const Geom& g,
                                              typename C::T* fout, const KParams& p, int tid,
-                                             typename C::T* sout = nullptr) {
+                                             typename C::T* sout = nullptr, const float* srows = nullptr) {
     using Cfg = TileCfg<N1, C, CFG>;
     using R = typename C::R;
     constexpr int Q = N1 * N1, TX = Cfg::TX, RR = Cfg::R, BX = Cfg::BX, A = Cfg::A, ES = Cfg::ES;
@@ -367,7 +380,7 @@ __device__ __forceinline__ bool tile_compute(const unsigned char* base, int x0, 
         gather_row<N1, C, WIN, false>(wrow, off, p, hprev, s);
         const int y = y0 + r0 + kk;
         if (x < g.nx && y < g.ny) {
-            collide_cell<N1, C, ROWS>(s, p, g, y);
+            collide_cell<N1, C, ROWS, ROWS>(s, p, g, y, srows + (r0 + kk) * kRowF);
             if (sout) {
                 typename C::T* q = sout + (r0 + kk) * TX + cx;
 #pragma unroll
@@ -424,6 +437,20 @@ __device__ __forceinline__ void sweep_tiled_body(const Src& src, const KParams& 
             tma_load_3d(base + l * WIN, map, &bars[l], (x0 + g.hx - p.sh[i] - 1) & ~(A - 1), y0 + HY - p.sh[j] - 1, l);
         }
     }
+    float* srows = nullptr;
+    if constexpr (ROWS) {
+        // the tile rows' reference entries, once the kernels before this one (a reference refresh
+        // writes the table) are complete
+        pdl_wait();
+        srows = reinterpret_cast<float*>(base + Cfg::ROWS_OFF);
+        constexpr int V = kRowF / 4;
+#pragma unroll 1
+        for (int k = tid; k < TY * V; k += Cfg::THREADS) {
+            const int r = k / V;
+            if (y0 + r < g.ny)
+                reinterpret_cast<float4*>(srows)[k] = ld_row4(p.rowf + (long long)(y0 + r + HY) * kRowF + 4 * (k - r * V));
+        }
+    }
     if (tid < 32) {
         bool ok = true;
 #pragma unroll 1
@@ -443,7 +470,7 @@ __device__ __forceinline__ void sweep_tiled_body(const Src& src, const KParams& 
         return;
     }
 
-    tile_compute<N1, C, CFG, ROWS>(base, x0, y0, g, reinterpret_cast<T*>(outv), p, tid);
+    tile_compute<N1, C, CFG, ROWS>(base, x0, y0, g, reinterpret_cast<T*>(outv), p, tid, nullptr, srows);
 }
 
 // The kernel, with a minimum of resident CTAs where TileCfg asks for one.
@@ -488,7 +515,8 @@ inline cudaError_t tiled_prepare() {
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!attr_set[dev]) {
         const cudaError_t e = cudaFuncSetAttribute(tiled_kernel<N1, C, CFG, Src, ROWS>(),
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   ROWS ? Cfg::SMEM_ROWS : Cfg::SMEM);
         if (e != cudaSuccess) return e;
         attr_set[dev] = true;
     }
@@ -505,7 +533,8 @@ inline cudaError_t tiled_launch_rows(const SweepMaps* maps, typename C::T* fout,
     src.fout = fout;
     src.tiles_x = (p.nx + Cfg::TX - 1) / Cfg::TX;
     src.ntiles = src.tiles_x * ((p.ny + Cfg::TY - 1) / Cfg::TY);
-    return launch_pdl(tiled_kernel<N1, C, CFG, SingleSrc, ROWS>(), dim3(src.ntiles), dim3(Cfg::THREADS), Cfg::SMEM,
+    return launch_pdl(tiled_kernel<N1, C, CFG, SingleSrc, ROWS>(), dim3(src.ntiles), dim3(Cfg::THREADS),
+                      ROWS ? Cfg::SMEM_ROWS : Cfg::SMEM,
                       s, src, p);
 }
 
