@@ -943,6 +943,12 @@ def run_closure(args, rank, world, local_rank):
     t2 = time.perf_counter()
     del X, Y
     errors = {str(seed): C.evaluate(cfg, net, norm, seed, nsteps) for seed in cfg.test_seeds}
+    # the accuracy bar: the plain fine run's own RMS error against a 2x finer run, both
+    # block-averaged to the coarse grid; the learned run meets it when no field's error exceeds it
+    bar = {str(seed): C.fine_grid_accuracy(cfg, seed, nsteps) for seed in cfg.test_seeds}
+    for sd, e in errors.items():
+        e["fine_grid_accuracy_bar"] = bar[sd]
+        e["bar_met"] = all(e["learned_coarse"][k] <= bar[sd]["rms"][k] for k in bar[sd]["rms"])
     # beyond the bench horizon (the training data cover coarse steps warm .. warm + snapshots)
     horizon = C.trajectory(cfg, net, norm, cfg.test_seeds[0], checkpoints=(32, 64, 128))
 

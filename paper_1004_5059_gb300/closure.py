@@ -395,10 +395,39 @@ def evaluate(cfg: ClosureConfig, net, norm: Normalisation, seed: int, steps: int
     res = {"plain_coarse": rms_errors(plain.moments(), want), "learned_coarse": rms_errors(learned.moments(), want),
            "plain_coarse_max": field_errors(plain.moments(), want),
            "learned_coarse_max": field_errors(learned.moments(), want)}
-    sums = [s.conserved_sums() for s in (truth, plain, learned)]
+    sums = [s.conserved_sums(allow_nonfinite=True) for s in (truth, plain, learned)]
     res["mass_drift_learned"] = float(abs(sums[2][0] - sums[1][0]) / sums[1][0])
     for s in (fine, plain, learned, truth):
         s.close()
+    return res
+
+
+def fine_grid_accuracy(cfg: ClosureConfig, seed: int, steps: int, refine: int = 2):
+    """The accuracy bar of the learned coarse run: how far the plain fine run itself is from a
+    run refine times finer still, both block-averaged to the coarse grid, after the same
+    physical time as `evaluate` (warm + steps coarse steps), in the RMS metric of `rms_errors`.
+    The finer run samples the same seeded field (same Fourier modes, same bump width in domain
+    units) and keeps the physical viscosity under acoustic scaling: tau - 1/2 grows by `refine`,
+    `refine` steps per fine step.  Returns {"rms": errors of the fine run, "finer": [n, tau]}."""
+    n2 = cfg.nf * refine
+    tau2 = 0.5 + refine * (cfg.tau_f - 0.5)
+    fine = _fine_sim(cfg, seed)
+    finer = tv.Simulation(n2, n2, "D2Q16", tau=tau2, storage="fp32_dev")
+    try:
+        finer.set_form("flow")
+    except tv.TvlbmError:
+        pass
+    finer.init_moments(*workloads.gaussian_bump_random_flow(n2, n2, seed=seed, amp_u=mach_of(seed, *cfg.mach),
+                                                           sigma=n2 / 16.0, kmax=max(1, cfg.nf // 32)))
+    total = cfg.m * (cfg.warm + steps)
+    fine.step(total)
+    finer.step(refine * total)
+    a, b = _coarse_sim(cfg), _coarse_sim(cfg)
+    tv.downsample(fine, a)
+    tv.downsample(finer, b)
+    res = {"rms": rms_errors(a.moments(), b.moments()), "finer": [n2, tau2]}
+    for sim in (fine, finer, a, b):
+        sim.close()
     return res
 
 

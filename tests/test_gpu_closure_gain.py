@@ -58,3 +58,18 @@ def test_learned_coarse_run_conserves(trained):
         assert abs(s1[k] - s0[k]) <= 1e-6 * abs(s0[0]), k
     fine.close()
     coarse.close()
+
+
+def test_fine_grid_accuracy_bar(trained):
+    """The bar the learned run is measured against: the fine run's own RMS error against a run
+    twice as fine (same seeded field, viscosity kept under acoustic scaling), both block-averaged
+    to the coarse grid after the same physical time.  It must be a real bar -- finite, nonzero,
+    well below the plain coarse run's error -- and the learned run's distance to it is reported
+    (the learned run does not reach it)."""
+    C, cfg, norm, net, hist = trained
+    bar = C.fine_grid_accuracy(cfg, 201, 32)
+    traj = C.trajectory(cfg, net, norm, 201, checkpoints=(32,))[-1]
+    print("fine-grid accuracy bar", bar, "plain coarse", traj["plain"], "learned coarse", traj["learned"])
+    assert bar["finer"] == [2 * cfg.nf, 0.5 + 2 * (cfg.tau_f - 0.5)]
+    for field in ("rho", "ux", "uy", "T"):
+        assert 0.0 < bar["rms"][field] < 0.5 * traj["plain"][field], (field, bar, traj)
