@@ -186,6 +186,7 @@ __device__ __forceinline__ void cell_collide_dev(float (&s)[N1 * N1], const KPar
             for (int a = 1; a < N; ++a) X2[i][a] = make_float2(Xp[i][a], Xp[N1 - 1 - i][a]);
         }
         const float2 keep2 = make_float2(keep, keep);
+        float4 rq = make_float4(0.f, 0.f, 0.f, 0.f);  // a row's C entries, two pairs at a time
 #pragma unroll
         for (int j = 0; j < N1; ++j) {
             const float bj = B[j] + wdr;
@@ -196,7 +197,12 @@ __device__ __forceinline__ void cell_collide_dev(float (&s)[N1 * N1], const KPar
                 float2 w2 = __fadd2_rn(A2[i], bj2);
 #pragma unroll
                 for (int a = 1; a < N; ++a) w2 = __ffma2_rn(X2[i][a], make_float2(P[j][N - a], P[j][N - a]), w2);
-                const float2 s2 = __ffma2_rn(keep2, make_float2(s[i + N1 * j], s[m + N1 * j]), w2);
+                float2 s2 = __ffma2_rn(keep2, make_float2(s[i + N1 * j], s[m + N1 * j]), w2);
+                if constexpr (ROW) {  // the row's shift kept by the relaxation and its reference's deviation
+                    const int pr = j * H + i;  // pair slot (row_slot)
+                    if (pr % 2 == 0) rq = row_ld4<ROW_SH>(row + 2 * pr);
+                    s2 = __fadd2_rn(s2, pr % 2 == 0 ? make_float2(rq.x, rq.y) : make_float2(rq.z, rq.w));
+                }
                 s[i + N1 * j] = s2.x;
                 s[m + N1 * j] = s2.y;
             }
@@ -214,7 +220,7 @@ __device__ __forceinline__ void cell_collide_dev(float (&s)[N1 * N1], const KPar
             }
         }
     }
-    if constexpr (ROW) {  // the row's gather shift kept by the relaxation and its reference's deviation
+    if constexpr (ROW && ODD) {  // the row's gather shift kept by the relaxation and its reference's deviation
 #pragma unroll
         for (int l4 = 0; l4 < (N1 * N1 + 3) / 4; ++l4) {
             const float4 c = row_ld4<ROW_SH>(row + 4 * l4);
@@ -223,7 +229,7 @@ __device__ __forceinline__ void cell_collide_dev(float (&s)[N1 * N1], const KPar
             for (int k = 0; k < 4; ++k)
                 if (4 * l4 + k < N1 * N1) s[4 * l4 + k] += cv[k];
         }
-    } else if (p.has_ref) {  // the reference's own deviation: d_eq -= Pref
+    } else if (!ROW && p.has_ref) {  // the reference's own deviation: d_eq -= Pref
 #pragma unroll
         for (int l = 0; l < N1 * N1; ++l) s[l] = fmaf(-om, p.Preff[l], s[l]);
     }

@@ -44,6 +44,14 @@ constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s: a TMA load never takes
 constexpr int kRowD = kMaxQ + 4;   // doubles per row: Pref_l, jref (2), eref, rref
 constexpr int kRowF = kMaxQ + 12;  // floats per row: C_l, S moments (4), jref (2), eref, refD (4)
 constexpr int kRowSM = kMaxQ, kRowJ = kMaxQ + 4, kRowE = kMaxQ + 6, kRowRD = kMaxQ + 7;
+// Slot of C_l in a float row: for an even node count the mirror pairs (i, n1 - 1 - i) of each
+// y-node j side by side, pair j (n1 / 2) + i (the order the FP32 collision relaxes them in);
+// for an odd one, l itself.
+__host__ __device__ constexpr int row_slot(int n1, int l) {
+    return (n1 & 1) ? l
+                    : 2 * ((l / n1) * (n1 / 2) + ((l % n1) < n1 / 2 ? l % n1 : n1 - 1 - l % n1)) +
+                          ((l % n1) < n1 / 2 ? 0 : 1);
+}
 static_assert(kMaxQ % 4 == 0 && kRowF % 4 == 0, "row entries are read as float4");
 
 enum Storage { ST_FP64 = 0, ST_FP32 = 1, ST_BF16_DEV = 2, ST_FP16_DEV = 3, ST_FP32_DEV = 4 };
@@ -111,7 +119,8 @@ struct KParams {
     //   rowd[r * kRowD + l]: Pref_l; [kMaxQ + 0..1]: jref; [kMaxQ + 2]: eref; [kMaxQ + 3]: rref, the
     //   reference's mass beyond rho0 (0 for an equilibrium of density rho0; a reference taken from
     //   the rows' mean populations has the rows' own density)
-    //   rowf[r * kRowF + l]: C_l; [kRowSM + 0..3]: FP32-constant moments (m0, mx, my, me) of S;
+    //   rowf[r * kRowF + row_slot(n1, l)]: C_l; [kRowSM + 0..3]: FP32-constant moments (m0, mx,
+    //   my, me) of S;
     //   [kRowJ + 0..1]: jref; [kRowE]: eref; [kRowRD + 0..3]: refD of the row's float Pref
     //   (the S mass entry includes rref)
     const float* rowf;

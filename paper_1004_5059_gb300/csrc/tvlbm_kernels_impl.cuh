@@ -445,7 +445,7 @@ __global__ void __launch_bounds__(64) ref_shift_kernel(const double* __restrict_
         const double r1 = rowd[(long long)(y - p.sh[j] - 1 + HY) * kRowD + l];
         const double self = rowd[(long long)r * kRowD + l];
         const double S = (1.0 - a) * r0 + a * r1 - self;
-        fr[l] = (float)((1.0 - om) * S - om * self);
+        fr[row_slot(N1, l)] = (float)((1.0 - om) * S - om * self);
         const double v = (double)(float)S;
         c[0] = (double)p.wf[i] * p.wf[j] * v;
         c[1] = (double)p.wxf[i] * p.wf[j] * v;
