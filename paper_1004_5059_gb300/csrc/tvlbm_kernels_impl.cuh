@@ -127,6 +127,10 @@ __global__ void __launch_bounds__(32 * wall_lanes<N1>()) wall_kernel(typename C:
     constexpr int H = N1 / 2, NL = wall_lanes<N1>();
     __shared__ R part[NL][32];
     __shared__ R amp[32];
+    // launched while the previous sweep drains: let the sweep after this kernel be scheduled,
+    // then wait until the previous one is complete before reading the populations it wrote
+    pdl_launch_dependents();
+    pdl_wait();
     const int tx = threadIdx.x, k = threadIdx.y;
     const int side = blockIdx.y;                 // 0: wall at y = -1/2, 1: wall at y = ny - 1/2
     const int xo = blockIdx.x * 32 + tx - FILL;  // output column, in [-FILL, nx + FILL)
@@ -513,8 +517,7 @@ struct Launch {
     template <class C>
     static cudaError_t wall_c(void* f, const KParams& p, cudaStream_t s) {
         const dim3 grid((p.nx + 2 * FILL + 31) / 32, 2), block(32, wall_lanes<N1>());
-        wall_kernel<N1, C><<<grid, block, 0, s>>>((typename C::T*)f, p);
-        return cudaGetLastError();
+        return launch_pdl(wall_kernel<N1, C>, grid, block, 0, s, (typename C::T*)f, p);
     }
     template <class C>
     static cudaError_t halo_c(void* f, const KParams& p, cudaStream_t s) {
