@@ -247,20 +247,29 @@ def noneq_coefficients(oracle, f=None) -> np.ndarray:
     return project(f - equilibrium_field(oracle, f), oracle.vs).reshape(-1, N_OUT)
 
 
-def closure_coefficients(oracle, p: dict, mu, inv_sigma, out_scale, f=None) -> np.ndarray:
-    """o[ny * nx, 12] = out_scale * MLP(normalised 3 x 3 features of the stored state f)."""
+def closure_coefficients(oracle, p: dict, mu, inv_sigma, out_scale, f=None, bf16=False) -> np.ndarray:
+    """o[ny * nx, 12] = out_scale * MLP(normalised 3 x 3 features of the stored state f).
+    With bf16, the network's inputs and hidden activations are rounded to BF16 where a BF16
+    network stores them (everything else in FP64), so that a BF16 implementation can be held
+    to the rounding of its accumulations rather than to that of its storage."""
     f = oracle.f if f is None else f
     X = neighbourhood(cell_features(f, oracle.vs), mu, inv_sigma)
-    Y, _ = forward(p, X)
+    if bf16:
+        X = bf16_round(X)
+        H1 = bf16_round(gelu(X @ p["W1"].T + p["b1"]))
+        H2 = bf16_round(gelu(H1 @ p["W2"].T + p["b2"]))
+        Y = H2 @ p["W3"].T + p["b3"]
+    else:
+        Y, _ = forward(p, X)
     return Y * np.asarray(out_scale, dtype=np.float64)
 
 
-def closure_step(oracle, p: dict, mu, inv_sigma, out_scale) -> np.ndarray:
+def closure_step(oracle, p: dict, mu, inv_sigma, out_scale, bf16=False) -> np.ndarray:
     """Advance oracle.f by one learned coarse step: stream; the coefficients come from the
     streamed state; each cell becomes f_eq(its moments) + the correction.  Returns the
-    coefficients used."""
+    coefficients used.  bf16: as closure_coefficients."""
     streamed = oracle.stream_only()
-    o = closure_coefficients(oracle, p, mu, inv_sigma, out_scale, f=streamed)
+    o = closure_coefficients(oracle, p, mu, inv_sigma, out_scale, f=streamed, bf16=bf16)
     nxt = equilibrium_field(oracle, streamed) + correction(o.reshape(oracle.ny, oracle.nx, N_OUT), oracle.vs)
     oracle.f[...] = nxt
     return o

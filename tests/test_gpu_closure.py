@@ -262,18 +262,23 @@ def test_closure_step_matches_oracle_and_conserves(tv):
     scale = np.full(12, 2e-4)
     m = tv.Mlp(nx * ny)
     m.set_params(cl.pack(p).astype(np.float32))
+    o64 = oracle.Oracle(nx, ny, "D2Q16", tau=0.55)
+    o64.f[...] = o.f
     s0 = sim.conserved_sums()
     coeffs = []
     for _ in range(3):
-        coeffs.append(cl.closure_step(o, p, mu, isg, scale))
+        coeffs.append(cl.closure_step(o, p, mu, isg, scale, bf16=True))
+        cl.closure_step(o64, p, mu, isg, scale)
         tv.step_closure(sim, m, mu, isg, scale, 1)
     got = sim.populations_f64()
     corr_max = max(np.max(np.abs(c)) for c in coeffs)
     assert corr_max > 1e-6
-    # per step: network error (BF16 activations and inputs) <= 3e-2 of the coefficient scale,
-    # times max_l w_l sum_k |psi_k(c_l)| (< 1.5 for D2Q16), over 3 steps
-    tol = 3 * 3e-2 * corr_max * 1.5
-    assert np.max(np.abs(got - o.f)) <= tol
+    # against the oracle with BF16 inputs and activations: per step the network's FP32
+    # accumulation (an occasional BF16 activation rounded the other way) <= 4e-3 of the
+    # coefficient scale, times max_l w_l sum_k |psi_k(c_l)| (< 1.5 for D2Q16), over 3 steps
+    assert np.max(np.abs(got - o.f)) <= 3 * 4e-3 * corr_max * 1.5
+    # and against the all-FP64 network: the BF16 storage itself, <= 3e-2 of the scale per step
+    assert np.max(np.abs(got - o64.f)) <= 3 * 3e-2 * corr_max * 1.5
     s1 = sim.conserved_sums()
     for k in range(4):
         assert abs(s1[k] - s0[k]) <= 1e-12 * max(1.0, abs(s0[0]))

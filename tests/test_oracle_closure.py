@@ -230,3 +230,26 @@ def test_closure_step_with_zero_network_is_bgk_with_unit_relaxation():
     cl.closure_step(a, p, np.zeros(6), np.ones(6), np.ones(12))
     b.run(1)
     assert np.max(np.abs(a.f - b.f)) < 1e-15
+
+
+def test_bf16_storage_option_rounds_inputs_and_hidden_layers_only():
+    """closure_coefficients(bf16=True): a network whose inputs and hidden activations are already
+    BF16 values is unchanged by the option; otherwise it differs from the FP64 network by BF16
+    rounding only (a few 2^-8 of the output scale); and the all-zero network gives its output
+    bias exactly either way."""
+    import workloads
+    nx = ny = 8
+    o = oracle.Oracle(nx, ny, "D2Q16", tau=0.6)
+    o.init_moments(*workloads.random_smooth(nx, ny, seed=5, amp_u=0.05, amp_T=0.03))
+    mu, isg, scale = np.zeros(6), np.full(6, 10.0), np.full(12, 1e-3)
+    p = cl.init_params(14, scale=1.5)
+    a = cl.closure_coefficients(o, p, mu, isg, scale)
+    b = cl.closure_coefficients(o, p, mu, isg, scale, bf16=True)
+    assert 0 < np.max(np.abs(a - b)) <= 3e-2 * np.max(np.abs(a))
+    # zero first and second layers with BF16-exact biases whose GELU is BF16-exact (0): only
+    # the rounding of the inputs could act, and W1 = 0 removes it
+    z = {name: np.zeros(shape) for name, shape in cl.PARAM_SHAPES}
+    z["b3"] = np.linspace(-1.0, 1.0, 12)
+    for flag in (False, True):
+        assert np.array_equal(cl.closure_coefficients(o, z, mu, isg, scale, bf16=flag),
+                              np.broadcast_to(z["b3"] * scale, (nx * ny, 12)))
