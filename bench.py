@@ -216,6 +216,38 @@ def kernel_traffic(workload, form, tile=None):
     return e.get("dram_bytes_per_launch")
 
 
+# SM instruction issue of one GB300: 152 SMs x 4 schedulers x 1 warp instruction per cycle x
+# 32 threads at the 2070 MHz maximum SM clock, in thread instructions per second
+ISSUE_PEAK = 152 * 4 * 32 * 2.07e9
+
+
+def kernel_instructions(workload, form, tile=None):
+    """Thread instructions per cell update of the sweep kernel from the committed ncu summary
+    (same conditions as kernel_traffic), else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        e = json.load(open(path)).get("%s/%s" % (workload, form))
+    except (OSError, ValueError):
+        return None
+    if not e or e.get("csrc_sha256") != csrc_hash(e.get("csrc_files")):
+        return None
+    if tile is not None and e.get("tile") is not None and list(e["tile"]) != list(tile):
+        return None
+    return e.get("thread_instructions_per_cell")
+
+
+def issue_roofline(workload, form, tile, cells, s_per_tstep):
+    """The sweep against the SM instruction-issue rate: recorded instructions per cell x cells
+    per second of the whole time step (other kernels of the step counted as sweep time, so a
+    lower bound), or None without a record."""
+    ipc = kernel_instructions(workload, form, tile)
+    if ipc is None:
+        return None
+    achieved = ipc * cells / s_per_tstep
+    return {"bound": "alu", "achieved": achieved / 1e12, "peak": ISSUE_PEAK / 1e12,
+            "unit": "T thread-instructions/s", "frac": achieved / ISSUE_PEAK, "instructions_per_cell": ipc}
+
+
 def traffic_per_time_step(workload, form, tile=None):
     """kernel_traffic divided by the time steps one launch advances (a dataflow launch runs many)."""
     b = kernel_traffic(workload, form, tile)
@@ -401,7 +433,8 @@ def run_ours(args, w, rank, world, local_rank, sub=None):
                      "peak_kind": peak_kind, "bytes_per_cell": bytes_per_cell,
                      "traffic": kernel_traffic(args.workload, chosen, line_tile),
                      "traffic_per_time_step": traffic_per_time_step(args.workload, chosen, line_tile),
-                     "algorithmic_bytes_per_time_step": bytes_per_cell * cells},
+                     "algorithmic_bytes_per_time_step": bytes_per_cell * cells,
+                     "issue": issue_roofline(args.workload, chosen, line_tile, cells, avg_launch_s)},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * 8 * cells,
                 "d2h_bytes_per_step": 4 * 8 * cells},
         # sweeps (+ wall kernel per step) and, with a refreshed per-row reference, the five kernels
@@ -537,7 +570,9 @@ def sub_record(name, w, sim, form, tuning, trials, timed, fields, tv, K=3, W=2):
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                         "peak_kind": peak_kind, "bytes_per_cell": bpc,
                         "traffic": kernel_traffic(name, form, form_tile(tv, sim, form, tuning["best"])
-                                                  if tuning else None)}}
+                                                  if tuning else None),
+                        "issue": issue_roofline(name, form, form_tile(tv, sim, form, tuning["best"])
+                                                if tuning else None, nx * ny, s_per_tstep)}}
     if w.get("refresh"):
         rec["deviation_reference"] = "per row, %s kind, refreshed every %d time steps inside the timed region" % (
             w.get("ref_kind", "equilibrium"), w["refresh"])
