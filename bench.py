@@ -47,11 +47,11 @@ WORKLOADS = {
                nx=64, ny=64, velset="D2Q16", storage="fp64", plain_storage="fp64", tau=0.8, walls=None, tsteps=200),
     "c2": dict(desc="D2Q36 4096x512 thermal Couette FP16-deviation storage tau=0.9, walls T=1.0/1.1, u_top=0.1, "
                     "1000 time steps", nx=4096, ny=512, velset="D2Q36", storage="fp16_dev", plain_storage="fp16_dev",
-               tau=0.9, walls=(0.0, 1.0, 0.1, 1.1), tsteps=1000, reference="rows", refresh=20, ref_kind="mean"),
+               tau=0.9, walls=(0.0, 1.0, 0.1, 1.1), tsteps=1000, reference="rows", refresh=100, ref_kind="mean"),
     "c2_bf16": dict(desc="D2Q36 4096x512 thermal Couette BF16-deviation storage tau=0.9, walls T=1.0/1.1, "
                          "u_top=0.1, 1000 time steps", nx=4096, ny=512, velset="D2Q36", storage="bf16_dev",
                     plain_storage="bf16_dev", tau=0.9, walls=(0.0, 1.0, 0.1, 1.1), tsteps=1000, reference="rows",
-                    refresh=20, ref_kind="mean"),
+                    refresh=40, ref_kind="mean"),
 }
 
 # configurations measured beside the default line (their own sub-records in the JSON line)

@@ -98,10 +98,12 @@ def test_half_storage_walls_d2q36(tv, storage, bound, form):
 
 
 # The half-storage parity claims on the channel workload (bar 1e-3 after 1000 steps): the per-row
-# reference refreshed every 20 steps from the rows' mean populations (kind "mean"), which leaves
-# only the departures from the row averages in the stored deviations -- for both BF16 and FP16 --
-# and FP16 with the rows' mean equilibria refreshed every 100 steps.
-C2_PARITY = [("bf16_dev", 20, "mean"), ("fp16_dev", 20, "mean"), ("fp16_dev", 100, "equilibrium")]
+# reference refreshed from the rows' mean populations (kind "mean"), which leaves only the
+# departures from the row averages since the last refresh in the stored deviations -- every 20
+# or 40 steps for BF16 (the bench's channel: 40), every 20 or 100 steps for FP16 (the bench's:
+# 100) -- and FP16 with the rows' mean equilibria refreshed every 100 steps.
+C2_PARITY = [("bf16_dev", 20, "mean"), ("bf16_dev", 40, "mean"), ("fp16_dev", 20, "mean"), ("fp16_dev", 100, "mean"),
+             ("fp16_dev", 100, "equilibrium")]
 # Regression checks at measured levels with margin, not parity claims: with the start's profile
 # held fixed (refresh 0) the top wall's shear layer, where u climbs to 0.1 against u_ref = 0,
 # dominates the FP16 u error; BF16 against the rows' mean equilibria keeps their non-equilibrium
