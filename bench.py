@@ -44,7 +44,10 @@ WORKLOADS = {
                     nx=4096, ny=4096, velset="D2Q16", storage="fp32_dev", plain_storage="fp32", tau=0.7, walls=None,
                     tsteps=100),
     "c0": dict(desc="D2Q16 64x64 periodic FP64 tau=0.8 shear wave, 200 time steps",
-               nx=64, ny=64, velset="D2Q16", storage="fp64", plain_storage="fp64", tau=0.8, walls=None, tsteps=200),
+               nx=64, ny=64, velset="D2Q16", storage="fp64", plain_storage="fp64", tau=0.8, walls=None, tsteps=200,
+               note="1 MB of state, resident in L2: its time per step is FP64 arithmetic on 4096 cells (GB300's "
+                    "FP64 rate is a small fraction of its FP32 rate) and launch latency, so its HBM roofline "
+                    "fraction is not meaningful"),
     "c2": dict(desc="D2Q36 4096x512 thermal Couette FP16-deviation storage tau=0.9, walls T=1.0/1.1, u_top=0.1, "
                     "1000 time steps", nx=4096, ny=512, velset="D2Q36", storage="fp16_dev", plain_storage="fp16_dev",
                tau=0.9, walls=(0.0, 1.0, 0.1, 1.1), tsteps=1000, reference="rows", refresh=100, ref_kind="mean"),
@@ -55,7 +58,7 @@ WORKLOADS = {
 }
 
 # configurations measured beside the default line (their own sub-records in the JSON line)
-EXTRA = ("c1_4096", "c2", "c2_bf16", "c3")
+EXTRA = ("c1_4096", "c2", "c2_bf16", "c3", "c0")
 
 BATCH = dict(desc="256 independent periodic D2Q16 domains, sides drawn from {128,256,512,768,1024}, tau~U[0.55,1.5], "
                    "Mach~U[0.05,0.3], seeded fields, FP32 populations; the bench step's 20 time steps as one "
@@ -556,7 +559,8 @@ def cpu_baseline(name, w, fields, sims=None, target_s=10.0):
 def sub_record(name, w, sim, form, tuning, trials, timed, fields, tv, K=3, W=2):
     """Compact record of a configuration measured beside the default line: K timed bench steps
     after W, MLUPS and the HBM roofline fraction, and the GPU against the oracle (a channel: after
-    the full run on an 8-column strip; a periodic grid: after a few time steps on the full grid)."""
+    the full run on an 8-column strip; a periodic grid: after its whole run if small, else a few
+    time steps, on the full grid)."""
     import oracle
     nx, ny, tsteps = w["nx"], w["ny"], w["tsteps"]
     ms = timed(sim, K, W)
@@ -576,6 +580,8 @@ def sub_record(name, w, sim, form, tuning, trials, timed, fields, tv, K=3, W=2):
     if w.get("refresh"):
         rec["deviation_reference"] = "per row, %s kind, refreshed every %d time steps inside the timed region" % (
             w.get("ref_kind", "equilibrium"), w["refresh"])
+    if w.get("note"):
+        rec["note"] = w["note"]
     cores = _oracle_threads()
     if w["walls"]:
         o = oracle.Oracle(8, ny, w["velset"], tau=w["tau"], dt=1.0, walls=w["walls"], threads=cores)
@@ -590,7 +596,7 @@ def sub_record(name, w, sim, form, tuning, trials, timed, fields, tv, K=3, W=2):
     else:
         o = oracle.Oracle(nx, ny, w["velset"], tau=w["tau"], dt=1.0, walls=w["walls"], threads=cores)
         o.init_moments(*fields)
-        checked = 3
+        checked = tsteps if nx * ny * tsteps <= 1 << 22 else 3  # a small grid: its whole run
         t0 = time.perf_counter()
         o.run(checked)
         dt = time.perf_counter() - t0
