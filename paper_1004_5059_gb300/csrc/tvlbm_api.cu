@@ -247,6 +247,19 @@ int create_common(int nx, int ny, int velset, double tau, double dt, const tvlbm
     return TVLBM_OK;
 }
 
+// The first cell (lowest index) whose fields are invalid -- rho or T not > 0, or any of the four
+// not finite -- into *first (left at its initial all-ones value when every cell is valid).
+__global__ void __launch_bounds__(256) validate_fields_kernel(const double* __restrict__ d, long long n,
+                                                              unsigned long long* __restrict__ first) {
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const double rho = d[k], ux = d[n + k], uy = d[2 * n + k], T = d[3 * n + k];
+        if (!(rho > 0.0) || !(T > 0.0) || !isfinite(rho) || !isfinite(T) || !isfinite(ux) || !isfinite(uy))
+            atomicMin(first, (unsigned long long)k);
+    }
+}
+
+// Host fields -> device scratch, checked on the device (nothing else is written when a cell is
+// invalid), then the initial equilibrium into both population buffers.
 int upload_fields_and_init(tvlbm_ctx* c, const double* rho, const double* ux, const double* uy, const double* T) {
     const size_t n = (size_t)c->nx * c->ny;
     double* d = (double*)dptr(c, c->L.off_mom);
@@ -254,6 +267,16 @@ int upload_fields_and_init(tvlbm_ctx* c, const double* rho, const double* ux, co
     for (int k = 0; k < 4; ++k)
         TVLBM_CUDA(c, cudaMemcpyAsync(d + k * n, src[k], n * sizeof(double), cudaMemcpyHostToDevice, c->stream),
                    "cudaMemcpyAsync fields");
+    unsigned long long* first = (unsigned long long*)dptr(c, c->L.off_part);  // reduction scratch, free here
+    TVLBM_CUDA(c, cudaMemsetAsync(first, 0xFF, sizeof(*first), c->stream), "cudaMemsetAsync");
+    const long long blocks = ((long long)n + 255) / 256 < 4096 ? ((long long)n + 255) / 256 : 4096;
+    validate_fields_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(d, (long long)n, first);
+    TVLBM_CUDA(c, cudaGetLastError(), "field check kernel");
+    unsigned long long bad = 0;
+    TVLBM_CUDA(c, cudaMemcpyAsync(&bad, first, sizeof(bad), cudaMemcpyDeviceToHost, c->stream), "cudaMemcpyAsync check");
+    TVLBM_CUDA(c, cudaStreamSynchronize(c->stream), "field check synchronize");
+    if (bad != ~0ull)
+        return fail(c, TVLBM_EINVAL, "init field invalid at cell %llu (rho, T must be > 0 and finite)", bad);
     for (int b = 0; b < 2; ++b) {
         TVLBM_CUDA(c, c->kt->init(c->storage, d, dptr(c, c->L.off_f[b]), c->kp, c->stream), "init kernel");
     }
@@ -535,15 +558,10 @@ int tvlbm_set_tile(tvlbm_ctx* c, int config) {
 int tvlbm_init_moments(tvlbm_ctx* c, const double* rho, const double* ux, const double* uy, const double* T) {
     if (!c) return TVLBM_EINVAL;
     if (!rho || !ux || !uy || !T) return fail(c, TVLBM_EINVAL, "null field pointer");
-    const size_t n = (size_t)c->nx * c->ny;
-    for (size_t k = 0; k < n; ++k) {
-        if (!(rho[k] > 0.0) || !(T[k] > 0.0) || !isfinite(rho[k]) || !isfinite(T[k]) || !isfinite(ux[k]) ||
-            !isfinite(uy[k]))
-            return fail(c, TVLBM_EINVAL, "init field invalid at cell %zu (rho, T must be > 0 and finite)", k);
-    }
     cudaSetDevice(c->device);
-    c->cur = 0;
-    return upload_fields_and_init(c, rho, ux, uy, T);
+    const int rc = upload_fields_and_init(c, rho, ux, uy, T);  // checks the fields on the device first
+    if (rc == TVLBM_OK) c->cur = 0;
+    return rc;
 }
 
 static int run_steps(tvlbm_ctx* c, int n);
