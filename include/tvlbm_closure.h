@@ -18,7 +18,9 @@
  * whose coefficients the network predicts from the streamed (pre-collision) state.  The
  * conserved moments come from the streaming, the non-conserved ones from the network.
  *
- * Network: 54 inputs -> 128 GELU -> 128 GELU -> 12 outputs, GELU(z) = z Phi(z) (exact, erf).
+ * Network: 54 inputs -> 128 GELU -> 128 GELU -> 12 outputs, GELU(z) = z Phi(z), Phi by the
+ * erf approximation of Abramowitz & Stegun eq. 7.1.26 (|error| <= 1.5e-7; see
+ * tvlbm_mlp_activation).
  * Inputs of cell (x, y): for (dy, dx) in {-1,0,1}^2 (row-major, dy outer) the 6 features
  * (rho, u_x, u_y, T, Pi^neq_xy, Pi^neq_xx - Pi^neq_yy) of cell (x+dx, y+dy) (periodic), each
  * normalised as (value - mu_q) * inv_sigma_q; Pi^neq = sum_l f_l c c - rho u u.
@@ -79,6 +81,12 @@ int tvlbm_mlp_loss_grad(tvlbm_mlp *m, const void *x, const float *ystar, int row
 int tvlbm_mlp_adam(tvlbm_mlp *m, float lr, float beta1, float beta2, float eps);
 
 const char *tvlbm_mlp_last_error(const tvlbm_mlp *m);
+
+/* The network's activation as its kernels evaluate it, on n device values: g[i] = GELU(z[i]) and
+ * dg[i] = GELU'(z[i]) = Phi(z) + z phi(z) (either output may be NULL).  z, g, dg: device FP32
+ * arrays of n entries, caller-owned.  Asynchronous on `stream` (a cudaStream_t; NULL = legacy
+ * default).  Errors: EINVAL (n < 0, z NULL), ECUDA. */
+int tvlbm_mlp_activation(const float *z, float *g, float *dg, int n, void *stream);
 
 /* ---- closure on a context (D2Q16, periodic, storage FP64 / FP32 / FP32_DEV, default
  * deviation reference); asynchronous on the context's stream unless stated ---------------- */

@@ -126,6 +126,7 @@ def _load_library() -> ctypes.CDLL:
         "tvlbm_mlp_loss_grad": (_I, [_P, _P, _P, _I, _DP, _FP]),
         "tvlbm_mlp_adam": (_I, [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
         "tvlbm_mlp_last_error": (ctypes.c_char_p, [_P]),
+        "tvlbm_mlp_activation": (_I, [_P, _P, _P, _I, _P]),
         "tvlbm_closure_moments": (_I, [_P, _P]),
         "tvlbm_closure_features": (_I, [_P, _FP, _FP, _P]),
         "tvlbm_closure_project": (_I, [_P, _P, _FP, _P]),
@@ -641,6 +642,21 @@ def closure_noneq(sim, o, inv_scale=None):
     isc = _fp(_f32(inv_scale, TVLBM_MLP_OUT)) if inv_scale is not None else None
     _check(_lib.tvlbm_closure_noneq(sim.ctx, isc, _dev_ptr(o, torch.float32, (sim.nx * sim.ny, TVLBM_MLP_OUT_PAD))),
            sim.ctx)
+
+
+def mlp_activation(z, stream=None):
+    """The network's activation as its kernels evaluate it: (GELU(z), GELU'(z)) for a device FP32
+    tensor z, as new device tensors."""
+    import torch
+    z = z.contiguous()
+    if z.dtype != torch.float32 or not z.is_cuda:
+        raise TypeError("z must be a CUDA float32 tensor")
+    g, dg = torch.empty_like(z), torch.empty_like(z)
+    s = stream if stream is not None else torch.cuda.current_stream(z.device).cuda_stream
+    rc = _lib.tvlbm_mlp_activation(_P(z.data_ptr()), _P(g.data_ptr()), _P(dg.data_ptr()), int(z.numel()), _P(s))
+    if rc != TVLBM_OK:
+        raise TvlbmError(rc, _lib.tvlbm_strerror(rc).decode())
+    return g, dg
 
 
 def downsample(fine, coarse):

@@ -42,9 +42,34 @@ constexpr int kMaxSplits = 128;
 
 using bf16 = __nv_bfloat16;
 
-__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+// GELU g(z) = z Phi(z), Phi(z) = (1 + erf(z / sqrt 2)) / 2, and g'(z) = Phi(z) + z phi(z).  erf by
+// the rational approximation of Abramowitz & Stegun, Handbook of Mathematical Functions, eq.
+// 7.1.26 (after Hastings): erf(x) = 1 - (a1 t + ... + a5 t^5) exp(-x^2), t = 1 / (1 + p x), x >= 0,
+// |error| <= 1.5e-7, odd in x; the reciprocal and the exponential by the hardware approximations.
+// The network stores its activations in BF16 (relative step 2^-8), so the error is invisible.
+// E2 = exp(-x^2) = exp(-z^2 / 2) also gives phi(z) = E2 / sqrt(2 pi).
+__device__ __forceinline__ float erf_as(float x, float& e2) {
+    const float ax = fabsf(x);
+    const float t = __fdividef(1.0f, fmaf(0.3275911f, ax, 1.0f));
+    const float poly =
+        t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f), 0.254829592f);
+    e2 = __expf(-ax * ax);
+    return copysignf(fmaf(-poly, e2, 1.0f), x);
+}
+__device__ __forceinline__ float gelu_f(float z) {
+    float e2;
+    return 0.5f * z * (1.0f + erf_as(z * 0.70710678118654752f, e2));
+}
 __device__ __forceinline__ float gelu_grad_f(float z) {
-    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+    float e2;
+    const float er = erf_as(z * 0.70710678118654752f, e2);
+    return fmaf(z * 0.39894228040143268f, e2, 0.5f * (1.0f + er));
+}
+__global__ void activation_kernel(const float* __restrict__ z, float* __restrict__ g, float* __restrict__ dg, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (g) g[i] = gelu_f(z[i]);
+        if (dg) dg[i] = gelu_grad_f(z[i]);
+    }
 }
 __device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
@@ -938,3 +963,11 @@ int tvlbm_mlp_adam(tvlbm_mlp* m, float lr, float beta1, float beta2, float eps) 
 const char* tvlbm_mlp_last_error(const tvlbm_mlp* m) { return m ? m->err : "null network"; }
 
 }  // extern "C"
+
+extern "C" int tvlbm_mlp_activation(const float* z, float* g, float* dg, int n, void* stream) {
+    if (!z || n < 0) return TVLBM_EINVAL;
+    if (n == 0) return TVLBM_OK;
+    const int blocks = (n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024;
+    activation_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(z, g, dg, n);
+    return cudaGetLastError() == cudaSuccess ? TVLBM_OK : TVLBM_ECUDA;
+}

@@ -344,3 +344,24 @@ def test_closure_rejects_unsupported_contexts(tv):
         tv.step_closure(s, m, mu, isg, sc, 1)
     s.close()
     m.close()
+
+
+def test_activation_within_its_error_bound(tv):
+    """The kernels' GELU (erf by Abramowitz & Stegun eq. 7.1.26, |error| <= 1.5e-7) and its
+    derivative on a dense grid: against the exact function in FP64 and against CUDA's own erff
+    (torch.erf), within the approximation's bound plus FP32 rounding."""
+    import torch
+    from scipy.special import erf
+    z = torch.linspace(-12.0, 12.0, 240001, dtype=torch.float32, device="cuda")
+    g, dg = tv.mlp_activation(z)
+    torch.cuda.synchronize()
+    zz = z.cpu().numpy().astype(np.float64)
+    phi_cdf = 0.5 * (1.0 + erf(zz / math.sqrt(2.0)))
+    phi_pdf = np.exp(-0.5 * zz * zz) / math.sqrt(2.0 * math.pi)
+    gg, dd = g.cpu().numpy().astype(np.float64), dg.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(gg - zz * phi_cdf) <= 3e-7 * (np.abs(zz) + 1.0))
+    assert np.all(np.abs(dd - (phi_cdf + zz * phi_pdf)) <= 1e-6)
+    cuda = (0.5 * z * (1.0 + torch.erf(z * 0.70710678118654752))).cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(gg - cuda) <= 3e-7 * (np.abs(zz) + 1.0))
+    assert tv.lib.tvlbm_mlp_activation(None, None, None, 4, None) == tv.TVLBM_EINVAL
+    assert tv.lib.tvlbm_mlp_activation(z.data_ptr(), None, None, -1, None) == tv.TVLBM_EINVAL
