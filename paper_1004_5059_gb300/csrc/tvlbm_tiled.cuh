@@ -396,10 +396,10 @@ __device__ __forceinline__ bool tile_compute(const unsigned char* base, int x0, 
     return imaged;
 }
 
-// Tiled sweep: CTA b owns tile b.  It lets the next step's launch be scheduled at once, and
-// thread 0 waits for the previous grid before starting the Q window loads; warp 0 then waits for
-// them, lane l watching barrier l (and l + 32), while the other warps sleep at the block
-// barrier.  Each thread walks R rows of one column (x-lerp of the previous row carried in
+// Tiled sweep: CTA b owns tile b.  It lets the next step's launch be scheduled at once; warp 0
+// waits for the previous grid and starts the Q window loads, lane l those of windows l and
+// l + 32, then waits for them, lane l watching its own barriers, while the other warps sleep at
+// the block barrier.  Each thread walks R rows of one column (x-lerp of the previous row carried in
 // registers), collides and stores straight to global memory.  Every wait is bounded; a timeout
 // sets the status word and the CTA returns after a bounded drain of its own loads.
 // ROWS: the launch has a per-row deviation reference (a separate instantiation, so the common
@@ -427,16 +427,23 @@ __device__ __forceinline__ void sweep_tiled_body(const Src& src, const KParams& 
     Geom g;
     src.tile(t, p, TX, TY, x0, y0, map, outv, g);
 
-    if (tid == 0) {
-#pragma unroll 1
-        for (int l = 0; l < Q; ++l) mbar_init(&bars[l], 1);
+    if (tid < 32) {
+        // warp 0: lane t sets up and starts windows t and t + 32 (Q <= 64), all lanes at once
+        static_assert(Q <= 64, "two windows per lane");
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+            if (tid + 32 * k < Q) mbar_init(&bars[tid + 32 * k], 1);
         fence_barrier_init();
         pdl_wait();  // the previous step's populations are complete from here on
 #pragma unroll
-        for (int l = 0; l < Q; ++l) {
-            const int i = l % N1, j = l / N1;
-            mbar_arrive_expect_tx(&bars[l], (uint32_t)(BX * Cfg::BY * ES));
-            tma_load_3d(base + l * WIN, map, &bars[l], (x0 + g.hx - p.sh[i] - 1) & ~(A - 1), y0 + HY - p.sh[j] - 1, l);
+        for (int k = 0; k < 2; ++k) {
+            const int l = tid + 32 * k;
+            if (l < Q) {
+                const int i = l % N1, j = l / N1;
+                mbar_arrive_expect_tx(&bars[l], (uint32_t)(BX * Cfg::BY * ES));
+                tma_load_3d(base + l * WIN, map, &bars[l], (x0 + g.hx - p.sh[i] - 1) & ~(A - 1),
+                            y0 + HY - p.sh[j] - 1, l);
+            }
         }
     }
     float* srows = nullptr;
