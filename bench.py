@@ -200,23 +200,32 @@ def csrc_hash(files):
     return h.hexdigest()
 
 
-def kernel_traffic(workload, form, tile=None):
-    """DRAM bytes per sweep launch from the committed ncu summary, if it was taken on the
-    current kernel sources with the same form and tile shape (else None)."""
+def profile_entry(workload, form, tile=None):
+    """The committed ncu record of the sweep kernel of `workload` in `form` (profiles/traffic.json:
+    one record, or a list of them for several tile shapes), if it was taken on the current kernel
+    sources with the same tile shape (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         d = json.load(open(path))
     except (OSError, ValueError):
         return None
-    e = d.get("%s/%s" % (workload, form))
-    if not e:
+    entries = d.get("%s/%s" % (workload, form))
+    if not entries:
         return None
-    # the sources the kernel is built from, as recorded with the counters
-    if e.get("csrc_sha256") != csrc_hash(e.get("csrc_files")):
-        return None
-    if tile is not None and e.get("tile") is not None and list(e["tile"]) != list(tile):
-        return None
-    return e.get("dram_bytes_per_launch")
+    for e in entries if isinstance(entries, list) else [entries]:
+        # the sources the kernel is built from, as recorded with the counters
+        if e.get("csrc_sha256") != csrc_hash(e.get("csrc_files")):
+            continue
+        if tile is not None and e.get("tile") is not None and list(e["tile"]) != list(tile):
+            continue
+        return e
+    return None
+
+
+def kernel_traffic(workload, form, tile=None):
+    """DRAM bytes per sweep launch from the committed ncu summary (profile_entry), else None."""
+    e = profile_entry(workload, form, tile)
+    return e.get("dram_bytes_per_launch") if e else None
 
 
 # SM instruction issue of one GB300: 152 SMs x 4 schedulers x 1 warp instruction per cycle x
@@ -226,17 +235,9 @@ ISSUE_PEAK = 152 * 4 * 32 * 2.07e9
 
 def kernel_instructions(workload, form, tile=None):
     """Thread instructions per cell update of the sweep kernel from the committed ncu summary
-    (same conditions as kernel_traffic), else None."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
-    try:
-        e = json.load(open(path)).get("%s/%s" % (workload, form))
-    except (OSError, ValueError):
-        return None
-    if not e or e.get("csrc_sha256") != csrc_hash(e.get("csrc_files")):
-        return None
-    if tile is not None and e.get("tile") is not None and list(e["tile"]) != list(tile):
-        return None
-    return e.get("thread_instructions_per_cell")
+    (profile_entry), else None."""
+    e = profile_entry(workload, form, tile)
+    return e.get("thread_instructions_per_cell") if e else None
 
 
 def issue_roofline(workload, form, tile, cells, s_per_tstep):
@@ -253,11 +254,10 @@ def issue_roofline(workload, form, tile, cells, s_per_tstep):
 
 def traffic_per_time_step(workload, form, tile=None):
     """kernel_traffic divided by the time steps one launch advances (a dataflow launch runs many)."""
-    b = kernel_traffic(workload, form, tile)
-    if b is None:
+    e = profile_entry(workload, form, tile)
+    if not e or e.get("dram_bytes_per_launch") is None:
         return None
-    d = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-    return b / d["%s/%s" % (workload, form)].get("time_steps_per_launch", 1)
+    return e["dram_bytes_per_launch"] / e.get("time_steps_per_launch", 1)
 
 
 def run_ours(args, w, rank, world, local_rank, sub=None):

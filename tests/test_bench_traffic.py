@@ -8,6 +8,13 @@ import shutil
 import bench
 
 
+def _records(d):
+    """(key, record) for every record; a key may hold one record or a list (several tile shapes)."""
+    for key, v in d.items():
+        for rec in v if isinstance(v, list) else [v]:
+            yield key, rec
+
+
 def _copy_tree(tmp_path):
     root = tmp_path / "repo"
     (root / "profiles").mkdir(parents=True)
@@ -18,7 +25,7 @@ def _copy_tree(tmp_path):
 
 def test_recorded_traffic_for_the_captured_kernel_only():
     d = json.load(open(os.path.join(bench.ROOT, "profiles", "traffic.json")))
-    for key, e in d.items():
+    for key, e in _records(d):
         workload, form = key.split("/")
         if e["csrc_sha256"] != bench.csrc_hash(e["csrc_files"]):
             # the kernel changed since its counters were taken: no traffic figure
@@ -37,7 +44,7 @@ def test_changed_source_voids_the_record(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(root))
     d = json.load(open(root / "profiles" / "traffic.json"))
     # as if every record had just been captured on the copied sources
-    for rec in d.values():
+    for _, rec in _records(d):
         rec["csrc_sha256"] = bench.csrc_hash(rec["csrc_files"])
     json.dump(d, open(root / "profiles" / "traffic.json", "w"))
     e = d["c1/flow"]
@@ -45,7 +52,7 @@ def test_changed_source_voids_the_record(tmp_path, monkeypatch):
     # a source the records do not name leaves them valid
     other = root / "paper_1004_5059_gb300" / "csrc" / "tvlbm_mlp.cu"
     other.write_text(other.read_text() + "\n// changed\n")
-    for key, rec in d.items():
+    for key, rec in _records(d):
         assert "tvlbm_mlp.cu" not in rec["csrc_files"]
         assert bench.kernel_traffic(*key.split("/"), rec["tile"]) == rec["dram_bytes_per_launch"]
     # a named one voids every record built from it
