@@ -853,7 +853,8 @@ FV = dict(desc="the paper's finite-volume scheme (Eq. FVLB + Prandtl term, tau_g
 
 
 def run_fv(args, rank, world, local_rank):
-    """Throughput of the finite-volume scheme (two kernels per step: collision term, update)."""
+    """Throughput of the finite-volume scheme: one fused kernel per step (collision term of each
+    block in shared memory, then the update), with the two-kernel form timed beside it."""
     import torch
     import paper_1004_5059_gb300 as tv
     torch.cuda.set_device(local_rank)
@@ -868,6 +869,23 @@ def run_fv(args, rank, world, local_rank):
     sim.set_scheme("fvlb", FV["tau_g"])
     sim.init_moments(*fields)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def timed(fused, steps, warmup):
+        sim.set_fv_fused(fused)
+        for _ in range(warmup):
+            sim.step(tsteps)
+        torch.cuda.synchronize()
+        evs = []
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sim.step(tsteps)
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs)
+
     for _ in range(args.warmup):
         sim.step(tsteps)
     torch.cuda.synchronize()
@@ -876,26 +894,24 @@ def run_fv(args, rank, world, local_rank):
         dist.barrier()
     clocks = Clocks(local_rank)
     clocks.start()
-    evs = []
-    for _ in range(args.steps):
-        flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        sim.step(tsteps)
-        b.record(stream)
-        evs.append((a, b))
-    torch.cuda.synchronize()
+    ms = timed(True, args.steps, 0)
     clk = clocks.stop()
-    ms = sum(a.elapsed_time(b) for a, b in evs)
     ms_max = max_over_ranks(ms, world, dev)
     cells = nx * ny
     value = aggregate_mlups(world, cells, tsteps, args.steps, ms_max / 1e3)
-    # algorithmic bytes per cell update: collision term reads Q and writes Q values, the update
-    # reads 2 Q distinct values (f and the collision term; the 3 x 3 neighbours come from cache)
-    # and writes Q: 5 Q x 4 bytes
-    bpc = 5 * 16 * 4
+    # algorithmic bytes per cell update of the fused kernel: read Q and write Q values (the halo
+    # ring's re-reads come from L2); the two-kernel form: the collision term reads Q and writes Q,
+    # the update reads 2 Q distinct values (f and the collision term; the 3 x 3 neighbours from
+    # cache) and writes Q
+    bpc, bpc_split = 2 * 16 * 4, 5 * 16 * 4
     peak, peak_kind = measured_peak_hbm()
     achieved = bpc * cells / (ms / 1e3 / (args.steps * tsteps)) / 1e9
+    split_steps = max(1, min(args.steps, 3))
+    ms_split = timed(False, split_steps, 1)
+    sec_split = ms_split / 1e3 / (split_steps * tsteps)
+    two_kernel = {"value": cells / sec_split / 1e6, "unit": UNIT, "bytes_per_cell": bpc_split,
+                  "roofline_frac": bpc_split * cells / sec_split / 1e9 / peak, "bench_steps": split_steps}
+    sim.set_fv_fused(True)
     pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in fields]
     out = [torch.empty((ny, nx), dtype=torch.float64).pin_memory().numpy() for _ in range(4)]
     torch.cuda.synchronize()
@@ -914,7 +930,8 @@ def run_fv(args, rank, world, local_rank):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_kind": peak_kind, "bytes_per_cell": bpc, "traffic": None},
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 32 * cells, "d2h_bytes_per_step": 32 * cells},
-            "gpu_launches": args.steps * tsteps * 2, "clocks": clk}
+            "two_kernel_form": two_kernel,
+            "gpu_launches": args.steps * tsteps, "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         from oracle import fvlb

@@ -158,6 +158,15 @@ int tvlbm_set_scheme(tvlbm_ctx *ctx, int scheme, double tau_g);
  * after tvlbm_set_scheme(TVLBM_SCHEME_FVLB).  Errors: EINVAL (not the finite-volume scheme). */
 int tvlbm_set_fv_pressure_scaling(tvlbm_ctx *ctx, int enable);
 
+/* Finite-volume scheme: one fused kernel per step (fused = 1, default) or two (fused = 0).  The
+ * fused kernel computes the collision term of Eq. OMEGAFVLB for a block of cells in shared memory
+ * and updates the block's inner cells from it (Eq. FVLB): Q values read and Q written per cell
+ * update.  The two-kernel form stores the collision term of every cell in the buffer
+ * tvlbm_set_scheme allocates and reads it back in the update (5 Q values per cell update).  Both
+ * run the same arithmetic and give the same populations bit for bit.  May be called at any time;
+ * takes effect at the next step.  Errors: EINVAL (null context). */
+int tvlbm_set_fv_fused(tvlbm_ctx *ctx, int fused);
+
 /* Finite-volume scheme on a channel (a context created with TVLBM_BC_WALLS): the first and
  * last node rows are wall nodes (walls on the nodes, unlike the volumetric scheme's faces).
  * Populations arriving at a wall node advance with the one-sided stencils of Eq. FVLB2; the

@@ -77,6 +77,7 @@ def _load_library() -> ctypes.CDLL:
         "tvlbm_set_scheme": (_I, [_P, _I, _D]),
         "tvlbm_set_fv_walls": (_I, [_P, _I, _I, _DP]),
         "tvlbm_set_fv_pressure_scaling": (_I, [_P, _I]),
+        "tvlbm_set_fv_fused": (_I, [_P, _I]),
         "tvlbm_set_reference": (_I, [_P, _D, _D, _D]),
         "tvlbm_set_reference_rows": (_I, [_P, _P, _P, _P]),
         "tvlbm_set_reference_refresh": (_I, [_P, _I]),
@@ -369,6 +370,10 @@ class Simulation:
         if yn is not None and yn.shape != (self.ny,):
             raise ValueError("y_nodes must hold ny positions")
         _check(_lib.tvlbm_set_fv_walls(self.ctx, 1 if exact else 0, int(nr_iters), _dp(yn)), self.ctx)
+
+    def set_fv_fused(self, fused=True):
+        """Finite-volume scheme: one fused kernel per step (default) or the two-kernel form."""
+        _check(_lib.tvlbm_set_fv_fused(self.ctx, 1 if fused else 0), self.ctx)
 
     def set_fv_pressure_scaling(self, enable=True):
         """Finite-volume scheme: tau -> tau / p, tau_g -> tau_g / p with p = rho T."""

@@ -36,6 +36,7 @@ struct tvlbm_ctx {
     double* fv_wall_eq;               // finite-volume channel: wall equilibria [2][nx][2] (device)
     int fv_exact, fv_nr_iters;        // finite-volume channel: Newton-Raphson imposition, iterations
     int fv_pscale;                    // finite-volume scheme: tau, tau_g divided by the local pressure
+    int fv_split;                     // finite-volume scheme: two kernels per step (0: one fused kernel)
     unsigned char* ref_mem;           // per-row deviation reference: one device allocation holding
     double* ref_rowd;                 //   the live tables (KParams::rowd / rowf),
     float* ref_rowf;

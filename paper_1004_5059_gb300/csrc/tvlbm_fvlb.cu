@@ -7,8 +7,10 @@
 // and the collision term of Eq. OMEGAFVLB: BGK plus the Prandtl-number term
 // (1 / tau_g) f_eq / (rho T^2) Pi : (c - u)(c - u), applied without its components along the
 // collision invariants (an exact Maxwellian has none; a truncated equilibrium leaves a residue).
-// Two kernels per step: the collision term of every cell (stored with the periodic frame images
-// in a population-sized buffer), then the update, which reads both fields at the 3 x 3 cells.
+// One fused kernel per step (fv_fused_kernel: the collision term of a block of cells in shared
+// memory, then the update of its inner cells), or, as the two-kernel form, the collision term of
+// every cell (stored with the periodic frame images in a population-sized buffer) and then the
+// update, which reads both fields at the 3 x 3 cells.  Both give the same populations.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
@@ -48,23 +50,20 @@ constexpr int fv_omega_minb() {
     return sizeof(typename C::R) == 4 ? (N1 <= 4 ? 4 : 2) : (N1 == 3 ? 3 : (N1 == 4 ? 2 : 1));
 }
 
+// Collision term of Eq. OMEGAFVLB at one cell from its populations s: BGK, plus with tau_g the
+// Prandtl term less its components along the collision invariants.
 template <int N1, class C>
-__global__ void __launch_bounds__(256, fv_omega_minb<N1, C>()) fv_omega_kernel(const typename C::T* __restrict__ f,
-                                                       typename C::T* __restrict__ om, const KParams p,
-                                                       const FvParams fp) {
+__device__ __forceinline__ void fv_omega_cell(const typename C::R (&s)[N1 * N1], const KParams& p, const FvParams& fp,
+                                              typename C::R (&w)[N1 * N1]) {
     using R = typename C::R;
     constexpr int Q = N1 * N1;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= p.nx || y >= p.ny) return;
-    R s[Q];
     R rho = 0, jx = 0, jy = 0, e2 = 0;
 #pragma unroll
     for (int j = 0; j < N1; ++j)
 #pragma unroll
         for (int i = 0; i < N1; ++i) {
-            const R v = C::ld(f + sidx(p, i + N1 * j, x, y));
+            const R v = s[i + N1 * j];
             const R cx = kx<R>(p, i), cy = kx<R>(p, j);
-            s[i + N1 * j] = v;
             rho += v;
             jx += v * cx;
             jy += v * cy;
@@ -76,7 +75,6 @@ __global__ void __launch_bounds__(256, fv_omega_minb<N1, C>()) fv_omega_kernel(c
     cell_equilibrium<N1, false, R>(p, rho, ux, uy, T - R(1), eq);
     // tau -> tau / p and tau_g -> tau_g / p (constant dynamic viscosity and conductivity)
     const R ps = fp.pscale ? rho * T : R(1);
-    R w[Q];
     const R itau = (R)fp.inv_tau * ps;
 #pragma unroll
     for (int l = 0; l < Q; ++l) w[l] = -(s[l] - eq[l]) * itau;
@@ -125,6 +123,20 @@ __global__ void __launch_bounds__(256, fv_omega_minb<N1, C>()) fv_omega_kernel(c
                 w[l] += raw[l] - wl * (b[0] + b[1] * cx + b[2] * cy + b[3] * (cx * cx + cy * cy));
             }
     }
+}
+
+template <int N1, class C>
+__global__ void __launch_bounds__(256, fv_omega_minb<N1, C>()) fv_omega_kernel(const typename C::T* __restrict__ f,
+                                                       typename C::T* __restrict__ om, const KParams p,
+                                                       const FvParams fp) {
+    using R = typename C::R;
+    constexpr int Q = N1 * N1;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= p.nx || y >= p.ny) return;
+    R s[Q], w[Q];
+#pragma unroll
+    for (int l = 0; l < Q; ++l) s[l] = C::ld(f + sidx(p, l, x, y));
+    fv_omega_cell<N1, C>(s, p, fp, w);
     store_collided<N1, C>(om, geom_of(p), x, y, w);
 }
 
@@ -136,6 +148,105 @@ constexpr int fv_update_minb() {
     return sizeof(typename C::R) == 4 ? (N1 <= 4 ? 4 : 3) : (N1 <= 3 ? 4 : (N1 == 4 ? 2 : 1));
 }
 
+// The update of Eq. FVLB, interior node: population l at the cell from the 3 x 3 neighbourhood of
+// populations f(dx, dy) and collision terms o(dx, dy) (dy = +1 the next row; P1 east, P2 north,
+// P3 west, P4 south, P5 NE, P6 NW, P7 SW, P8 SE).  ysc: the y spacing factor 2 / (dy_j + dy_j-1)
+// of the stencil (1 on the unit grid).
+template <class R, class F, class O>
+__device__ __forceinline__ R fv_interior(const F& f, const O& o, R ysc, R dt, R cx, R cy) {
+    const R f1 = f(1, 0), f2 = f(0, 1), f3 = f(-1, 0), f4 = f(0, -1);
+    const R f5 = f(1, 1), f6 = f(-1, 1), f7 = f(-1, -1), f8 = f(1, -1);
+    const R gx = R(0.375) * (f1 - f3) + R(0.0625) * (f5 - f6 - f7 + f8);
+    const R gy = ysc * (R(0.375) * (f2 - f4) + R(0.0625) * (f5 + f6 - f7 - f8));
+    const R obar = R(0.5625) * o(0, 0) + R(0.09375) * (o(1, 0) + o(0, 1) + o(-1, 0) + o(0, -1)) +
+                   R(0.015625) * (o(1, 1) + o(-1, 1) + o(-1, -1) + o(1, -1));
+    return f(0, 0) + dt * (obar - cx * gx - cy * gy);
+}
+
+// What the update of a cell row needs to know about the row: wall node (1 bottom, 2 top, 0
+// interior), its fluid-side neighbour row (in), the wall normal's sign, and the y factor (the
+// wall spacing dy_w for a wall node, else the interior spacing factor).
+template <class R>
+struct FvRow {
+    int wall, in;
+    R sgn, yf;
+};
+template <class R>
+__device__ __forceinline__ FvRow<R> fv_row(const KParams& p, const FvParams& fp, int y) {
+    FvRow<R> r;
+    r.wall = fp.walls ? (y == 0 ? 1 : (y == p.ny - 1 ? 2 : 0)) : 0;
+    r.sgn = r.wall == 1 ? R(1) : R(-1);  // n = +y at the bottom, -y at the top
+    r.in = r.wall == 1 ? 1 : -1;
+    if (r.wall) r.yf = fp.dy ? (R)(r.wall == 1 ? fp.dy[0] : fp.dy[p.ny - 2]) : R(1);
+    else r.yf = fp.dy ? (R)(2.0 / (fp.dy[y] + fp.dy[y - 1])) : R(1);
+    return r;
+}
+
+// Population l = i + N1 j of the update of Eq. FVLB at a wall node of a channel (Eq. FVLB2), its
+// neighbourhood read through ld: ld.f(l, dx, dy) and ld.om(l, dx, dy).  Populations arriving at
+// the wall (c . n <= 0) advance with the one-sided stencils into the fluid, the leaving ones keep
+// their imposed values.
+template <int N1, class C, class Ld>
+__device__ __forceinline__ typename C::R fv_wall_one(const Ld& ld, const KParams& p, const FvParams& fp,
+                                                     const FvRow<typename C::R>& rw, int i, int j) {
+    using R = typename C::R;
+    const int l = i + N1 * j;
+    const R cy = kx<R>(p, j);
+    const R f0 = ld.f(l, 0, 0);
+    if (rw.sgn * cy > R(0)) return f0;
+    const int in = rw.in;
+    const R fE = ld.f(l, 1, 0), fW = ld.f(l, -1, 0), fI = ld.f(l, 0, in), fIE = ld.f(l, 1, in), fIW = ld.f(l, -1, in);
+    const R gx = R(0.375) * (fE - fW) + R(0.125) * (fIE - fIW);
+    const R gy = rw.sgn * (R(2) / rw.yf) * (R(0.375) * (fI - f0) + R(0.0625) * (fIE + fIW - fE - fW));
+    const R obar = R(0.5625) * ld.om(l, 0, 0) + R(0.09375) * (ld.om(l, 1, 0) + ld.om(l, -1, 0)) +
+                   R(0.1875) * ld.om(l, 0, in) + R(0.03125) * (ld.om(l, 1, in) + ld.om(l, -1, in));
+    return f0 + (R)fp.dt * (obar - kx<R>(p, i) * gx - cy * gy);
+}
+
+// Population l of the update at an interior node, its neighbourhood read through ld.
+template <int N1, class C, class Ld>
+__device__ __forceinline__ typename C::R fv_interior_one(const Ld& ld, const KParams& p, const FvParams& fp,
+                                                         const FvRow<typename C::R>& rw, int i, int j) {
+    using R = typename C::R;
+    const int l = i + N1 * j;
+    return fv_interior<R>([&](int dx, int dy) { return ld.f(l, dx, dy); },
+                          [&](int dx, int dy) { return ld.om(l, dx, dy); }, rw.yf, (R)fp.dt, kx<R>(p, i),
+                          kx<R>(p, j));
+}
+
+// Every population of the update at the cell of row y (the wall test taken once per cell, so
+// the loads of all velocities can be issued together).
+template <int N1, class C, class Ld>
+__device__ __forceinline__ void fv_update_cell(const Ld& ld, const KParams& p, const FvParams& fp, int y,
+                                               typename C::R (&s)[N1 * N1]) {
+    const FvRow<typename C::R> rw = fv_row<typename C::R>(p, fp, y);
+    if (rw.wall) {
+#pragma unroll
+        for (int j = 0; j < N1; ++j)
+#pragma unroll
+            for (int i = 0; i < N1; ++i) s[i + N1 * j] = fv_wall_one<N1, C>(ld, p, fp, rw, i, j);
+        return;
+    }
+#pragma unroll
+    for (int j = 0; j < N1; ++j)
+#pragma unroll
+        for (int i = 0; i < N1; ++i) s[i + N1 * j] = fv_interior_one<N1, C>(ld, p, fp, rw, i, j);
+}
+
+// Neighbourhood reads of the two-kernel form: both fields in global memory (framed layout).
+template <class C>
+struct FvGlobalNbr {
+    const typename C::T* fb;  // the cell's element in plane 0 of the populations
+    const typename C::T* ob;  // and of the collision term
+    long long plane, pitch;
+    __device__ __forceinline__ typename C::R f(int l, int dx, int dy) const {
+        return C::ld(fb + l * plane + dy * pitch + dx);
+    }
+    __device__ __forceinline__ typename C::R om(int l, int dx, int dy) const {
+        return C::ld(ob + l * plane + dy * pitch + dx);
+    }
+};
+
 template <int N1, class C>
 __global__ void __launch_bounds__(256, fv_update_minb<N1, C>()) fv_update_kernel(const typename C::T* __restrict__ f,
                                                         const typename C::T* __restrict__ om,
@@ -145,63 +256,81 @@ __global__ void __launch_bounds__(256, fv_update_minb<N1, C>()) fv_update_kernel
     constexpr int Q = N1 * N1;
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= p.nx || y >= p.ny) return;
-    const long long pitch = p.pitch;
+    const long long c0 = sidx(p, 0, x, y);
+    const FvGlobalNbr<C> ld{f + c0, om + c0, p.plane, (long long)p.pitch};
     R s[Q];
-    const int wall = fp.walls ? (y == 0 ? 1 : (y == p.ny - 1 ? 2 : 0)) : 0;  // 1: bottom, 2: top
-    if (wall) {
-        // wall node (Eq. FVLB2): populations arriving at the wall (c . n <= 0) advance with the
-        // one-sided stencils into the fluid; the leaving ones keep their imposed values
-        const R sgn = wall == 1 ? R(1) : R(-1);  // n = +y at the bottom, -y at the top
-        const long long in = wall == 1 ? pitch : -pitch;  // the fluid-side row
-        const R dyw = fp.dy ? (R)(wall == 1 ? fp.dy[0] : fp.dy[p.ny - 2]) : R(1);
-#pragma unroll
-        for (int j = 0; j < N1; ++j)
-#pragma unroll
-            for (int i = 0; i < N1; ++i) {
-                const int l = i + N1 * j;
-                const long long c0 = sidx(p, l, x, y);
-                const typename C::T* fq = f + c0;
-                const typename C::T* oq = om + c0;
-                const R f0 = C::ld(fq);
-                const R cy = kx<R>(p, j);
-                if (sgn * cy > R(0)) {
-                    s[l] = f0;
-                    continue;
-                }
-                const R fE = C::ld(fq + 1), fW = C::ld(fq - 1), fI = C::ld(fq + in), fIE = C::ld(fq + in + 1),
-                        fIW = C::ld(fq + in - 1);
-                const R gx = R(0.375) * (fE - fW) + R(0.125) * (fIE - fIW);
-                const R gy = sgn * (R(2) / dyw) * (R(0.375) * (fI - f0) + R(0.0625) * (fIE + fIW - fE - fW));
-                const R obar = R(0.5625) * C::ld(oq) + R(0.09375) * (C::ld(oq + 1) + C::ld(oq - 1)) +
-                               R(0.1875) * C::ld(oq + in) + R(0.03125) * (C::ld(oq + in + 1) + C::ld(oq + in - 1));
-                s[l] = f0 + (R)fp.dt * (obar - kx<R>(p, i) * gx - cy * gy);
-            }
-        store_collided<N1, C>(fout, geom_of(p), x, y, s);
-        return;
-    }
-    // interior node: y spacing factor 2 / (dy_j + dy_j-1) of the stencil (1 on the unit grid)
-    const R ysc = fp.dy ? (R)(2.0 / (fp.dy[y] + fp.dy[y - 1])) : R(1);
-#pragma unroll
-    for (int j = 0; j < N1; ++j)
-#pragma unroll
-        for (int i = 0; i < N1; ++i) {
-            const int l = i + N1 * j;
-            const long long c0 = sidx(p, l, x, y);
-            const typename C::T* fq = f + c0;
-            const typename C::T* oq = om + c0;
-            // P1 east, P2 north, P3 west, P4 south, P5 NE, P6 NW, P7 SW, P8 SE (+y is the next row)
-            const R f1 = C::ld(fq + 1), f2 = C::ld(fq + pitch), f3 = C::ld(fq - 1), f4 = C::ld(fq - pitch);
-            const R f5 = C::ld(fq + pitch + 1), f6 = C::ld(fq + pitch - 1), f7 = C::ld(fq - pitch - 1),
-                    f8 = C::ld(fq - pitch + 1);
-            const R gx = R(0.375) * (f1 - f3) + R(0.0625) * (f5 - f6 - f7 + f8);
-            const R gy = ysc * (R(0.375) * (f2 - f4) + R(0.0625) * (f5 + f6 - f7 - f8));
-            const R obar = R(0.5625) * C::ld(oq) +
-                           R(0.09375) * (C::ld(oq + 1) + C::ld(oq + pitch) + C::ld(oq - 1) + C::ld(oq - pitch)) +
-                           R(0.015625) * (C::ld(oq + pitch + 1) + C::ld(oq + pitch - 1) + C::ld(oq - pitch - 1) +
-                                          C::ld(oq - pitch + 1));
-            s[l] = C::ld(fq) + (R)fp.dt * (obar - kx<R>(p, i) * gx - kx<R>(p, j) * gy);
-        }
+    fv_update_cell<N1, C>(ld, p, fp, y, s);
     store_collided<N1, C>(fout, geom_of(p), x, y, s);
+}
+
+// Fused form: one kernel per step.  A CTA of 32 x BY threads holds a 32 x BY block of cells in
+// shared memory, populations and collision terms; its inner 30 x (BY - 2) cells are the CTA's
+// output, the outer ring their halo.  Each thread loads its cell (the ring from the periodic
+// images or ghost rows of the frame), computes the cell's collision term, and after one block
+// barrier the inner cells are updated from their 3 x 3 neighbourhoods in shared memory: the
+// collision term never goes through global memory (read Q, write Q values per cell update
+// instead of 5 Q), at the cost of recomputing it on the ring (32 BY / (30 (BY - 2)) of the
+// cells).  Same arithmetic as the two-kernel form, so the same populations bit for bit.
+template <int N1, class C>
+constexpr int fv_fused_by() {  // rows of the block: 16 where both fields of 512 cells fit 160 KB
+    return 2 * N1 * N1 * 32 * 16 * (int)sizeof(typename C::T) <= 160 * 1024 ? 16 : 8;
+}
+template <int N1, class C>
+constexpr int fv_fused_minb() {  // 2 CTAs (64 registers) for FP32 up to D2Q16, else 1
+    return (sizeof(typename C::R) == 4 && N1 <= 4) ? 2 : 1;
+}
+template <int N1, class C>
+constexpr size_t fv_fused_smem() {
+    return 2 * (size_t)N1 * N1 * 32 * fv_fused_by<N1, C>() * sizeof(typename C::T);
+}
+
+template <class C, int CELLS>
+struct FvSharedNbr {
+    const typename C::T* fs;  // [Q][CELLS] populations of the block
+    const typename C::T* os;  // [Q][CELLS] collision terms of the block
+    int c;                    // the cell's index in the block (row-major, 32 per row)
+    __device__ __forceinline__ typename C::R f(int l, int dx, int dy) const {
+        return (typename C::R)fs[l * CELLS + c + dy * 32 + dx];
+    }
+    __device__ __forceinline__ typename C::R om(int l, int dx, int dy) const {
+        return (typename C::R)os[l * CELLS + c + dy * 32 + dx];
+    }
+};
+
+template <int N1, class C>
+__global__ void __launch_bounds__(32 * fv_fused_by<N1, C>(), fv_fused_minb<N1, C>())
+    fv_fused_kernel(const typename C::T* __restrict__ f, typename C::T* __restrict__ fout, const KParams p,
+                    const FvParams fp) {
+    using R = typename C::R;
+    using T = typename C::T;
+    static_assert(std::is_same<R, T>::value, "the fused form keeps the stored values in shared memory as read");
+    constexpr int Q = N1 * N1, BY = fv_fused_by<N1, C>(), CELLS = 32 * BY;
+    extern __shared__ __align__(16) unsigned char fv_smem[];
+    T* fs = reinterpret_cast<T*>(fv_smem);
+    T* os = fs + Q * CELLS;
+    const int tx = threadIdx.x, ty = threadIdx.y, c = ty * 32 + tx;
+    const int x = blockIdx.x * 30 + tx - 1, y = blockIdx.y * (BY - 2) + ty - 1;
+    // cells up to x = nx and y = ny lie in the frame (periodic images, or the ghost rows beyond a
+    // wall, which no wall node's stencil reads); the ring beyond them belongs to no output
+    if (x <= p.nx && y <= p.ny) {
+        R s[Q], w[Q];
+        const T* fb = f + sidx(p, 0, x, y);
+#pragma unroll
+        for (int l = 0; l < Q; ++l) {
+            s[l] = C::ld(fb + l * p.plane);
+            fs[l * CELLS + c] = s[l];
+        }
+        fv_omega_cell<N1, C>(s, p, fp, w);
+#pragma unroll
+        for (int l = 0; l < Q; ++l) os[l * CELLS + c] = w[l];
+    }
+    __syncthreads();
+    if (tx >= 1 && tx <= 30 && ty >= 1 && ty <= BY - 2 && x < p.nx && y < p.ny) {
+        const FvSharedNbr<C, CELLS> ld{fs, os, c};
+        R s[Q];
+        fv_update_cell<N1, C>(ld, p, fp, y, s);
+        store_collided<N1, C>(fout, geom_of(p), x, y, s);
+    }
 }
 
 // Equilibrium of unit density at velocity (u, 0) and temperature T, FP64.
@@ -314,20 +443,30 @@ __global__ void fv_impose_kernel(typename C::T* __restrict__ f, const KParams p,
 
 template <int N1, class C>
 cudaError_t launch_fv(const void* f, void* om, void* fout, const KParams& p, const FvParams& fp, const WallParams& wp,
-                      cudaStream_t s) {
+                      bool split, cudaStream_t s) {
     using T = typename C::T;
-    const dim3 b(32, 8), g((p.nx + 31) / 32, (p.ny + 7) / 8);
     if (fp.walls) fv_impose_kernel<N1, C><<<(2 * p.nx + 127) / 128, 128, 0, s>>>((T*)f, p, wp);
-    fv_omega_kernel<N1, C><<<g, b, 0, s>>>((const T*)f, (T*)om, p, fp);
-    fv_update_kernel<N1, C><<<g, b, 0, s>>>((const T*)f, (const T*)om, (T*)fout, p, fp);
+    if (split) {
+        const dim3 b(32, 8), g((p.nx + 31) / 32, (p.ny + 7) / 8);
+        fv_omega_kernel<N1, C><<<g, b, 0, s>>>((const T*)f, (T*)om, p, fp);
+        fv_update_kernel<N1, C><<<g, b, 0, s>>>((const T*)f, (const T*)om, (T*)fout, p, fp);
+    } else {
+        constexpr int BY = fv_fused_by<N1, C>();
+        constexpr size_t smem = fv_fused_smem<N1, C>();
+        cudaError_t e = cudaFuncSetAttribute(fv_fused_kernel<N1, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        const dim3 b(32, BY), g((p.nx + 29) / 30, (p.ny + BY - 3) / (BY - 2));
+        fv_fused_kernel<N1, C><<<g, b, smem, s>>>((const T*)f, (T*)fout, p, fp);
+    }
     return cudaGetLastError();
 }
 
 template <int N1>
 cudaError_t launch_fv_storage(int storage, const void* f, void* om, void* fout, const KParams& p, const FvParams& fp,
-                              const WallParams& wp, cudaStream_t s) {
-    return storage == TVLBM_FP64 ? launch_fv<N1, CodecF64>(f, om, fout, p, fp, wp, s)
-                                 : launch_fv<N1, CodecF32>(f, om, fout, p, fp, wp, s);
+                              const WallParams& wp, bool split, cudaStream_t s) {
+    return storage == TVLBM_FP64 ? launch_fv<N1, CodecF64>(f, om, fout, p, fp, wp, split, s)
+                                 : launch_fv<N1, CodecF32>(f, om, fout, p, fp, wp, split, s);
 }
 
 // Inverse of the 4 x 4 Gram matrix of (1, c_x, c_y, |c|^2) under the set's weights (Gauss-Jordan).
@@ -401,9 +540,9 @@ int fvlb_steps(tvlbm_ctx* c, int n) {
         void* fout = c->mem + c->L.off_f[1 - c->cur];
         cudaError_t e;
         switch (c->n1) {
-            case 3: e = launch_fv_storage<3>(c->storage, f, c->fv_omega, fout, c->kp, fp, wp, c->stream); break;
-            case 4: e = launch_fv_storage<4>(c->storage, f, c->fv_omega, fout, c->kp, fp, wp, c->stream); break;
-            default: e = launch_fv_storage<6>(c->storage, f, c->fv_omega, fout, c->kp, fp, wp, c->stream); break;
+            case 3: e = launch_fv_storage<3>(c->storage, f, c->fv_omega, fout, c->kp, fp, wp, c->fv_split != 0, c->stream); break;
+            case 4: e = launch_fv_storage<4>(c->storage, f, c->fv_omega, fout, c->kp, fp, wp, c->fv_split != 0, c->stream); break;
+            default: e = launch_fv_storage<6>(c->storage, f, c->fv_omega, fout, c->kp, fp, wp, c->fv_split != 0, c->stream); break;
         }
         if (e != cudaSuccess) {
             snprintf(c->err, sizeof(c->err), "finite-volume kernels: %s", cudaGetErrorString(e));
@@ -451,6 +590,12 @@ extern "C" int tvlbm_set_fv_pressure_scaling(tvlbm_ctx* c, int enable) {
         return TVLBM_EINVAL;
     }
     c->fv_pscale = enable ? 1 : 0;
+    return TVLBM_OK;
+}
+
+extern "C" int tvlbm_set_fv_fused(tvlbm_ctx* c, int fused) {
+    if (!c) return TVLBM_EINVAL;
+    c->fv_split = fused ? 0 : 1;
     return TVLBM_OK;
 }
 

@@ -49,6 +49,27 @@ def test_channel_matches_oracle(tv, exact, mesh):
     sim.close()
 
 
+@pytest.mark.parametrize("exact,mesh,nx", [(False, "uniform", 8), (True, "tanh", 8), (True, "tanh", 67)])
+def test_channel_fused_equals_two_kernels(tv, exact, mesh, nx):
+    """The fused finite-volume kernel on a channel (wall nodes inside its blocks, ghost rows in
+    their halo ring) gives the two-kernel form's populations bit for bit."""
+    ny = 29
+    y = np.linspace(0.0, 6.0, ny) if mesh == "uniform" else fvlb.tanh_nodes(ny, 6.0, 1.5)
+    walls = (0.02, 1.0, -0.03, 1.05)
+    out = []
+    for fused in (True, False):
+        sim = tv.Simulation(nx, ny, "D2Q16", tau=0.5, dt=0.01, walls=walls, storage="fp64")
+        sim.set_scheme("fvlb", 2.0)
+        sim.set_fv_walls(exact=exact, nr_iters=32, y_nodes=y)
+        sim.set_fv_fused(fused)
+        sim.init_moments(*fields(nx, ny))
+        sim.step(30)
+        out.append(sim.populations_f64())
+        sim.close()
+    assert np.all(np.isfinite(out[0]))
+    assert np.array_equal(out[0], out[1])
+
+
 def test_exact_walls_move_with_the_walls(tv):
     nx, ny = 4, 13
     y = fvlb.tanh_nodes(ny, 6.0, 1.5)
