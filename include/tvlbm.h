@@ -180,6 +180,24 @@ int tvlbm_set_fv_fused(tvlbm_ctx *ctx, int fused);
  * not the finite-volume scheme, nr_iters < 1 with exact, y_nodes not increasing), ENOMEM. */
 int tvlbm_set_fv_walls(tvlbm_ctx *ctx, int exact, int nr_iters, const double *y_nodes);
 
+/* Volumetric scheme on a mesh that is non-uniform in y (the grid refinement of Sec. "Grid
+ * Refinement for simple unidirectional flows", Eqs. NONUNI1-2, e.g. cells crowded towards the
+ * walls): cell y spans [faces[y], faces[y+1]] (faces: host array of ny + 1 increasing values,
+ * copied; x keeps unit cells).  Per velocity, destination row y gathers sum_r w_r f_r with
+ * w_r = |[faces[y] - c_y dt, faces[y+1] - c_y dt] within cell r| / h_y, the uniform scheme's area
+ * overlap on unequal cells; with walls (a TVLBM_BC_WALLS context, walls at faces[0] and faces[ny])
+ * the part beyond a wall is filled with A(x) f_eq(1, u_w, T_w) for the incoming velocities, A
+ * re-emitting what the outgoing ones carry beyond it (Eq. IMPOSITION), so mass is conserved.
+ * Periodic contexts repeat the mesh with period faces[ny] - faces[0].  The conserved quantities
+ * are the sums weighted by the cell heights, which tvlbm_conserved_sums then returns.  Runs the
+ * plain form only (sets it; other forms are refused while a mesh is set), FP64, FP32 or
+ * FP32-deviation storage with a single reference, the volumetric scheme.  A row may gather from
+ * at most 64 cells (cells far thinner than c dt are refused).  faces = NULL returns to unit
+ * cells.  Allocates the tables (a few bytes per row and velocity); synchronises.  Errors: EINVAL
+ * (faces not finite or not increasing, storage, scheme, a per-row reference, too thin cells),
+ * ENOMEM, ECUDA. */
+int tvlbm_set_y_faces(tvlbm_ctx *ctx, const double *faces);
+
 /* Enable (1, default) or disable (0) replay of multi-step runs through captured CUDA graphs. */
 int tvlbm_set_graphs(tvlbm_ctx *ctx, int enable);
 

@@ -78,6 +78,7 @@ def _load_library() -> ctypes.CDLL:
         "tvlbm_set_fv_walls": (_I, [_P, _I, _I, _DP]),
         "tvlbm_set_fv_pressure_scaling": (_I, [_P, _I]),
         "tvlbm_set_fv_fused": (_I, [_P, _I]),
+        "tvlbm_set_y_faces": (_I, [_P, _DP]),
         "tvlbm_set_reference": (_I, [_P, _D, _D, _D]),
         "tvlbm_set_reference_rows": (_I, [_P, _P, _P, _P]),
         "tvlbm_set_reference_refresh": (_I, [_P, _I]),
@@ -370,6 +371,17 @@ class Simulation:
         if yn is not None and yn.shape != (self.ny,):
             raise ValueError("y_nodes must hold ny positions")
         _check(_lib.tvlbm_set_fv_walls(self.ctx, 1 if exact else 0, int(nr_iters), _dp(yn)), self.ctx)
+
+    def set_y_faces(self, faces=None):
+        """Volumetric scheme on a mesh non-uniform in y: cell y spans [faces[y], faces[y+1]]
+        (ny + 1 increasing values; None: unit cells).  Plain form only."""
+        if faces is None:
+            _check(_lib.tvlbm_set_y_faces(self.ctx, None), self.ctx)
+            return
+        fa = np.ascontiguousarray(faces, dtype=np.float64)
+        if fa.shape != (self.ny + 1,):
+            raise ValueError("faces must hold ny + 1 values")
+        _check(_lib.tvlbm_set_y_faces(self.ctx, _dp(fa)), self.ctx)
 
     def set_fv_fused(self, fused=True):
         """Finite-volume scheme: one fused kernel per step (default) or the two-kernel form."""

@@ -63,6 +63,7 @@ void drop_graphs(tvlbm_ctx* c) {
 cudaError_t launch_step(tvlbm_ctx* c, int from, cudaStream_t s) {
     void* fin = dptr(c, c->L.off_f[from]);
     void* fout = dptr(c, c->L.off_f[1 - from]);
+    if (c->mesh_mem) return mesh_launch_step(c, fin, fout, s);  // non-uniform y mesh: its own sweep
     if (c->kp.walls) {
         const cudaError_t e = c->kt->wall(c->storage, fin, c->kp, s);
         if (e != cudaSuccess) return e;
@@ -417,6 +418,7 @@ int tvlbm_destroy(tvlbm_ctx* c) {
     if (c->fv_omega) cudaFree(c->fv_omega);
     if (c->fv_dy) cudaFree(c->fv_dy);
     if (c->fv_wall_eq) cudaFree(c->fv_wall_eq);
+    if (c->mesh_mem) cudaFree(c->mesh_mem);
     if (c->ref_mem) cudaFree(c->ref_mem);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     if (c->own_mem && c->mem) cudaFree(c->mem);
@@ -436,6 +438,8 @@ int tvlbm_set_form(tvlbm_ctx* c, int form) {
         return fail(c, TVLBM_EINVAL, "unknown form %d", form);
     if (form != FORM_PLAIN && !c->have_tmap)
         return fail(c, TVLBM_EINVAL, "tiled forms not available (no TMA descriptor for this storage/driver)");
+    if (form != FORM_PLAIN && c->mesh_mem)
+        return fail(c, TVLBM_EINVAL, "a non-uniform mesh runs the plain form only");
     int tiles_x = 0, tiles_y = 0;
     if (form == FORM_FLOW && !flow_tiles(c, c->tile_cfg, &tiles_x, &tiles_y))
         return fail(c, TVLBM_EINVAL,
@@ -472,6 +476,7 @@ int tvlbm_set_reference(tvlbm_ctx* c, double ux, double uy, double T) {
 }
 
 static int rows_applicable(tvlbm_ctx* c) {
+    if (c->mesh_mem) return fail(c, TVLBM_EINVAL, "a non-uniform mesh takes no per-row reference");
     if (c->storage == TVLBM_FP64 || c->storage == TVLBM_FP32)
         return fail(c, TVLBM_EINVAL, "the reference applies to deviation storage only");
     if (!c->kp.walls) return fail(c, TVLBM_EINVAL, "a per-row reference needs a domain with walls");
@@ -632,7 +637,9 @@ int tvlbm_conserved_sums(tvlbm_ctx* c, double out[5]) {
     cudaSetDevice(c->device);
     double* part = (double*)dptr(c, c->L.off_part);
     double* sums = (double*)dptr(c, c->L.off_sums);
-    TVLBM_CUDA(c, c->kt->reduce(c->storage, fcur(c), part, sums, c->kp, c->stream), "reduction kernels");
+    TVLBM_CUDA(c, c->mesh_mem ? mesh_reduce(c, fcur(c), part, sums, c->stream)
+                              : c->kt->reduce(c->storage, fcur(c), part, sums, c->kp, c->stream),
+               "reduction kernels");
     TVLBM_CUDA(c, cudaMemcpyAsync(out, sums, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "cudaMemcpyAsync sums");
     TVLBM_CUDA(c, cudaStreamSynchronize(c->stream), "sums synchronize");
     const int rc = check_status(c);

@@ -9,6 +9,22 @@
 #include "tvlbm_host.h"
 #include "tvlbm_kernels.cuh"
 
+namespace tvlbm {
+// Gather tables of a mesh non-uniform in y (tvlbm_set_y_faces, tvlbm_mesh.cu): cell y spans
+// [F_y, F_{y+1}], height h_y; x stays uniform.
+struct MeshDev {
+    int k;             // entries per (y-node, row) of the gather table
+    int kb;            // entries per y-node of the wall tables
+    const int* src;    // [n1][ny][k] source row of each entry (-1 / ny: beyond the bottom / top wall)
+    const double* wd;  // [n1][ny][k] its weight |shifted row interval within the source| / h_y (0 pads)
+    const float* wf;
+    const int* bsrc;   // [n1][kb] fluid rows whose image crosses the wall that node j moves towards
+    const double* bd;  // [n1][kb] the length beyond that wall (0 pads)
+    const float* bf;
+    const double* h;   // [ny] cell heights
+};
+}  // namespace tvlbm
+
 struct tvlbm_ctx {
     int nx, ny, velset, n1, Q, N, storage, form, graphs;
     double tau, dt, rho0;
@@ -37,6 +53,8 @@ struct tvlbm_ctx {
     int fv_exact, fv_nr_iters;        // finite-volume channel: Newton-Raphson imposition, iterations
     int fv_pscale;                    // finite-volume scheme: tau, tau_g divided by the local pressure
     int fv_split;                     // finite-volume scheme: two kernels per step (0: one fused kernel)
+    unsigned char* mesh_mem;          // non-uniform y mesh: one device allocation holding the tables
+    tvlbm::MeshDev mesh;              //   (null: unit cells)
     unsigned char* ref_mem;           // per-row deviation reference: one device allocation holding
     double* ref_rowd;                 //   the live tables (KParams::rowd / rowf),
     float* ref_rowf;
@@ -56,3 +74,8 @@ struct tvlbm_ctx {
 
 // Finite-volume scheme (tvlbm_fvlb.cu): n explicit steps of the context's state.
 int fvlb_steps(tvlbm_ctx* c, int n);
+
+// Non-uniform y mesh (tvlbm_mesh.cu): one time step from fin into fout (the wall fill, then the
+// sweep), and the FP64 conserved sums weighted by the cell heights.
+cudaError_t mesh_launch_step(tvlbm_ctx* c, const void* fin, void* fout, cudaStream_t s);
+cudaError_t mesh_reduce(tvlbm_ctx* c, const void* f, double* partials, double* out5, cudaStream_t s);

@@ -564,6 +564,10 @@ extern "C" int tvlbm_set_scheme(tvlbm_ctx* c, int scheme, double tau_g) {
         snprintf(c->err, sizeof(c->err), "unknown scheme %d", scheme);
         return TVLBM_EINVAL;
     }
+    if (c->mesh_mem) {
+        snprintf(c->err, sizeof(c->err), "the finite-volume scheme takes its mesh from tvlbm_set_fv_walls");
+        return TVLBM_EINVAL;
+    }
     if ((c->storage != TVLBM_FP64 && c->storage != TVLBM_FP32) || isnan(tau_g) || tau_g == 0.0 || !isfinite(c->tau)) {
         snprintf(c->err, sizeof(c->err), "the finite-volume scheme needs FP64 or FP32 storage, finite tau and tau_g != 0");
         return TVLBM_EINVAL;

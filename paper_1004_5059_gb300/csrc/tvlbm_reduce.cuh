@@ -7,7 +7,8 @@
 //     M = sum f_l,  P = sum c_l f_l,  E = sum |c_l|^2 f_l / 2,
 // taken per row j of the tensor-product set from the node coordinates xd[] (c_l = (x_i, x_j)).
 // The cell source is a template parameter, so the context's ghost-framed storage and a packed
-// caller-owned array share one summation body (and hence one cell order).
+// caller-owned array share one summation body (and hence one cell order); a source may weight
+// each cell (its size on a non-uniform mesh: the conserved quantities are the size-weighted sums).
 #pragma once
 
 #include "tvlbm_kernels.cuh"
@@ -34,6 +35,7 @@ struct FramedCells {
     }
     __device__ double value(const KParams& p, const Cell& k, int l) const { return (double)C::ld(f + sidx(p, l, k.x, k.y)); }
     __device__ double base(const KParams& p, const Cell& k, int l) const { return p.rho0d + kPrefRow<double>(p, l, k.y); }
+    __device__ double weight(const KParams&, const Cell&) const { return 1.0; }
 };
 
 // A packed caller-owned array: population l of cell c = y * nx + x at f[l * ncell + c], deviations
@@ -50,6 +52,7 @@ struct PackedCells {
     __device__ Cell at(const KParams&, long long c) const { return {(int)c}; }
     __device__ double value(const KParams&, const Cell& k, int l) const { return (double)C::ld(f + l * ncell + k.c); }
     __device__ double base(const KParams&, const Cell&, int) const { return rho0; }
+    __device__ double weight(const KParams&, const Cell&) const { return 1.0; }
 };
 
 // Pass 1 body: p supplies the node coordinates xd[] and marginal weights wd[] (w_l = wd_i wd_j).
@@ -60,6 +63,7 @@ __device__ __forceinline__ void reduce_cells(const Cells& cells, double* __restr
     for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;
          c += (long long)gridDim.x * blockDim.x) {
         const typename Cells::Cell k = cells.at(p, c);
+        const double hw = cells.weight(p, k);  // the cell's size where cells differ (else 1)
 #pragma unroll
         for (int j = 0; j < N1; ++j) {
             double r = 0, rx = 0, rxx = 0;
@@ -68,7 +72,7 @@ __device__ __forceinline__ void reduce_cells(const Cells& cells, double* __restr
                 const int l = i + N1 * j;
                 const double v = cells.value(p, k, l);
                 acc[4] += isfinite(v) ? 0.0 : 1.0;
-                const double fv = to_f<C, double>(v, p.wd[i] * p.wd[j], cells.base(p, k, l));
+                const double fv = to_f<C, double>(v, p.wd[i] * p.wd[j], cells.base(p, k, l)) * hw;
                 r += fv;
                 rx += p.xd[i] * fv;
                 rxx += p.xd[i] * p.xd[i] * fv;
