@@ -971,6 +971,147 @@ def run_fv_reference(args, rank):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+MESH = dict(desc="volumetric scheme on a mesh non-uniform in y: D2Q16 1024x1024 thermal Couette channel (walls "
+                 "u = 0, T = 1 and u = 0.1, T = 1.1), tanh faces (beta = 2.3, cells 0.09 to 2.3) over a height of "
+                 "1024, FP32 deviation storage, tau = 0.9, dt = 1, 100 steps per bench step",
+            nx=1024, ny=1024, beta=2.3, tau=0.9, dt=1.0, tsteps=100, walls=(0.0, 1.0, 0.1, 1.1),
+            sample_nx=64, sample_ny=64, sample_steps=60)
+
+
+def run_mesh(args, rank, world, local_rank):
+    """Throughput of the volumetric step on the tanh mesh (plain form: per-row gather tables and
+    the wall fill), with unit cells timed beside it on the same grid, and the errors against the
+    oracle on a 64x64 channel of the same mesh law."""
+    import torch
+    import paper_1004_5059_gb300 as tv
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    nx, ny, tsteps, walls = MESH["nx"], MESH["ny"], MESH["tsteps"], MESH["walls"]
+    stream = torch.cuda.current_stream(dev)
+    sim = tv.Simulation(nx, ny, "D2Q16", tau=MESH["tau"], dt=MESH["dt"], storage="fp32_dev", walls=walls,
+                        stream=stream)
+    sim.set_y_faces(workloads.tanh_faces(ny, float(ny), MESH["beta"]))
+    fields = workloads.couette_linear(nx, ny, walls[1], walls[3])
+    sim.init_moments(*fields)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def timed(steps, warmup):
+        for _ in range(warmup):
+            sim.step(tsteps)
+        torch.cuda.synchronize()
+        evs = []
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sim.step(tsteps)
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs)
+
+    timed(0, args.warmup)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    clocks = Clocks(local_rank)
+    clocks.start()
+    ms = timed(args.steps, 0)
+    clk = clocks.stop()
+    ms_max = max_over_ranks(ms, world, dev)
+    cells = nx * ny
+    value = aggregate_mlups(world, cells, tsteps, args.steps, ms_max / 1e3)
+    bpc = 2 * 16 * 4  # read and write Q FP32 values per cell update (the wall fill and the extra
+    peak, peak_kind = measured_peak_hbm()  # gather rows of the thin cells come from L2)
+    achieved = bpc * cells / (ms / 1e3 / (args.steps * tsteps)) / 1e9
+    # unit cells on the same grid, same form (the uniform scheme's plain sweep and wall kernel)
+    sim.set_y_faces(None)
+    sim.set_form("plain")
+    sim.init_moments(*fields)
+    ms_u = timed(max(1, min(args.steps, 3)), 1)
+    unit = {"value": cells * tsteps * max(1, min(args.steps, 3)) / (ms_u / 1e3) / 1e6, "unit": UNIT,
+            "form": "plain", "note": "unit cells, the uniform scheme's plain sweep and wall kernel"}
+    sim.set_y_faces(workloads.tanh_faces(ny, float(ny), MESH["beta"]))
+    pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in fields]
+    out = [torch.empty((ny, nx), dtype=torch.float64).pin_memory().numpy() for _ in range(4)]
+    torch.cuda.synchronize()
+    te = time.perf_counter()
+    for _ in range(2):
+        sim.init_moments(*pinned)
+        sim.step(tsteps)
+        tv.tvlbm_moments(sim.ctx, nx, ny, out=out)
+    e2e = aggregate_mlups(world, cells, tsteps, 2, max_over_ranks(time.perf_counter() - te, world, dev))
+    sim.close()
+    line = {"metric": METRIC + " (volumetric scheme, non-uniform y mesh)", "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (channel fields)",
+            "config": {"workload": MESH["desc"], "nx": nx, "ny": ny, "time_steps_per_bench_step": tsteps,
+                       "form": "plain", "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "L2 flushed (512 MiB write) between timed steps"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_kind": peak_kind, "bytes_per_cell": bpc, "traffic": None},
+            "unit_cells": unit,
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 32 * cells, "d2h_bytes_per_step": 32 * cells},
+            "gpu_launches": args.steps * tsteps * 2, "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle.mesh import MeshOracle
+        snx, sny, sst = MESH["sample_nx"], MESH["sample_ny"], MESH["sample_steps"]
+        sf = workloads.tanh_faces(sny, float(sny), MESH["beta"])
+        sw = workloads.couette_linear(snx, sny, walls[1], walls[3])
+        o = MeshOracle(snx, sf, "D2Q16", tau=MESH["tau"], dt=MESH["dt"], walls=walls)
+        o.init_moments(*sw)
+        t0 = time.perf_counter()
+        o.step(sst)
+        dt_ = time.perf_counter() - t0
+        g = tv.Simulation(snx, sny, "D2Q16", tau=MESH["tau"], dt=MESH["dt"], storage="fp32_dev", walls=walls)
+        g.set_y_faces(sf)
+        g.init_moments(*sw)
+        g.step(sst)
+        got, want = g.moments(), o.moments()
+        g.close()
+        du = np.max(np.abs(got[1] - want[1]) + np.abs(got[2] - want[2])) / np.max(np.hypot(want[1], want[2]))
+        line["accuracy_vs_oracle"] = {
+            "sample": "%dx%d channel, same mesh law and walls, %d steps" % (snx, sny, sst),
+            "max_rel_err_rho": float(np.max(np.abs(got[0] - want[0])) / np.max(np.abs(want[0]))),
+            "max_rel_err_u": float(du),
+            "max_rel_err_T": float(np.max(np.abs(got[3] - want[3])) / np.max(np.abs(want[3])))}
+        line["cpu_baseline"] = {"value": snx * sny * sst / dt_ / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": "%d steps of the %dx%d channel (numpy gather, C collision, one core)"
+                                          % (sst, snx, sny)}
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return line if rank == 0 else None
+
+
+def run_mesh_reference(args, rank):
+    if rank != 0:
+        return None
+    from oracle.mesh import MeshOracle
+    snx, sny = MESH["sample_nx"], MESH["sample_ny"]
+    walls = MESH["walls"]
+    o = MeshOracle(snx, workloads.tanh_faces(sny, float(sny), MESH["beta"]), "D2Q16", tau=MESH["tau"], dt=MESH["dt"], walls=walls)
+    o.init_moments(*workloads.couette_linear(snx, sny, walls[1], walls[3]))
+    for _ in range(args.warmup):
+        o.step(1)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt_ = time.perf_counter() - t0
+    value = snx * sny * args.steps / dt_ / 1e6
+    return {"impl": "reference", "metric": METRIC + " (volumetric scheme, non-uniform y mesh)", "value": value,
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt_ * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": MESH["desc"], "sample": "one step of a %dx%d channel per bench step (oracle)"
+                       % (snx, sny)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "one step of a %dx%d channel per bench step" % (snx, sny)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
 def _closure_setup():
     from paper_1004_5059_gb300 import closure as C
     cfg = C.ClosureConfig(nf=CLOSURE["nf"], m=CLOSURE["m"])
@@ -1170,7 +1311,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c1", choices=sorted(WORKLOADS) + ["c3", "c4", "fv"])
+    ap.add_argument("--workload", default="c1", choices=sorted(WORKLOADS) + ["c3", "c4", "fv", "mesh"])
     ap.add_argument("--form", default=None, choices=["tiled", "flow", "plain", "strip"],
                     help="sweep form (default: the fastest of tiled, strip and, on periodic domains, flow)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -1184,6 +1325,11 @@ def main():
     rank, world, local_rank = dist_env()
     if args.workload == "fv":
         line = run_fv(args, rank, world, local_rank) if args.impl == "ours" else run_fv_reference(args, rank)
+        if rank == 0 and line is not None:
+            print(json.dumps(line))
+        return
+    if args.workload == "mesh":
+        line = run_mesh(args, rank, world, local_rank) if args.impl == "ours" else run_mesh_reference(args, rank)
         if rank == 0 and line is not None:
             print(json.dumps(line))
         return

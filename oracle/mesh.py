@@ -84,15 +84,6 @@ def beyond_walls(faces, s):
     return out
 
 
-def tanh_faces(ny, height, beta):
-    """Cell faces of a channel of the given height crowded towards both walls (the tanh law of
-    Eq. NONUNI2 applied to the faces): F_k = H/2 (1 + tanh(beta (2k/ny - 1)) / tanh(beta))."""
-    k = np.arange(ny + 1, dtype=np.float64)
-    F = 0.5 * height * (1.0 + np.tanh(beta * (2.0 * k / ny - 1.0)) / math.tanh(beta))
-    F[0], F[-1] = 0.0, float(height)  # the walls exactly (the formula's end values up to rounding)
-    return F
-
-
 class MeshOracle:
     """Volumetric TVLBM on nx uniform columns and the y cells of `faces` (ny + 1 increasing
     values): periodic in y, or walls=(u_lo, T_lo, u_hi, T_hi) at F_0 and F_ny."""

@@ -7,7 +7,8 @@ import numpy as np
 import pytest
 
 import workloads
-from oracle.mesh import MeshOracle, tanh_faces
+from oracle.mesh import MeshOracle
+from workloads import random_faces, tanh_faces
 
 pytestmark = pytest.mark.gpu
 
@@ -21,11 +22,6 @@ def tv():
         pytest.skip("no GPU")
     import paper_1004_5059_gb300 as tv
     return tv
-
-
-def random_faces(ny, seed, lo=0.4, hi=1.6):
-    rng = np.random.default_rng(seed)
-    return np.concatenate([[0.0], np.cumsum(rng.uniform(lo, hi, ny))])
 
 
 def pair(tv, nx, faces, velset, storage, walls, tau=0.7, dt=0.5, seed=3):

@@ -9,7 +9,8 @@ import pytest
 
 import workloads
 from oracle import Oracle
-from oracle.mesh import MeshOracle, beyond_walls, tanh_faces, y_overlaps
+from oracle.mesh import MeshOracle, beyond_walls, y_overlaps
+from workloads import random_faces as _random_faces, tanh_faces
 
 WALLS = (0.02, 1.0, -0.03, 1.05)
 
@@ -19,8 +20,7 @@ def unit_faces(ny):
 
 
 def random_faces(ny, seed, lo=0.3, hi=1.7):
-    rng = np.random.default_rng(seed)
-    return np.concatenate([[0.0], np.cumsum(rng.uniform(lo, hi, ny))])
+    return _random_faces(ny, seed, lo, hi)
 
 
 @pytest.mark.parametrize("velset", ["D2Q9", "D2Q16", "D2Q36"])

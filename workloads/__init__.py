@@ -120,3 +120,21 @@ def batched_domains(count: int = 256, seed: int = 3, sizes=(128, 256, 512, 768, 
     mach = rng.uniform(0.05, 0.3, size=count)
     seeds = seed * 100003 + np.arange(count)
     return [dict(n=int(side[i]), tau=float(tau[i]), mach=float(mach[i]), seed=int(seeds[i])) for i in range(count)]
+
+
+def tanh_faces(ny: int, height: float, beta: float):
+    """Cell faces of a channel crowded towards both walls (the tanh law of Eq. NONUNI2 applied to
+    the faces, as in Sec. "Grid Refinement for simple unidirectional flows"):
+    F_k = H/2 (1 + tanh(beta (2k/ny - 1)) / tanh(beta)), k = 0..ny, the walls F_0 = 0 and
+    F_ny = H exactly.  Mesh geometry (input data), not the method's arithmetic."""
+    k = np.arange(ny + 1, dtype=np.float64)
+    F = 0.5 * height * (1.0 + np.tanh(beta * (2.0 * k / ny - 1.0)) / np.tanh(beta))
+    F[0], F[-1] = 0.0, float(height)
+    return F
+
+
+def random_faces(ny: int, seed: int, lo: float = 0.4, hi: float = 1.6):
+    """Seeded cell faces with heights drawn uniformly from [lo, hi] (F_0 = 0)."""
+    rng = np.random.default_rng(seed)
+    return np.concatenate([[0.0], np.cumsum(rng.uniform(lo, hi, ny))])
+
