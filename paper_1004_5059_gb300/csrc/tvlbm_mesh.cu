@@ -39,8 +39,10 @@ __device__ __forceinline__ const R* wall_lengths(const MeshDev& m) {
 }
 
 // One time step of the fluid cells: gather along the mesh tables, collide, store (with the
-// periodic images of the frame).
-template <int N1, class C>
+// periodic images of the frame).  KT > 0: every row's list padded to KT entries (padding: weight
+// 0 on the row's first source), unrolled so that all loads of a velocity are in flight together;
+// KT = 0: a loop that ends at the first zero weight.  Both add the same terms in the same order.
+template <int N1, class C, int KT>
 __global__ void __launch_bounds__(256) mesh_sweep_kernel(const typename C::T* __restrict__ fin,
                                                          typename C::T* __restrict__ fout, const KParams p,
                                                          const MeshDev m) {
@@ -56,26 +58,52 @@ __global__ void __launch_bounds__(256) mesh_sweep_kernel(const typename C::T* __
         const long long e0 = ((long long)j * p.ny + y) * m.k;
         const int* src = m.src + e0;
         const R* wt = gather_weights<R>(m) + e0;
+        if constexpr (KT > 0) {
+            long long ro[KT];  // row offsets of the entries (same for every x-node of this y-node)
+            R ws[KT];
 #pragma unroll
-        for (int i = 0; i < N1; ++i) {
-            const int l = i + N1 * j;
-            const R ax = ka<R>(p, i);
-            const T* col = fin + (long long)l * p.plane + (x + p.hx - p.sh[i]);
-            // the first entry, then the others as lerps towards theirs (weights summing to one:
-            // a state uniform in space stays exactly uniform)
-            const T* b = col + (long long)(__ldg(src) + HY) * p.pitch;
-            const R v0 = C::ld(b);
-            const R r0 = fma(ax, C::ld(b - 1) - v0, split_rest<C>(p, l, v0));
-            R acc = r0;
-            for (int k = 1; k < m.k; ++k) {
-                const R wk = __ldg(wt + k);
-                if (wk == R(0)) break;  // the row's list has ended
-                const T* bk = col + (long long)(__ldg(src + k) + HY) * p.pitch;
-                const R vk = C::ld(bk);
-                const R rk = fma(ax, C::ld(bk - 1) - vk, split_rest<C>(p, l, vk));
-                acc = fma(wk, rk - r0, acc);
+            for (int k = 0; k < KT; ++k) {
+                ro[k] = (long long)(__ldg(src + k) + HY) * p.pitch;
+                ws[k] = __ldg(wt + k);
             }
-            s[l] = acc;
+#pragma unroll
+            for (int i = 0; i < N1; ++i) {
+                const int l = i + N1 * j;
+                const R ax = ka<R>(p, i);
+                const T* col = fin + (long long)l * p.plane + (x + p.hx - p.sh[i]);
+                R r[KT];
+#pragma unroll
+                for (int k = 0; k < KT; ++k) {
+                    const R v = C::ld(col + ro[k]);
+                    r[k] = fma(ax, C::ld(col + ro[k] - 1) - v, split_rest<C>(p, l, v));
+                }
+                // the first entry, then the others as lerps towards theirs (weights summing to
+                // one: a state uniform in space stays exactly uniform)
+                R acc = r[0];
+#pragma unroll
+                for (int k = 1; k < KT; ++k) acc = fma(ws[k], r[k] - r[0], acc);
+                s[l] = acc;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < N1; ++i) {
+                const int l = i + N1 * j;
+                const R ax = ka<R>(p, i);
+                const T* col = fin + (long long)l * p.plane + (x + p.hx - p.sh[i]);
+                const T* b = col + (long long)(__ldg(src) + HY) * p.pitch;
+                const R v0 = C::ld(b);
+                const R r0 = fma(ax, C::ld(b - 1) - v0, split_rest<C>(p, l, v0));
+                R acc = r0;
+                for (int k = 1; k < m.k; ++k) {
+                    const R wk = __ldg(wt + k);
+                    if (wk == R(0)) break;  // the row's list has ended
+                    const T* bk = col + (long long)(__ldg(src + k) + HY) * p.pitch;
+                    const R vk = C::ld(bk);
+                    const R rk = fma(ax, C::ld(bk - 1) - vk, split_rest<C>(p, l, vk));
+                    acc = fma(wk, rk - r0, acc);
+                }
+                s[l] = acc;
+            }
         }
     }
     const Geom g = geom_of(p);
@@ -159,7 +187,11 @@ cudaError_t step_as(const void* fin, void* fout, const KParams& p, const MeshDev
         mesh_wall_kernel<N1, C><<<grid, block, 0, s>>>((T*)fin, p, m);
     }
     const dim3 block(32, 8), grid((p.nx + 31) / 32, (p.ny + 7) / 8);
-    mesh_sweep_kernel<N1, C><<<grid, block, 0, s>>>((const T*)fin, (T*)fout, p, m);
+    // the table's row length m.k is the longest list; shorter lists are padded to it
+    if (m.k <= 2) mesh_sweep_kernel<N1, C, 2><<<grid, block, 0, s>>>((const T*)fin, (T*)fout, p, m);
+    else if (m.k == 3) mesh_sweep_kernel<N1, C, 3><<<grid, block, 0, s>>>((const T*)fin, (T*)fout, p, m);
+    else if (m.k == 4) mesh_sweep_kernel<N1, C, 4><<<grid, block, 0, s>>>((const T*)fin, (T*)fout, p, m);
+    else mesh_sweep_kernel<N1, C, 0><<<grid, block, 0, s>>>((const T*)fin, (T*)fout, p, m);
     return cudaGetLastError();
 }
 
@@ -288,7 +320,7 @@ extern "C" int tvlbm_set_y_faces(tvlbm_ctx* c, const double* faces) {
     // gather tables
     std::vector<Entries> rows((size_t)n1 * ny);
     Entries e;
-    int K = 1;
+    int K = 2;  // rows padded to at least two entries (the unrolled gather reads two)
     for (int j = 0; j < n1; ++j) {
         const double sft = c->rule.x[j] * c->dt;
         for (int y = 0; y < ny; ++y) {

@@ -48,6 +48,28 @@ def test_fp64_matches_oracle(tv, velset, walls):
     sim.close()
 
 
+def _pattern(heights, ny):
+    return np.concatenate([[0.0], np.cumsum(np.resize(np.asarray(heights, dtype=np.float64), ny))])
+
+
+# longest row lists of 2, 3, 4 entries (the unrolled gathers) and 5 and 8 (the general loop), by
+# the mesh oracle's tables: near-unit cells, random cells, and a tall cell among shorter ones,
+# periodic and with walls
+@pytest.mark.parametrize("faces,walls", [
+    (random_faces(21, 4, 0.9, 1.1), None),
+    (random_faces(21, 4), WALLS),
+    (_pattern([2.0, 0.5, 0.5, 0.5], 21), None),
+    (_pattern([2.5, 0.3, 0.3, 0.3, 0.3], 21), WALLS),
+    (_pattern([3.0, 0.25, 0.25, 0.25, 0.25, 0.25, 0.25], 21), None)])
+def test_every_row_length_matches_oracle(tv, faces, walls):
+    sim, ref = pair(tv, 29, faces, "D2Q16", "fp64", walls, dt=1.0 if walls is None else 0.5)
+    sim.step(10)
+    ref.step(10)
+    got = sim.populations_f64()
+    assert np.max(np.abs(got - ref.f)) <= 1e-12 * np.max(np.abs(ref.f))
+    sim.close()
+
+
 def test_fp32_deviation_matches_oracle_over_200_steps(tv):
     faces = tanh_faces(24, 24.0, 1.8)
     sim, ref = pair(tv, 40, faces, "D2Q16", "fp32_dev", WALLS, seed=5)
