@@ -42,8 +42,13 @@ __device__ __forceinline__ const R* wall_lengths(const MeshDev& m) {
 // periodic images of the frame).  KT > 0: every row's list padded to KT entries (padding: weight
 // 0 on the row's first source), unrolled so that all loads of a velocity are in flight together;
 // KT = 0: a loop that ends at the first zero weight.  Both add the same terms in the same order.
+template <int N1, class C>
+constexpr int mesh_sweep_minb() {  // resident CTAs of 256 threads: 3 (85 registers) for FP32 up to D2Q16
+    return (sizeof(typename C::R) == 4 && N1 <= 4) ? 3 : 1;
+}
+
 template <int N1, class C, int KT>
-__global__ void __launch_bounds__(256) mesh_sweep_kernel(const typename C::T* __restrict__ fin,
+__global__ void __launch_bounds__(256, mesh_sweep_minb<N1, C>()) mesh_sweep_kernel(const typename C::T* __restrict__ fin,
                                                          typename C::T* __restrict__ fout, const KParams p,
                                                          const MeshDev m) {
     using R = typename C::R;
@@ -140,9 +145,11 @@ __global__ void __launch_bounds__(32 * wall_lanes<N1>()) mesh_wall_kernel(typena
         if (col) {
             const int* src = m.bsrc + j * m.kb;
             const R* len = wall_lengths<R>(m) + j * m.kb;
+            // padded entries (length 0 on row 0) add exact zeros: no data-dependent exit, so the
+            // unrolled iterations' loads are in flight together
+#pragma unroll 4
             for (int e = 0; e < m.kb; ++e) {
                 const R le = __ldg(len + e);
-                if (le == R(0)) break;
                 const T* b = f + sidx(p, l, x - p.sh[i], __ldg(src + e));
                 acc += le * ((R(1) - ax) * to_f<C, R>(C::ld(b), w, ref) + ax * to_f<C, R>(C::ld(b - 1), w, ref));
             }
@@ -365,7 +372,7 @@ extern "C" int tvlbm_set_y_faces(tvlbm_ctx* c, const double* faces) {
             const Entries& r = rows[(size_t)j * ny + y];
             const size_t b = ((size_t)j * ny + y) * K;
             for (int k = 0; k < K; ++k) {
-                // padding repeats the row's first source (never read: its weight 0 ends the list)
+                // padding repeats the row's first source with weight 0 (adds an exact zero)
                 src[b + k] = k < (int)r.size() ? r[k].first : r[0].first;
                 wd[b + k] = k < (int)r.size() ? r[k].second / h[y] : 0.0;
                 wf[b + k] = (float)wd[b + k];
@@ -374,7 +381,7 @@ extern "C" int tvlbm_set_y_faces(tvlbm_ctx* c, const double* faces) {
     for (int j = 0; j < n1; ++j)
         for (int k = 0; k < KB; ++k) {
             const bool on = k < (int)walls[j].size();
-            bsrc[(size_t)j * KB + k] = on ? walls[j][k].first : 0;
+            bsrc[(size_t)j * KB + k] = on ? walls[j][k].first : 0;  // padding: row 0, length 0
             bd[(size_t)j * KB + k] = on ? walls[j][k].second : 0.0;
             bf[(size_t)j * KB + k] = (float)bd[(size_t)j * KB + k];
         }
