@@ -82,8 +82,9 @@ int tvlbm_mlp_adam(tvlbm_mlp *m, float lr, float beta1, float beta2, float eps);
 
 const char *tvlbm_mlp_last_error(const tvlbm_mlp *m);
 
-/* The network's activation as its kernels evaluate it, on n device values: g[i] = GELU(z[i]) and
- * dg[i] = GELU'(z[i]) = Phi(z) + z phi(z) (either output may be NULL).  z, g, dg: device FP32
+/* The network's activation as its kernels evaluate it, on n device values: g[i] = GELU(z[i]) (as
+ * the forward epilogues compute it, pairs of entries in packed FP32) and dg[i] = GELU'(z[i]) =
+ * Phi(z) + z phi(z) (either output may be NULL).  z, g, dg: device FP32
  * arrays of n entries, caller-owned.  Asynchronous on `stream` (a cudaStream_t; NULL = legacy
  * default).  Errors: EINVAL (n < 0, z NULL), ECUDA. */
 int tvlbm_mlp_activation(const float *z, float *g, float *dg, int n, void *stream);

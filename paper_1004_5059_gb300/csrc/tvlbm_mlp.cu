@@ -60,15 +60,48 @@ __device__ __forceinline__ float gelu_f(float z) {
     float e2;
     return 0.5f * z * (1.0f + erf_as(z * 0.70710678118654752f, e2));
 }
+// Two GELUs in packed FP32 pairs, per lane the operations of gelu_f in its order (a packed
+// multiply, add or fused multiply-add rounds each lane as the scalar instruction; the
+// reciprocal, the exponential, |x| and the sign stay scalar).  The forward epilogues and
+// tvlbm_mlp_activation's g use it.
+__device__ __forceinline__ float2 gelu2_f(float2 z) {
+    const float2 x = __fmul2_rn(z, make_float2(0.70710678118654752f, 0.70710678118654752f));
+    const float2 ax = make_float2(fabsf(x.x), fabsf(x.y));
+    const float2 d = __ffma2_rn(make_float2(0.3275911f, 0.3275911f), ax, make_float2(1.0f, 1.0f));
+    const float2 t = make_float2(__fdividef(1.0f, d.x), __fdividef(1.0f, d.y));
+    float2 q = __ffma2_rn(t, make_float2(1.061405429f, 1.061405429f), make_float2(-1.453152027f, -1.453152027f));
+    q = __ffma2_rn(t, q, make_float2(1.421413741f, 1.421413741f));
+    q = __ffma2_rn(t, q, make_float2(-0.284496736f, -0.284496736f));
+    q = __ffma2_rn(t, q, make_float2(0.254829592f, 0.254829592f));
+    const float2 poly = __fmul2_rn(t, q);
+    const float2 sq = __fmul2_rn(make_float2(-ax.x, -ax.y), ax);
+    const float2 e2 = make_float2(__expf(sq.x), __expf(sq.y));
+    const float2 r = __ffma2_rn(make_float2(-poly.x, -poly.y), e2, make_float2(1.0f, 1.0f));
+    const float2 er = make_float2(copysignf(r.x, x.x), copysignf(r.y, x.y));
+    return __fmul2_rn(__fmul2_rn(make_float2(0.5f, 0.5f), z), __fadd2_rn(make_float2(1.0f, 1.0f), er));
+}
 __device__ __forceinline__ float gelu_grad_f(float z) {
     float e2;
     const float er = erf_as(z * 0.70710678118654752f, e2);
     return fmaf(z * 0.39894228040143268f, e2, 0.5f * (1.0f + er));
 }
 __global__ void activation_kernel(const float* __restrict__ z, float* __restrict__ g, float* __restrict__ dg, int n) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        if (g) g[i] = gelu_f(z[i]);
-        if (dg) dg[i] = gelu_grad_f(z[i]);
+    // pairs of entries, g in the packed form of the forward epilogues (an odd last entry alone)
+    for (int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x); i < n; i += 2 * gridDim.x * blockDim.x) {
+        if (i + 1 < n) {
+            if (g) {
+                const float2 r = gelu2_f(make_float2(z[i], z[i + 1]));
+                g[i] = r.x;
+                g[i + 1] = r.y;
+            }
+            if (dg) {
+                dg[i] = gelu_grad_f(z[i]);
+                dg[i + 1] = gelu_grad_f(z[i + 1]);
+            }
+        } else {
+            if (g) g[i] = gelu_f(z[i]);
+            if (dg) dg[i] = gelu_grad_f(z[i]);
+        }
     }
 }
 __device__ __forceinline__ float warp_sum_f(float v) {
@@ -451,7 +484,11 @@ __global__ void __launch_bounds__(kFusedThreads) mlp_fused_forward_kernel(const 
             __syncwarp();
             tmem_ld16(taddr + (uint32_t)c0, v);
 #pragma unroll
-            for (int k = 0; k < 16; ++k) v[k] = gelu_f(v[k] + b1[c0 + k]);
+            for (int k = 0; k < 16; k += 2) {
+                const float2 g = gelu2_f(__fadd2_rn(make_float2(v[k], v[k + 1]), make_float2(b1[c0 + k], b1[c0 + k + 1])));
+                v[k] = g.x;
+                v[k + 1] = g.y;
+            }
             store_h_sw128(hs, r, c0, v);
         }
     }
@@ -481,7 +518,11 @@ __global__ void __launch_bounds__(kFusedThreads) mlp_fused_forward_kernel(const 
             __syncwarp();
             tmem_ld16(taddr + (uint32_t)(NH + c0), v);
 #pragma unroll
-            for (int k = 0; k < 16; ++k) v[k] = gelu_f(v[k] + b2[c0 + k]);
+            for (int k = 0; k < 16; k += 2) {
+                const float2 g = gelu2_f(__fadd2_rn(make_float2(v[k], v[k + 1]), make_float2(b2[c0 + k], b2[c0 + k + 1])));
+                v[k] = g.x;
+                v[k + 1] = g.y;
+            }
             store_h_sw128(hs, r, c0, v);
         }
     }
