@@ -116,19 +116,25 @@ __global__ void __launch_bounds__(256, mesh_sweep_minb<N1, C>()) mesh_sweep_kern
     store_collided<N1, C>(fout, g, x, y, s);
 }
 
+// Threads per (column, outgoing velocity) of the wall kernel: each sums every CH-th crossing row.
+template <int N1>
+constexpr int mesh_wall_chunks() {
+    return 1024 / (32 * wall_lanes<N1>()) >= 4 ? 4 : (1024 / (32 * wall_lanes<N1>()) >= 2 ? 2 : 1);
+}
+
 // The wall fill before a step: per wall and column (frame columns included), M_out(x) from the
 // outgoing velocities' rows that cross the wall (after the x part of the gather), then the
-// ghost row of every incoming velocity.  One thread per (column, outgoing velocity); the
-// column's shares are added in a fixed order in shared memory.
+// ghost row of every incoming velocity.  Threads (column, outgoing velocity, chunk c) sum the
+// crossing rows c, c + CH, ...; the column's shares are added in a fixed order in shared memory.
 template <int N1, class C>
-__global__ void __launch_bounds__(32 * wall_lanes<N1>()) mesh_wall_kernel(typename C::T* __restrict__ f, const KParams p,
-                                                                          const MeshDev m) {
+__global__ void __launch_bounds__(32 * wall_lanes<N1>() * mesh_wall_chunks<N1>())
+    mesh_wall_kernel(typename C::T* __restrict__ f, const KParams p, const MeshDev m) {
     using R = typename C::R;
     using T = typename C::T;
-    constexpr int NL = wall_lanes<N1>();
-    __shared__ R part[NL][32];
+    constexpr int NL = wall_lanes<N1>(), CH = mesh_wall_chunks<N1>();
+    __shared__ R part[CH][NL][32];
     __shared__ R amp[32];
-    const int tx = threadIdx.x, k = threadIdx.y;
+    const int tx = threadIdx.x, k = threadIdx.y, c = threadIdx.z;
     const int side = blockIdx.y;                 // 0: wall at F_0, 1: wall at F_ny
     const int xo = blockIdx.x * 32 + tx - FILL;  // output column, in [-FILL, nx + FILL)
     const bool col = xo < p.nx + FILL;
@@ -148,22 +154,23 @@ __global__ void __launch_bounds__(32 * wall_lanes<N1>()) mesh_wall_kernel(typena
             // padded entries (length 0 on row 0) add exact zeros: no data-dependent exit, so the
             // unrolled iterations' loads are in flight together
 #pragma unroll 4
-            for (int e = 0; e < m.kb; ++e) {
+            for (int e = c; e < m.kb; e += CH) {
                 const R le = __ldg(len + e);
                 const T* b = f + sidx(p, l, x - p.sh[i], __ldg(src + e));
                 acc += le * ((R(1) - ax) * to_f<C, R>(C::ld(b), w, ref) + ax * to_f<C, R>(C::ld(b - 1), w, ref));
             }
         }
-        part[k][tx] = acc;
+        part[c][k][tx] = acc;
     }
     __syncthreads();
-    if (k == 0) {
+    if (k == 0 && c == 0) {
         R sum = 0;
-        for (int kk = 0; kk < NL; ++kk) sum += part[kk][tx];
+        for (int kk = 0; kk < NL; ++kk)
+            for (int cc = 0; cc < CH; ++cc) sum += part[cc][kk][tx];
         amp[tx] = sum * kinvden<R>(p, side);
     }
     __syncthreads();
-    if (!col) return;
+    if (!col || c != 0) return;
     const int j = side == 0 ? N1 - 1 - jj : jj;  // the incoming velocity of this lane
     const int l = i + N1 * j;
     const R w = kw<R>(p, i) * kw<R>(p, j);
@@ -190,7 +197,7 @@ template <int N1, class C>
 cudaError_t step_as(const void* fin, void* fout, const KParams& p, const MeshDev& m, cudaStream_t s) {
     using T = typename C::T;
     if (p.walls) {
-        const dim3 block(32, wall_lanes<N1>()), grid((p.nx + 2 * FILL + 31) / 32, 2);
+        const dim3 block(32, wall_lanes<N1>(), mesh_wall_chunks<N1>()), grid((p.nx + 2 * FILL + 31) / 32, 2);
         mesh_wall_kernel<N1, C><<<grid, block, 0, s>>>((T*)fin, p, m);
     }
     const dim3 block(32, 8), grid((p.nx + 31) / 32, (p.ny + 7) / 8);
