@@ -806,41 +806,8 @@ __global__ void __launch_bounds__(FlowCfg<N1, C, CFG>::THREADS, FlowCfg<N1, C, C
 
     if (tid >= F::CONSUMERS) {  // ---- producer warp ----
         if (tid != F::CONSUMERS) return;
-        for (int n = 0;; ++n) {
-            const int st = n % F::STAGES;
-            const uint32_t par = ((n / F::STAGES) & 1) ^ 1;  // first use of each stage passes at once
-            const int task = atomicAdd(src.next_task, 1);
-            int code = task < total ? 0 : -1;
-            int k = 0, t = 0;
-            if (!code) {
-                const int* nb[9];
-                flow_task(src, task, k, t, nb);
-                const uint64_t t0 = global_ns();
-                const int need = k * F::DONE_PER_TASK + src.wait_extra;
-                for (;;) {
-                    int ready = 0;
-#pragma unroll
-                    for (int d = 0; d < 9; ++d) ready += ld_relaxed_gpu(nb[d]) >= need ? 1 : 0;
-                    if (ready == 9) break;
-                    if (*(volatile int*)src.abort || global_ns() - t0 > (uint64_t)src.wait_ns) {
-                        code = -2;
-                        break;
-                    }
-                    __nanosleep(64);
-                }
-            }
-            if (!mbar_wait_bounded(&empty[st], par, kWaitLimitNs)) code = -2;
-            if (code == -2) {
-                atomicExch(src.abort, 1);
-                if (p.status) atomicOr(p.status, 1);
-            }
-            if (code) {
-                slot[st] = code;
-                mbar_arrive(&full[st]);  // release: the consumers see the slot
-                return;
-            }
-            fence_acquire_gpu();
-            fence_proxy_async_global();
+        // Issue the TMA loads of task `task` (step k, tile t) into stage st and publish it.
+        auto issue = [&](int st, int t, int k) {
             int x0, y0;
             Geom g;
             const CUtensorMap *map, *smap;
@@ -855,6 +822,75 @@ __global__ void __launch_bounds__(FlowCfg<N1, C, CFG>::THREADS, FlowCfg<N1, C, C
                 const int i = l % N1, j = l / N1;
                 tma_load_3d(sb + l * WIN, map, &full[st], (x0 + g.hx - p.sh[i] - 1) & ~(A - 1), y0 + HY - p.sh[j] - 1,
                             l);
+            }
+        };
+        // Wait (bounded) until the 3 x 3 neighbourhoods of nt tasks (their completion counters nb,
+        // the counts need) have completed their previous step: 0, or -2 once the wait gives up.
+        auto await_nb = [&](const int* const (*nb)[9], const int* need, int nt) -> int {
+            const uint64_t t0 = global_ns();
+            for (;;) {
+                int ready = 0;
+                for (int q = 0; q < nt; ++q)
+#pragma unroll
+                    for (int d = 0; d < 9; ++d) ready += ld_relaxed_gpu(nb[q][d]) >= need[q] ? 1 : 0;
+                if (ready == 9 * nt) return 0;
+                if (*(volatile int*)src.abort || global_ns() - t0 > (uint64_t)src.wait_ns) return -2;
+                __nanosleep(64);
+            }
+        };
+        // Tasks come two at a time (stage 0, then stage 1, in the order they were handed out).
+        // Two tasks of the same step do not depend on each other: their neighbourhoods are polled
+        // together and one acquire fence covers both (the fence is the larger part of a task's
+        // cost for this thread).  Across a step boundary the second may depend on the first, so
+        // it is polled only after the first is issued.  With one stage, one task at a time.
+        constexpr int PAIR = F::STAGES == 2 ? 2 : 1;
+        for (int m = 0;; ++m) {
+            const int task0 = atomicAdd(src.next_task, PAIR);
+            const bool together = PAIR == 2 && task0 / src.ntiles == (task0 + 1) / src.ntiles;
+            int code[2], k[2] = {0, 0}, t[2] = {0, 0}, need[2] = {0, 0};
+            const int* nb[2][9];
+            int nt = 0;  // tasks of this round that exist
+#pragma unroll
+            for (int q = 0; q < PAIR; ++q) {
+                code[q] = task0 + q < total ? 0 : -1;
+                if (!code[q]) {
+                    flow_task(src, task0 + q, k[q], t[q], nb[q]);
+                    need[q] = k[q] * F::DONE_PER_TASK + src.wait_extra;
+                    ++nt;
+                }
+            }
+            bool fenced = false;
+            if (together && nt > 0) {
+                const int c = await_nb(nb, need, nt);
+                if (c) code[0] = code[1] = c;
+                else {
+                    fence_acquire_gpu();
+                    fence_proxy_async_global();
+                    fenced = true;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < PAIR; ++q) {
+                const int st = q, n = PAIR * m + q;
+                const uint32_t par = ((n / F::STAGES) & 1) ^ 1;  // first use of each stage passes at once
+                if (!code[q] && !fenced) {
+                    code[q] = await_nb(nb + q, need + q, 1);
+                    if (!code[q]) {
+                        fence_acquire_gpu();
+                        fence_proxy_async_global();
+                    }
+                }
+                if (!mbar_wait_bounded(&empty[st], par, kWaitLimitNs)) code[q] = -2;
+                if (code[q] == -2) {
+                    atomicExch(src.abort, 1);
+                    if (p.status) atomicOr(p.status, 1);
+                }
+                if (code[q]) {
+                    slot[st] = code[q];
+                    mbar_arrive(&full[st]);  // release: the consumers see the slot
+                    return;
+                }
+                issue(st, t[q], k[q]);
             }
         }
     }
